@@ -1,0 +1,464 @@
+"""Benchmark of the Hermite block-timestep N-body path on GB300.
+
+Default workload (N = 1): Plummer sphere, N = 16384, equal masses, eps = 1/1024,
+mixed precision (FP32 pair arithmetic, FP64 state / predictor / corrector),
+eta = 0.01, power-of-two block steps, integrated from t = 0 to t = 1.
+One bench step = load the resident initial state (nb_init_dev: initial forces
+with s = N and first steps), energy at t = 0, nb_run to t = 1 (one CUDA-graph
+launch), energy at t = 1. The metric is force+jerk interactions per second
+(sum over block steps of s*N, plus the initial s = N pass); block steps per
+second and |dE/E| are reported beside it, and the same for the FP64 GPU path.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank integrates its own replica (the workload is
+one system; ranks share no data), timing is the max over ranks, and the value
+is the sum of all ranks' interactions over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FLOP_PER_INTERACTION = 60          # the customary count for one force + jerk pair
+T_END = 1.0
+WORKLOAD = {"workload": "plummer N=16384 eps=1/1024 eta=0.01 t=0->1, mixed FP32/FP64",
+            "model": "plummer", "n": 16384, "eps": 1.0 / 1024, "eta": 0.01, "t_end": T_END,
+            "seed": 20071108}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend: str):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+    return ws, rank
+
+
+def dist_max(x: float, device=None) -> float:
+    ws, _, _ = dist_env()
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(x: float, device=None) -> float:
+    ws, _, _ = dist_env()
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def dist_barrier():
+    ws, _, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, period_ms: int = 200):
+        self.index = index
+        self.period = period_ms
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms={self.period}"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- helpers
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def fp32_peak_tflops(num_sms: int, sm_mhz: float) -> float:
+    """Non-tensor FP32 peak: SMs x 128 FMA lanes x 2 flop x clock."""
+    return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(snap, t_end: float, nthreads: int):
+    """The FP64 CPU oracle, as it stands, on the workload from t = 0 to t_end."""
+    import oracle
+    t0 = time.perf_counter()
+    sysr = oracle.System(snap.m, snap.x, snap.v, snap.eps2, eta=WORKLOAD["eta"], nthreads=nthreads)
+    assert sysr.status == 0
+    assert sysr.run(t_end) == 0
+    dt = time.perf_counter() - t0
+    c = sysr.counters
+    inter = c["interactions"] + float(snap.n) * snap.n   # + the initial s = N pass
+    return {"seconds": dt, "interactions": inter, "block_steps": c["block_steps"]}
+
+
+# ---------------------------------------------------------------- reference
+
+def run_reference(args):
+    ws, rank = dist_init("gloo")
+    if rank != 0:
+        return 0
+    import ics
+    import oracle
+    oracle.build()
+    snap = ics.config(2)
+    nthreads = oracle.default_threads()
+    t_sample = args.ref_t_end
+    for _ in range(args.warmup):
+        oracle_sample(snap, t_sample / 4, nthreads)
+    secs, inter, bsteps = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        r = oracle_sample(snap, t_sample, nthreads)
+        secs += r["seconds"]; inter += r["interactions"]; bsteps += r["block_steps"]
+    value = inter / secs
+    line = {
+        "impl": "reference", "metric": "force+jerk interactions/s", "value": value,
+        "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer sphere)",
+        "config": dict(WORKLOAD, sample=f"t=0->{t_sample} per step"),
+        "block_steps_per_s": bsteps / secs,
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"init (s=N pass) + block steps to t={t_sample} of the N=16384 Plummer run, "
+                                   f"per step; host {cpu_model()}"},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def main_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    dev = torch.device("cuda", local)
+
+    import ics
+    import paper_0711_0643_gb300 as pkg
+    if rank == 0 or ws == 1:
+        pkg.build()
+    dist_barrier()
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+
+    snap = ics.config(2)
+    n = snap.n
+    m_d = torch.tensor(snap.m, device=dev)
+    x_d = torch.tensor(snap.x, device=dev)
+    v_d = torch.tensor(snap.v, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def make_ctx(prec):
+        c = nb.Context(precision=prec, device=local, stream=sptr)
+        nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+        c.n = n
+        nb.nb_autotune(c.ctx)
+        return c
+
+    def step(c):
+        nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+        E0, _, _ = nb.nb_energy(c.ctx)
+        nb.nb_run(c.ctx, T_END)
+        E1, _, _ = nb.nb_energy(c.ctx)
+        st = nb.nb_stats(c.ctx)
+        return E0, E1, st
+
+    def timed_steps(c, k):
+        ms, last = [], None
+        for _ in range(k):
+            l2_flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(c)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return ms, last
+
+    # ---- mixed precision: the headline
+    c = make_ctx(nb.NB_PREC_MIXED)
+    for _ in range(args.warmup):
+        step(c)
+    dist_barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local).start()
+    ms, (E0, E1, st) = timed_steps(c, args.steps)
+    torch.cuda.synchronize(dev)
+    dist_barrier()
+    clk = clocks.stop()
+    total_ms = dist_max(sum(ms), dev)
+    inter_step = st["interactions"] + float(n) * n
+    inter_all = dist_sum(inter_step * args.steps, dev)
+    value = inter_all / (total_ms / 1e3)
+    bsteps = st["block_steps"]
+    dE = abs(E1 - E0) / abs(E0)
+    # kernels per step: layout (2) + pad, predict, iota, force, init_steps (5) + energy 2 x 2
+    # + first select (1) + 4 per block step (predict, force, correct, select)
+    launches = 2 + 5 + 4 + 1 + 4 * bsteps
+
+    # ---- roofline of the dominant kernel (force), same trajectory, events around each launch
+    nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+    torch.cuda.synchronize(dev)
+    clk_rf = ClockSampler(local).start()
+    force_ms, nlaunch = nb.nb_run_timed(c.ctx, T_END)
+    clk_rf_s = clk_rf.stop()
+    st_rf = nb.nb_stats(c.ctx)
+    sm_mhz = clk["sm_mhz"] or clk_rf_s["sm_mhz"] or load_peaks().get("clocks_under_load", {}).get("sm_mhz_median")
+    peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None
+    achieved = FLOP_PER_INTERACTION * st_rf["interactions"] / (force_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "kernel": "force_mixed_kernel", "launches": nlaunch,
+                "avg_launch_us": 1e3 * force_ms / max(nlaunch, 1),
+                "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz} MHz (median SM clock "
+                              f"sampled during the timed region)",
+                "flop_convention": f"{FLOP_PER_INTERACTION} flop per force+jerk interaction"}
+
+    # ---- end to end through the C ABI with host buffers
+    m_h = np.ascontiguousarray(snap.m); x_h = np.ascontiguousarray(snap.x); v_h = np.ascontiguousarray(snap.v)
+    ce = nb.Context(precision=nb.NB_PREC_MIXED, device=local, stream=sptr)
+    ce.init(snap)
+    nb.nb_autotune(ce.ctx)
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        nb.nb_init(ce.ctx, m_h, x_h, v_h, snap.eps2)
+        nb.nb_energy(ce.ctx)
+        nb.nb_run(ce.ctx, T_END)
+        nb.nb_energy(ce.ctx)
+        out = ce.state()
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    ce.close()
+    e2e_total = dist_max(sum(e2e_ms), dev)
+    e2e_value = dist_sum(inter_step * len(e2e_ms), dev) / (e2e_total / 1e3)
+    h2d = n * (8 + 24 + 24)
+    d2h = n * (8 + 24 * 4 + 8 + 8) + 3 * 8
+
+    # ---- FP64 GPU path on the same workload (one step, events)
+    fp64 = None
+    if not args.no_fp64:
+        c64 = make_ctx(nb.NB_PREC_FP64)
+        step(c64)   # warm
+        ms64, (F0, F1, st64) = timed_steps(c64, 1)
+        fp64 = {"interactions_per_s": (st64["interactions"] + float(n) * n) / (ms64[0] / 1e3),
+                "block_steps_per_s": st64["block_steps"] / (ms64[0] / 1e3),
+                "abs_dE_over_E": abs(F1 - F0) / abs(F0), "ms_per_step": ms64[0],
+                "block_steps": st64["block_steps"]}
+        c64.close()
+
+    # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed, one evaluation per s
+    sweep = None
+    if args.sweep and rank == 0:
+        sweep = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        nth = oracle.default_threads()
+        r = oracle_sample(snap, args.ref_t_end, nth)
+        cpu = {"value": r["interactions"] / r["seconds"], "unit": "interactions/s", "cores": nth,
+               "kind": "oracle", "sample": f"init (s=N pass) + {r['block_steps']} block steps to "
+                                          f"t={args.ref_t_end} of the same N=16384 Plummer run "
+                                          f"({r['seconds']:.1f} s); host {cpu_model()}"}
+
+    c.close()
+    if rank == 0:
+        line = {
+            "metric": "force+jerk interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pair arithmetic, f64 state",
+            "data": "synthetic (seeded Plummer sphere, N-body units)",
+            "config": dict(WORKLOAD, l2="flushed (256 MB write) before every timed step",
+                           parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+            "block_steps_per_s": dist_sum(bsteps * args.steps, dev) / (total_ms / 1e3),
+            "block_steps": bsteps, "abs_dE_over_E": dE,
+            "gpu_launches": launches * args.steps,
+            "clocks": clk,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / len(e2e_ms)},
+            "fp64_gpu": fp64,
+            "force_sweep": sweep,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz):
+    """King W0 = 6, N = 1,048,576, eps = 1e-3: one mixed force evaluation per active-set
+    size s in {1, 64, 1024, 16384, N} (active = first s of a seeded permutation, ascending),
+    split factor autotuned; interactions/s and FP32 roofline fraction per s."""
+    import ics
+    snap = ics.config(5)
+    n = snap.n
+    m_d = torch.tensor(snap.m, device=dev)
+    x_d = torch.tensor(snap.x, device=dev)
+    v_d = torch.tensor(snap.v, device=dev)
+    c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+    nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+    nb.nb_predict(c.ctx, 0.0)
+    nb.nb_autotune(c.ctx)
+    perm = np.argsort(ics.SplitMix64(ics.BASE_SEED + 5).uniform(n))
+    out = {"workload": "king W0=6 N=1048576 eps=1e-3, single evaluation", "points": []}
+    stream = torch.cuda.current_stream(dev)
+    for s in (1, 64, 1024, 16384, n):
+        idx = np.sort(perm[:s]).astype(np.int32)
+        idx_d = torch.tensor(idx, device=dev)
+        a_d = torch.empty((s, 3), dtype=torch.float64, device=dev)
+        k_d = torch.empty_like(a_d)
+        p_d = torch.empty(s, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
+        reps = 3 if s < n else 2
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        ips = s * float(n) / sec
+        tfl = FLOP_PER_INTERACTION * ips / 1e12
+        peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None
+        out["points"].append({"s": s, "ms": sec * 1e3, "interactions_per_s": ips, "tflops": tfl,
+                              "frac_fp32_peak": tfl / peak if peak else None})
+    c.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-t-end", type=float, default=1.0 / 16,
+                    help="integration horizon of one oracle sample (bounded CPU work)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
+                    help="full-N force sweep on King N=2^20 (default on)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return main_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,216 @@
+/*
+ * nbody.h -- C ABI of the GB300 (sm_103a) Hermite block-timestep direct N-body
+ * library (libnbody.so).
+ *
+ * The library implements the hot path of the integrator described in
+ * Portegies Zwart et al., "A parallel gravitational N-body kernel" (Sect. 2.1):
+ * block selection by the smallest t_i + dt_i, the Hermite predictor for all
+ * particles, the softened acceleration / jerk / potential of the active block
+ * against all N predicted particles (Eq. Force), the Hermite corrector and
+ * the Aarseth time step (Eq. timestep) quantised to powers of two. The
+ * paper's j-parallelisation over processors (Sect. 3) becomes an on-chip
+ * decomposition: j-tiles staged in shared memory, register-blocked i, and a
+ * fixed-order reduction over j-splits.
+ *
+ * Conventions
+ *   - G = 1. Vectors are double[n][3], row-major (x0 y0 z0 x1 ...).
+ *   - Host pointers are caller-owned and are only read/written during the call.
+ *     "_dev" entry points take device pointers of the context's device and
+ *     work on the context's stream; they return before the GPU work ends.
+ *   - The library allocates and owns all its device memory (freed by
+ *     nb_destroy). A context is not thread-safe; use one per host thread.
+ *   - Every call returns an nb_status. NB_ERR_CUDA reports a CUDA runtime
+ *     error; device-side conditions (non-finite values, a time step below
+ *     dt_min, a device wait that ran past its spin limit) are accumulated in
+ *     a device status word and reported by the next call that synchronises
+ *     (nb_next_block, nb_force_jerk, nb_step, nb_run, nb_energy, nb_get_state,
+ *     nb_sync). nb_last_error() gives a one-line description.
+ *   - Precision: NB_PREC_MIXED does the pair arithmetic in FP32 with
+ *     double-single (hi + lo) positions and compensated partial sums; the
+ *     state, predictor, corrector and energy stay FP64. NB_PREC_FP64 does all
+ *     of it in FP64.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx;
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = -1,           /* bad argument (size, NULL, order) */
+    NB_ERR_CUDA = -2,          /* CUDA runtime error, or no usable device */
+    NB_ERR_NONFINITE = -3,     /* a force, position or velocity became NaN/inf */
+    NB_ERR_DT_UNDERFLOW = -4,  /* a quantised step fell below dt_min */
+    NB_ERR_TIMEOUT = -5,       /* a device-side wait exceeded its spin limit */
+    NB_ERR_STATE = -6          /* call out of order (e.g. nb_correct before nb_force_jerk) */
+} nb_status;
+
+typedef enum { NB_PREC_MIXED = 0, NB_PREC_FP64 = 1 } nb_precision;
+
+typedef struct {
+    double eta;           /* accuracy parameter nu of Eq. (timestep); default 0.01 */
+    double dt_max;        /* largest step, a power of two; default 1/16 */
+    double dt_min;        /* smallest step; default 2^-40 (below: NB_ERR_DT_UNDERFLOW) */
+    int32_t precision;    /* nb_precision; default NB_PREC_MIXED */
+    int32_t autotune;     /* 1: time the kernel variants per active-set size on first use */
+    int64_t spin_limit;   /* iteration cap of every device-side wait; default 1<<24 */
+    int32_t device;       /* CUDA device ordinal; -1 = the current device */
+    int32_t inject;       /* test hook: 1 = the next force launch waits on a barrier that
+                             nothing completes, so its spin limit must expire */
+} nb_config;
+
+/* Counters since nb_init (block steps, particle steps sum s, interactions sum s*N). */
+typedef struct {
+    int64_t block_steps;
+    int64_t particle_steps;
+    double interactions;
+    double t_now;          /* largest t_i */
+} nb_counters;
+
+/* Full particle state; arrays of length n ([n][3] for vectors), caller-owned. */
+typedef struct {
+    int64_t n;
+    double *m, *x, *v, *a, *k, *t, *dt;
+} nb_state_view;
+
+/* Fills *cfg with the defaults listed above. */
+void nb_config_default(nb_config *cfg);
+
+/* Creates a context on cfg->device. stream: a cudaStream_t to run on, or NULL
+ * for a stream the library creates (non-blocking). cfg NULL = defaults.
+ * Errors: NB_ERR_ARG (ctx NULL, bad config), NB_ERR_CUDA (no device). */
+nb_status nb_create(nb_ctx **ctx, const nb_config *cfg, void *stream);
+
+/* Frees the context and its device memory. NULL is ignored. */
+void nb_destroy(nb_ctx *ctx);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *nb_last_error(const nb_ctx *ctx);
+
+/* Loads n particles (m[n], x[n][3], v[n][3], host) with softening eps2 = eps^2
+ * (Plummer softening; the paper's Eq. Force has none), sets t_i = 0, computes
+ * a and k by a full force pass (s = n) and the first steps
+ * dt_i = 2^floor(log2(eta |a|/|k|)) capped at dt_max (Sect. 2.1 is silent on
+ * the start; this is the usual Aarseth start with eta_s = eta).
+ * Errors: NB_ERR_ARG (n < 1 or n > 2^31-1, eps2 < 0), NB_ERR_NONFINITE,
+ * NB_ERR_DT_UNDERFLOW, NB_ERR_CUDA. */
+nb_status nb_init(nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v,
+                  double eps2);
+
+/* As nb_init with device pointers (same layouts). */
+nb_status nb_init_dev(nb_ctx *ctx, int64_t n, const double *m_dev, const double *x_dev,
+                      const double *v_dev, double eps2);
+
+/* Block selection (Sect. 2.1, first bullet): t_next = min_i (t_i + dt_i) and the
+ * active list {i : t_i + dt_i == t_next} in ascending i, kept on the device
+ * for nb_force_jerk/nb_correct. Writes *t_next and *s (host). */
+nb_status nb_next_block(nb_ctx *ctx, double *t_next, int64_t *s);
+
+/* Copies the active list of the last nb_next_block (int32[s], ascending) to host. */
+nb_status nb_get_active(nb_ctx *ctx, int32_t *idx);
+
+/* Hermite predictor (Sect. 2.1): every particle j to time t:
+ * x_p = x + v d + a d^2/2 + k d^3/6, v_p = v + a d + k d^2/2, d = t - t_j.
+ * Writes the predicted j-records used by nb_force_jerk; the state is unchanged. */
+nb_status nb_predict(nb_ctx *ctx, double t);
+
+/* Copies the predicted positions and velocities of the last nb_predict (or of the
+ * predictor step inside nb_step / nb_run) to host arrays xp[n][3], vp[n][3]
+ * (either may be NULL). In mixed precision these are the j-records as the
+ * force kernel sees them: hi + lo for positions, the FP32 velocity. */
+nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp);
+
+/* Eq. (Force) and its time derivative on the active list idx[s] (host, int32,
+ * strictly ascending, each < n) against all n particles as last predicted:
+ *   a_i = sum_{j != i} m_j r / (r^2+eps^2)^{3/2},
+ *   k_i = sum_{j != i} m_j [ w / (r^2+eps^2)^{3/2} - 3 (r.w) r / (r^2+eps^2)^{5/2} ],
+ *   phi_i = - sum_{j != i} m_j / (r^2+eps^2)^{1/2},   r = x_j - x_i, w = v_j - v_i.
+ * idx NULL = the active list of the last nb_next_block (s must match it).
+ * a, k: double[s][3]; phi: double[s] (host); any of them may be NULL (then that
+ * output stays on the device for nb_correct). s = 0 is a no-op.
+ * Errors: NB_ERR_ARG (s < 0, s > n, idx not ascending or out of range),
+ * NB_ERR_NONFINITE (a result is NaN/inf), NB_ERR_TIMEOUT, NB_ERR_CUDA. */
+nb_status nb_force_jerk(nb_ctx *ctx, const int32_t *idx, int64_t s, double *a, double *k,
+                        double *phi);
+
+/* As nb_force_jerk with device pointers: idx_dev int32[s] (strictly ascending,
+ * each < n, not checked), a_dev/k_dev double[s][3], phi_dev double[s]; any
+ * output may be NULL. Asynchronous on the context's stream. */
+nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, double *a_dev,
+                            double *k_dev, double *phi_dev);
+
+/* Hermite corrector and new steps (Sect. 2.1, Eq. timestep) for the active list
+ * of the last nb_force_jerk, whose members must all have t_i + dt_i == t_block
+ * (the paper's "dt" argument is read as the block time; each particle's own
+ * step is dt_i = t_block - t_i). Uses the forces of that call.
+ * Errors: NB_ERR_STATE (no forces pending, or a member not due at t_block),
+ * NB_ERR_NONFINITE, NB_ERR_DT_UNDERFLOW, NB_ERR_CUDA. */
+nb_status nb_correct(nb_ctx *ctx, double t_block);
+
+/* One block step on the device: select, predict all, force on the block,
+ * correct (no host round trip). */
+nb_status nb_step(nb_ctx *ctx);
+
+/* Block steps until the next block time exceeds t_end (t_end must be a multiple
+ * of dt_max for every particle to land on it). One CUDA-graph launch whose
+ * while-node repeats predict -> force -> correct -> select on the device.
+ * One call runs at most 2^24 block steps (then NB_ERR_STATE, "block-step cap"). */
+nb_status nb_run(nb_ctx *ctx, double t_end);
+
+/* Same trajectory as nb_run, driven from the host one block step at a time, with
+ * CUDA events around every force launch. *force_ms = summed force-kernel time,
+ * *launches = number of force launches (NULL allowed). For measurement. */
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches);
+
+/* Kinetic, potential (softened, W = sum m_i phi_i / 2) and total energy of the
+ * current state, in FP64 on the device. Exact only when all t_i are equal
+ * (e.g. after nb_run). Any pointer may be NULL. */
+nb_status nb_energy(nb_ctx *ctx, double *E, double *K, double *W);
+
+/* Copies the full FP64 state to / from host arrays (view->n must equal the
+ * context's n; set_state also needs a consistent t, dt). */
+nb_status nb_get_state(nb_ctx *ctx, nb_state_view *view);
+nb_status nb_set_state(nb_ctx *ctx, const nb_state_view *view);
+
+/* Counters since nb_init. */
+nb_status nb_stats(nb_ctx *ctx, nb_counters *out);
+
+/* Waits for the context's stream and reports pending device-side errors. */
+nb_status nb_sync(nb_ctx *ctx);
+
+/* Kernel tuning. nb_autotune times every force-kernel variant and split factor
+ * for active-set sizes 1, 2, 4, ..., n on the current predicted state and keeps
+ * the fastest per size bucket. nb_set_tuning forces (variant, split) for a
+ * bucket (bucket b holds s in (2^(b-1), 2^b]); variant -1 restores the default.
+ * nb_get_tuning reads the table (variant[32], split[32]). */
+nb_status nb_autotune(nb_ctx *ctx);
+nb_status nb_set_tuning(nb_ctx *ctx, int32_t bucket, int32_t variant, int32_t split);
+nb_status nb_get_tuning(nb_ctx *ctx, int32_t *variant, int32_t *split);
+/* Number of force-kernel variants of the context's precision and a short name. */
+int32_t nb_num_variants(const nb_ctx *ctx);
+const char *nb_variant_name(const nb_ctx *ctx, int32_t variant);
+
+/* Batched ensemble of nc independent systems (Sect. 2.1 applied to each):
+ * offsets[nc+1] delimit each system's particles in the concatenated arrays
+ * m[N], x[N][3], v[N][3] (host, N = offsets[nc]); eps2[nc] per system. Each
+ * system keeps its own block schedule. Replaces any single-system state. */
+nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, const double *m,
+                           const double *x, const double *v, const double *eps2);
+
+/* Advances every system of the ensemble to t_end in one persistent launch. */
+nb_status nb_ensemble_run(nb_ctx *ctx, double t_end);
+
+/* Per-system energies (E[nc], host) and counters summed over the ensemble. */
+nb_status nb_ensemble_energy(nb_ctx *ctx, double *E);
+nb_status nb_ensemble_get_state(nb_ctx *ctx, nb_state_view *view);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

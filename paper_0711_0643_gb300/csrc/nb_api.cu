@@ -1,0 +1,902 @@
+// C ABI of libnbody.so: context, device memory, the block-step engine and the
+// kernel tuner. See include/nbody.h for the contract of every entry point.
+//
+// Engine: nb_run builds (once per context) a CUDA graph
+//     select -> WHILE( predict -> force -> correct -> select )
+// where select sets the while-node condition on the device (next block time
+// <= t_end, no error). One graph launch integrates to t_end with no host
+// round trip per block step; the force kernel sizes its work from the active
+// count it reads on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nb;
+
+struct nb_ctx {
+    nb_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    int64_t n = 0, n_pad = 0, n_tiles = 0;
+    double eps2 = 0.0;
+
+    // state [3][n_pad] for vectors
+    double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr, *k = nullptr, *t = nullptr, *dt = nullptr;
+    JRecs j{};
+    double *xp = nullptr, *vp = nullptr;
+    double *stage = nullptr;      // [3 n] staging for layout changes
+    int32_t *idx = nullptr;
+    int64_t *s = nullptr;
+    double *t_next = nullptr, *t_end = nullptr;
+    double *part = nullptr;
+    int64_t part_cap = 0;
+    int32_t *split_used = nullptr;
+    Tuning *tune_dev = nullptr;
+    Tuning tune{};
+    int32_t *status = nullptr;
+    int64_t *counters = nullptr;  // [0] block steps [1] particle steps [2] cap
+    double *interactions = nullptr;
+    double *en_scratch = nullptr;
+    int en_ctas = 0;
+    double *en_out = nullptr;
+    double *out_a = nullptr, *out_k = nullptr, *out_phi = nullptr;
+    int32_t *sel_cnt = nullptr;
+    double *sel_min = nullptr;
+    int32_t *done_ctr = nullptr;
+
+    bool have_state = false;
+    bool forces_pending = false;
+    int64_t block_s = -1;          // s of the last selection / force call
+    bool tuned = false;
+
+    cudaGraphExec_t run_exec = nullptr;
+    std::vector<cudaEvent_t> ev;   // timing events for nb_run_timed
+
+    std::string err;
+    int inject_pending = 0;
+};
+
+namespace {
+
+constexpr int64_t kMaxRunSteps = int64_t(1) << 24;   // block steps per nb_run call
+
+nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, NB_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+StepArgs step_args(nb_ctx *c)
+{
+    StepArgs A{};
+    A.n = c->n;
+    A.n_pad = c->n_pad;
+    A.m = c->m; A.x = c->x; A.v = c->v; A.a = c->a; A.k = c->k; A.t = c->t; A.dt = c->dt;
+    A.j = c->j;
+    A.xp = c->xp; A.vp = c->vp;
+    A.precision = c->cfg.precision;
+    A.eps2 = c->eps2;
+    A.eta = c->cfg.eta; A.dt_max = c->cfg.dt_max; A.dt_min = c->cfg.dt_min;
+    A.idx = c->idx; A.s = c->s; A.t_next = c->t_next; A.t_end = c->t_end;
+    A.part = c->part; A.split_used = c->split_used;
+    A.status = c->status; A.counters = c->counters; A.interactions = c->interactions;
+    A.chunk_cnt = c->sel_cnt; A.chunk_min = c->sel_min; A.done_ctr = c->done_ctr;
+    A.select_ctas = 1;
+    return A;
+}
+
+ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
+{
+    ForceArgs F{};
+    F.n = c->n;
+    F.n_tiles = c->n_tiles;
+    F.j = c->j;
+    F.xp = c->xp; F.vp = c->vp; F.m = c->m;
+    F.eps2f = (float)c->eps2;
+    F.eps2 = c->eps2;
+    F.idx = c->idx;
+    F.s = c->s;
+    F.part = c->part;
+    F.part_cap = c->part_cap;
+    F.split_used = c->split_used;
+    F.tune = c->tune_dev;
+    F.force_variant = variant;
+    F.force_split = split;
+    F.status = c->status;
+    F.spin_limit = c->cfg.spin_limit;
+    F.inject = 0;
+    return F;
+}
+
+int force_grid(nb_ctx *c)
+{
+    const int occ = c->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
+    return c->num_sms * occ;
+}
+
+cudaError_t launch_force(nb_ctx *c, const ForceArgs &F)
+{
+    return c->cfg.precision == NB_PREC_FP64 ? launch_force_f64(F, force_grid(c), c->stream)
+                                            : launch_force_mixed(F, force_grid(c), c->stream);
+}
+
+// force launch honouring the one-shot injection hook
+cudaError_t launch_force_ctx(nb_ctx *c)
+{
+    ForceArgs F = force_args(c);
+    if (c->inject_pending) {
+        F.inject = 1;
+        c->inject_pending = 0;
+    }
+    return launch_force(c, F);
+}
+
+void free_system(nb_ctx *c)
+{
+    if (c->run_exec) {
+        cudaGraphExecDestroy(c->run_exec);
+        c->run_exec = nullptr;
+    }
+    void *ptrs[] = {c->m, c->x, c->v, c->a, c->k, c->t, c->dt, c->j.hi, c->j.lo, c->j.vel, c->xp, c->vp,
+                    c->stage, c->idx, c->part, c->en_scratch, c->out_a, c->out_k, c->out_phi};
+    for (void *p : ptrs) dfree(p);
+    c->m = c->x = c->v = c->a = c->k = c->t = c->dt = nullptr;
+    c->j = JRecs{};
+    c->xp = c->vp = c->stage = nullptr;
+    c->idx = nullptr;
+    c->part = nullptr;
+    c->en_scratch = nullptr;
+    c->out_a = c->out_k = c->out_phi = nullptr;
+    c->n = c->n_pad = c->n_tiles = 0;
+    c->have_state = false;
+    c->forces_pending = false;
+    c->tuned = false;
+}
+
+nb_status alloc_system(nb_ctx *ctx, int64_t n)
+{
+    free_system(ctx);
+    ctx->n = n;
+    ctx->n_tiles = (n + kJT - 1) / kJT;
+    ctx->n_pad = ctx->n_tiles * kJT;
+    const int64_t np = ctx->n_pad;
+    CK(dalloc(&ctx->m, np));
+    CK(dalloc(&ctx->x, 3 * np));
+    CK(dalloc(&ctx->v, 3 * np));
+    CK(dalloc(&ctx->a, 3 * np));
+    CK(dalloc(&ctx->k, 3 * np));
+    CK(dalloc(&ctx->t, np));
+    CK(dalloc(&ctx->dt, np));
+    CK(dalloc(&ctx->j.hi, np));
+    CK(dalloc(&ctx->j.lo, np));
+    CK(dalloc(&ctx->j.vel, np));
+    CK(dalloc(&ctx->xp, 3 * np));
+    CK(dalloc(&ctx->vp, 3 * np));
+    CK(dalloc(&ctx->stage, 3 * np));
+    CK(dalloc(&ctx->idx, np));
+    // partials: room for s * split * 8 doubles; at least 4 splits of a full block
+    ctx->part_cap = std::max<int64_t>(4 * np * kPartStride, int64_t(1) << 23);
+    CK(dalloc(&ctx->part, ctx->part_cap));
+    ctx->en_ctas = (int)((n + 127) / 128);
+    CK(dalloc(&ctx->en_scratch, 2 * (size_t)ctx->en_ctas));
+    CK(dalloc(&ctx->out_a, 3 * np));
+    CK(dalloc(&ctx->out_k, 3 * np));
+    CK(dalloc(&ctx->out_phi, np));
+    CK(cudaMemsetAsync(ctx->a, 0, 3 * np * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->k, 0, 3 * np * sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(ctx->t, 0, np * sizeof(double), ctx->stream));
+    return NB_OK;
+}
+
+void fill_default_tuning(nb_ctx *c)
+{
+    const int occ = c->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
+    for (int b = 0; b < kBuckets; ++b) {
+        int64_t s = int64_t(1) << b;
+        if (s > c->n) s = c->n;
+        int v, S;
+        default_tuning(c->cfg.precision, c->n, s, c->num_sms, occ, &v, &S);
+        c->tune.variant[b] = v;
+        c->tune.split[b] = S;
+    }
+}
+
+nb_status upload_tuning(nb_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->tune_dev, &ctx->tune, sizeof(Tuning), cudaMemcpyHostToDevice, ctx->stream));
+    return NB_OK;
+}
+
+// Reads and clears the device status word; maps it to an nb_status.
+nb_status sync_status(nb_ctx *ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream));
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st == 0) return NB_OK;
+    CK(cudaMemset(ctx->status, 0, sizeof(int32_t)));
+    if (st & kStTimeout) return fail(ctx, NB_ERR_TIMEOUT, "a device-side wait exceeded the spin limit");
+    if (st & kStNonfinite) return fail(ctx, NB_ERR_NONFINITE, "non-finite force, position or velocity");
+    if (st & kStUnderflow) return fail(ctx, NB_ERR_DT_UNDERFLOW, "time step below dt_min");
+    if (st & kStState) return fail(ctx, NB_ERR_STATE, "active particle not due at the block time");
+    if (st & kStSteps) return fail(ctx, NB_ERR_STATE, "block-step cap reached");
+    return fail(ctx, NB_ERR_CUDA, "unknown device status %d", st);
+}
+
+// Common tail of nb_init / nb_init_dev: state x, v, m loaded (SoA), a = k = 0.
+nb_status init_forces(nb_ctx *ctx)
+{
+    StepArgs A = step_args(ctx);
+    CK(launch_pad_records(A, ctx->stream));
+    CK(launch_predict(A, false, 0.0, ctx->stream));    // t = 0, a = k = 0: records = positions
+    CK(launch_fill_iota(ctx->idx, ctx->n, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->s, &ctx->n, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    fill_default_tuning(ctx);
+    nb_status rs = upload_tuning(ctx);
+    if (rs != NB_OK) return rs;
+    CK(launch_force_ctx(ctx));
+    CK(launch_init_steps(A, ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters, 0, 2 * sizeof(int64_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->interactions, 0, sizeof(double), ctx->stream));
+    ctx->have_state = true;
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    nb_status st = sync_status(ctx);
+    if (st == NB_OK && ctx->cfg.autotune && !ctx->tuned) st = nb_autotune(ctx);
+    return st;
+}
+
+nb_status check_ctx(nb_ctx *ctx, bool need_state)
+{
+    if (!ctx) return NB_ERR_ARG;
+    ctx->err.clear();
+    if (need_state && !ctx->have_state) return fail(ctx, NB_ERR_STATE, "no particles loaded (call nb_init)");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(ctx, NB_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return NB_OK;
+}
+
+nb_status build_run_graph(nb_ctx *ctx)
+{
+    if (ctx->run_exec) return NB_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    StepArgs A = step_args(ctx);
+    // 1) first selection (sets the condition)
+    CK(cudaStreamBeginCaptureToGraph(ctx->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaError_t e1 = launch_select(A, (unsigned long long)h, true, ctx->stream);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, NB_ERR_CUDA, "graph capture (select): %s / %s", cudaGetErrorString(e1),
+                    cudaGetErrorString(e2));
+    }
+    size_t nn = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+    // 2) while node
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    CK(cudaGraphAddNode(&wn, g, nodes.data(), nullptr, nn, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // 3) body: predict -> force -> correct -> select
+    CK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaError_t eb = launch_predict(A, true, 0.0, ctx->stream);
+    if (eb == cudaSuccess) eb = launch_force(ctx, force_args(ctx));
+    if (eb == cudaSuccess) eb = launch_correct(A, false, ctx->stream);
+    if (eb == cudaSuccess) eb = launch_select(A, (unsigned long long)h, true, ctx->stream);
+    cudaGraph_t body_out = body;
+    cudaError_t ee = cudaStreamEndCapture(ctx->stream, &body_out);
+    if (eb != cudaSuccess || ee != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, NB_ERR_CUDA, "graph capture (body): %s / %s", cudaGetErrorString(eb),
+                    cudaGetErrorString(ee));
+    }
+    cudaError_t ei = cudaGraphInstantiate(&ctx->run_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        ctx->run_exec = nullptr;
+        return fail(ctx, NB_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+    return NB_OK;
+}
+
+nb_status set_t_end(nb_ctx *ctx, double t_end)
+{
+    CK(cudaMemcpyAsync(ctx->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    return NB_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+void nb_config_default(nb_config *cfg)
+{
+    if (!cfg) return;
+    cfg->eta = 0.01;
+    cfg->dt_max = 1.0 / 16.0;
+    cfg->dt_min = std::ldexp(1.0, -40);
+    cfg->precision = NB_PREC_MIXED;
+    cfg->autotune = 0;
+    cfg->spin_limit = int64_t(1) << 24;
+    cfg->device = -1;
+    cfg->inject = 0;
+}
+
+nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    nb_ctx *ctx = new nb_ctx();
+    if (cfg)
+        ctx->cfg = *cfg;
+    else
+        nb_config_default(&ctx->cfg);
+    const nb_config &c = ctx->cfg;
+    auto bad = [&](const char *why) {
+        delete ctx;
+        (void)why;
+        return NB_ERR_ARG;
+    };
+    if (!(c.eta > 0) || !(c.dt_max > 0) || !(c.dt_min > 0) || c.dt_min > c.dt_max) return bad("steps");
+    int e2;
+    if (std::frexp(c.dt_max, &e2) != 0.5) return bad("dt_max must be a power of two");
+    if (c.precision != NB_PREC_MIXED && c.precision != NB_PREC_FP64) return bad("precision");
+    if (c.spin_limit < 1) return bad("spin_limit");
+    int dev = c.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        delete ctx;
+        return NB_ERR_CUDA;
+    }
+    if (cudaSetDevice(dev) != cudaSuccess) {
+        delete ctx;
+        return NB_ERR_CUDA;
+    }
+    ctx->device = dev;
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete ctx;
+        return NB_ERR_CUDA;
+    }
+    if (stream) {
+        ctx->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return NB_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    ctx->inject_pending = c.inject;
+    (void)force_mixed_ctas_per_sm();   // sets kernel attributes before any graph capture
+    (void)force_f64_ctas_per_sm();
+    bool ok = dalloc(&ctx->s, 1) == cudaSuccess && dalloc(&ctx->t_next, 1) == cudaSuccess &&
+              dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
+              dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
+              dalloc(&ctx->counters, 3) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
+              dalloc(&ctx->en_out, 2) == cudaSuccess && dalloc(&ctx->sel_cnt, 1024) == cudaSuccess &&
+              dalloc(&ctx->sel_min, 1024) == cudaSuccess && dalloc(&ctx->done_ctr, 1) == cudaSuccess;
+    if (!ok) {
+        nb_destroy(ctx);
+        return NB_ERR_CUDA;
+    }
+    int64_t init_counters[3] = {0, 0, int64_t(1) << 40};
+    int32_t one = 1;
+    bool ok2 = cudaMemset(ctx->status, 0, sizeof(int32_t)) == cudaSuccess &&
+               cudaMemcpy(ctx->counters, init_counters, sizeof init_counters, cudaMemcpyHostToDevice) ==
+                   cudaSuccess &&
+               cudaMemcpy(ctx->split_used, &one, sizeof one, cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemset(ctx->interactions, 0, sizeof(double)) == cudaSuccess;
+    if (!ok2) {
+        nb_destroy(ctx);
+        return NB_ERR_CUDA;
+    }
+    *out = ctx;
+    return NB_OK;
+}
+
+void nb_destroy(nb_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_system(ctx);
+    void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
+                    ctx->counters, ctx->interactions, ctx->en_out, ctx->sel_cnt, ctx->sel_min, ctx->done_ctr};
+    for (void *p : ptrs) dfree(p);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *nb_last_error(const nb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+nb_status nb_init(nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v, double eps2)
+{
+    nb_status st = check_ctx(ctx, false);
+    if (st != NB_OK) return st;
+    if (n < 1 || n > INT32_MAX) return fail(ctx, NB_ERR_ARG, "n = %lld out of range", (long long)n);
+    if (!m || !x || !v) return fail(ctx, NB_ERR_ARG, "null input array");
+    if (!(eps2 >= 0.0) || !std::isfinite(eps2)) return fail(ctx, NB_ERR_ARG, "eps2 must be finite and >= 0");
+    st = alloc_system(ctx, n);
+    if (st != NB_OK) return st;
+    ctx->eps2 = eps2;
+    const int64_t np = ctx->n_pad;
+    CK(cudaMemcpyAsync(ctx->m, m, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_aos_to_soa(ctx->stage, ctx->x, n, np, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(ctx->stage, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_aos_to_soa(ctx->stage, ctx->v, n, np, ctx->stream));
+    return init_forces(ctx);
+}
+
+nb_status nb_init_dev(nb_ctx *ctx, int64_t n, const double *m, const double *x, const double *v, double eps2)
+{
+    nb_status st = check_ctx(ctx, false);
+    if (st != NB_OK) return st;
+    if (n < 1 || n > INT32_MAX) return fail(ctx, NB_ERR_ARG, "n = %lld out of range", (long long)n);
+    if (!m || !x || !v) return fail(ctx, NB_ERR_ARG, "null input array");
+    if (!(eps2 >= 0.0) || !std::isfinite(eps2)) return fail(ctx, NB_ERR_ARG, "eps2 must be finite and >= 0");
+    if (n != ctx->n) {
+        st = alloc_system(ctx, n);
+        if (st != NB_OK) return st;
+    } else {
+        CK(cudaMemsetAsync(ctx->a, 0, 3 * ctx->n_pad * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(ctx->k, 0, 3 * ctx->n_pad * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(ctx->t, 0, ctx->n_pad * sizeof(double), ctx->stream));
+    }
+    ctx->eps2 = eps2;
+    if (ctx->run_exec) {   // eps2 is baked into the captured launches
+        cudaGraphExecDestroy(ctx->run_exec);
+        ctx->run_exec = nullptr;
+    }
+    const int64_t np = ctx->n_pad;
+    CK(cudaMemcpyAsync(ctx->m, m, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(launch_aos_to_soa(x, ctx->x, n, np, ctx->stream));
+    CK(launch_aos_to_soa(v, ctx->v, n, np, ctx->stream));
+    return init_forces(ctx);
+}
+
+nb_status nb_next_block(nb_ctx *ctx, double *t_next, int64_t *s)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    StepArgs A = step_args(ctx);
+    CK(launch_select(A, 0, false, ctx->stream));
+    double tn;
+    int64_t ss;
+    CK(cudaMemcpyAsync(&tn, ctx->t_next, sizeof tn, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ss, ctx->s, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream));
+    st = sync_status(ctx);
+    if (st != NB_OK) return st;
+    ctx->block_s = ss;
+    ctx->forces_pending = false;
+    if (t_next) *t_next = tn;
+    if (s) *s = ss;
+    return NB_OK;
+}
+
+nb_status nb_get_active(nb_ctx *ctx, int32_t *idx)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (ctx->block_s < 0) return fail(ctx, NB_ERR_STATE, "no active list (call nb_next_block)");
+    if (!idx) return fail(ctx, NB_ERR_ARG, "null idx");
+    if (ctx->block_s > 0)
+        CK(cudaMemcpyAsync(idx, ctx->idx, ctx->block_s * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
+}
+
+nb_status nb_predict(nb_ctx *ctx, double t)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!std::isfinite(t)) return fail(ctx, NB_ERR_ARG, "t must be finite");
+    CK(launch_predict(step_args(ctx), false, t, ctx->stream));
+    return NB_OK;
+}
+
+nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    const int64_t n = ctx->n;
+    // stage holds 3n doubles: positions first, then velocities through out_a
+    StepArgs A = step_args(ctx);
+    CK(launch_records_to_aos(A, xp ? ctx->stage : nullptr, vp ? ctx->out_a : nullptr, ctx->stream));
+    if (xp) CK(cudaMemcpyAsync(xp, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (vp) CK(cudaMemcpyAsync(vp, ctx->out_a, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
+}
+
+static nb_status force_common(nb_ctx *ctx, int64_t s, double *a_dev, double *k_dev, double *phi_dev)
+{
+    CK(launch_force_ctx(ctx));
+    CK(launch_reduce_out(ctx->part, ctx->split_used, nullptr, s, a_dev, k_dev, phi_dev, ctx->status,
+                         ctx->stream));
+    ctx->forces_pending = true;
+    ctx->block_s = s;
+    return NB_OK;
+}
+
+nb_status nb_force_jerk(nb_ctx *ctx, const int32_t *idx, int64_t s, double *a, double *k, double *phi)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
+    if (s == 0) return NB_OK;
+    if (idx) {
+        for (int64_t q = 0; q < s; ++q) {
+            if (idx[q] < 0 || idx[q] >= ctx->n) return fail(ctx, NB_ERR_ARG, "idx[%lld] out of range", (long long)q);
+            if (q > 0 && idx[q] <= idx[q - 1]) return fail(ctx, NB_ERR_ARG, "idx not strictly ascending");
+        }
+        CK(cudaMemcpyAsync(ctx->idx, idx, s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->s, &s, sizeof s, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));   // idx, s are host stack/caller memory
+    } else if (s != ctx->block_s) {
+        return fail(ctx, NB_ERR_ARG, "s does not match the last nb_next_block");
+    }
+    st = force_common(ctx, s, ctx->out_a, ctx->out_k, ctx->out_phi);
+    if (st != NB_OK) return st;
+    if (a) CK(cudaMemcpyAsync(a, ctx->out_a, 3 * s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (k) CK(cudaMemcpyAsync(k, ctx->out_k, 3 * s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, ctx->out_phi, s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
+}
+
+nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, double *a, double *k, double *phi)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
+    if (s == 0) return NB_OK;
+    if (!idx_dev) return fail(ctx, NB_ERR_ARG, "null idx_dev");
+    CK(cudaMemcpyAsync(ctx->idx, idx_dev, s * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->s, &s, sizeof s, cudaMemcpyHostToDevice, ctx->stream));
+    return force_common(ctx, s, a, k, phi);
+}
+
+nb_status nb_correct(nb_ctx *ctx, double t_block)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!ctx->forces_pending) return fail(ctx, NB_ERR_STATE, "no forces pending (call nb_force_jerk)");
+    CK(cudaMemcpyAsync(ctx->t_next, &t_block, sizeof t_block, cudaMemcpyHostToDevice, ctx->stream));
+    StepArgs A = step_args(ctx);
+    CK(launch_check_due(A, t_block, ctx->stream));
+    st = sync_status(ctx);
+    if (st != NB_OK) return st;
+    CK(launch_correct(A, true, ctx->stream));
+    ctx->forces_pending = false;
+    return sync_status(ctx);
+}
+
+nb_status nb_step(nb_ctx *ctx)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    StepArgs A = step_args(ctx);
+    CK(launch_select(A, 0, false, ctx->stream));
+    CK(launch_predict(A, true, 0.0, ctx->stream));
+    CK(launch_force_ctx(ctx));
+    CK(launch_correct(A, false, ctx->stream));
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    return sync_status(ctx);
+}
+
+nb_status nb_run(nb_ctx *ctx, double t_end)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!std::isfinite(t_end)) return fail(ctx, NB_ERR_ARG, "t_end must be finite");
+    st = build_run_graph(ctx);
+    if (st != NB_OK) return st;
+    st = set_t_end(ctx, t_end);
+    if (st != NB_OK) return st;
+    {
+        // bound this call's device-side loop: at most kMaxRunSteps block steps
+        int64_t done = 0;
+        CK(cudaMemcpyAsync(&done, ctx->counters, sizeof done, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int64_t cap = done + kMaxRunSteps;
+        CK(cudaMemcpyAsync(ctx->counters + 2, &cap, sizeof cap, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (ctx->inject_pending) {   // the hook applies to plain launches; run one step that way
+        st = nb_step(ctx);
+        if (st != NB_OK) return st;
+    }
+    CK(cudaGraphLaunch(ctx->run_exec, ctx->stream));
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    return sync_status(ctx);
+}
+
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!std::isfinite(t_end)) return fail(ctx, NB_ERR_ARG, "t_end must be finite");
+    StepArgs A = step_args(ctx);
+    int64_t nl = 0;
+    double total = 0.0;
+    if (ctx->ev.size() < 2) {
+        ctx->ev.assign(2, nullptr);
+        CK(cudaEventCreate(&ctx->ev[0]));
+        CK(cudaEventCreate(&ctx->ev[1]));
+    }
+    for (;;) {
+        CK(launch_select(A, 0, false, ctx->stream));
+        double tn;
+        int64_t ss;
+        CK(cudaMemcpyAsync(&tn, ctx->t_next, sizeof tn, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&ss, ctx->s, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!(tn <= t_end) || ss <= 0) break;
+        CK(launch_predict(A, true, 0.0, ctx->stream));
+        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+        CK(launch_force_ctx(ctx));
+        CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+        CK(launch_correct(A, false, ctx->stream));
+        int32_t stw = 0;
+        CK(cudaMemcpyAsync(&stw, ctx->status, sizeof stw, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        total += ms;
+        ++nl;
+        if (stw) break;
+    }
+    if (force_ms) *force_ms = total;
+    if (launches) *launches = nl;
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    return sync_status(ctx);
+}
+
+nb_status nb_energy(nb_ctx *ctx, double *E, double *K, double *W)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    CK(launch_energy(step_args(ctx), ctx->en_scratch, ctx->en_ctas, ctx->en_out, ctx->stream));
+    double kw[2];
+    CK(cudaMemcpyAsync(kw, ctx->en_out, sizeof kw, cudaMemcpyDeviceToHost, ctx->stream));
+    st = sync_status(ctx);
+    if (st != NB_OK) return st;
+    if (K) *K = kw[0];
+    if (W) *W = kw[1];
+    if (E) *E = kw[0] + kw[1];
+    return NB_OK;
+}
+
+nb_status nb_get_state(nb_ctx *ctx, nb_state_view *view)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!view || view->n != ctx->n) return fail(ctx, NB_ERR_ARG, "state view size mismatch");
+    const int64_t n = ctx->n, np = ctx->n_pad;
+    auto vec = [&](double *src, double *dst) -> nb_status {
+        if (!dst) return NB_OK;
+        CK(launch_soa_to_aos(src, ctx->stage, n, np, ctx->stream));
+        CK(cudaMemcpyAsync(dst, ctx->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return NB_OK;
+    };
+    if (view->m) CK(cudaMemcpyAsync(view->m, ctx->m, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (view->t) CK(cudaMemcpyAsync(view->t, ctx->t, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (view->dt) CK(cudaMemcpyAsync(view->dt, ctx->dt, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = vec(ctx->x, view->x)) != NB_OK) return st;
+    if ((st = vec(ctx->v, view->v)) != NB_OK) return st;
+    if ((st = vec(ctx->a, view->a)) != NB_OK) return st;
+    if ((st = vec(ctx->k, view->k)) != NB_OK) return st;
+    return sync_status(ctx);
+}
+
+nb_status nb_set_state(nb_ctx *ctx, const nb_state_view *view)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!view || view->n != ctx->n) return fail(ctx, NB_ERR_ARG, "state view size mismatch");
+    if (!view->m || !view->x || !view->v || !view->a || !view->k || !view->t || !view->dt)
+        return fail(ctx, NB_ERR_ARG, "set_state needs every array");
+    const int64_t n = ctx->n, np = ctx->n_pad;
+    CK(cudaStreamSynchronize(ctx->stream));
+    auto vec = [&](const double *src, double *dst) -> nb_status {
+        CK(cudaMemcpyAsync(ctx->stage, src, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(launch_aos_to_soa(ctx->stage, dst, n, np, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return NB_OK;
+    };
+    CK(cudaMemcpyAsync(ctx->m, view->m, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->t, view->t, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->dt, view->dt, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if ((st = vec(view->x, ctx->x)) != NB_OK) return st;
+    if ((st = vec(view->v, ctx->v)) != NB_OK) return st;
+    if ((st = vec(view->a, ctx->a)) != NB_OK) return st;
+    if ((st = vec(view->k, ctx->k)) != NB_OK) return st;
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    return sync_status(ctx);
+}
+
+nb_status nb_stats(nb_ctx *ctx, nb_counters *out)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (!out) return fail(ctx, NB_ERR_ARG, "null counters");
+    int64_t c[2];
+    double inter;
+    CK(cudaMemcpyAsync(c, ctx->counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&inter, ctx->interactions, sizeof inter, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> t(ctx->n);
+    CK(cudaMemcpyAsync(t.data(), ctx->t, ctx->n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->block_steps = c[0];
+    out->particle_steps = c[1];
+    out->interactions = inter;
+    out->t_now = *std::max_element(t.begin(), t.end());
+    return NB_OK;
+}
+
+nb_status nb_sync(nb_ctx *ctx)
+{
+    nb_status st = check_ctx(ctx, false);
+    if (st != NB_OK) return st;
+    return sync_status(ctx);
+}
+
+int32_t nb_num_variants(const nb_ctx *ctx)
+{
+    if (!ctx) return 0;
+    return ctx->cfg.precision == NB_PREC_FP64 ? kF64Variants : kMixedVariants;
+}
+
+const char *nb_variant_name(const nb_ctx *ctx, int32_t v)
+{
+    if (!ctx || v < 0 || v >= nb_num_variants(ctx)) return "";
+    return ctx->cfg.precision == NB_PREC_FP64 ? f64_variant_name(v) : mixed_variant_name(v);
+}
+
+nb_status nb_set_tuning(nb_ctx *ctx, int32_t bucket, int32_t variant, int32_t split)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (bucket < 0 || bucket >= kBuckets) return fail(ctx, NB_ERR_ARG, "bucket out of range");
+    if (variant >= nb_num_variants(ctx)) return fail(ctx, NB_ERR_ARG, "variant out of range");
+    if (variant < 0) {
+        const int occ = ctx->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
+        int64_t s = std::min<int64_t>(int64_t(1) << bucket, ctx->n);
+        int vv, SS;
+        default_tuning(ctx->cfg.precision, ctx->n, s, ctx->num_sms, occ, &vv, &SS);
+        variant = vv;
+        split = SS;
+    }
+    if (split < 1) return fail(ctx, NB_ERR_ARG, "split must be >= 1");
+    ctx->tune.variant[bucket] = variant;
+    ctx->tune.split[bucket] = split;
+    return upload_tuning(ctx);
+}
+
+nb_status nb_get_tuning(nb_ctx *ctx, int32_t *variant, int32_t *split)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (variant) std::memcpy(variant, ctx->tune.variant, sizeof ctx->tune.variant);
+    if (split) std::memcpy(split, ctx->tune.split, sizeof ctx->tune.split);
+    return NB_OK;
+}
+
+// Autotuner: for each bucket (s = 1, 2, 4, ..., n) time every variant at a few
+// split factors around its default on the current predicted records, with the
+// active list 0..s-1, and keep the fastest (median of 3 launches).
+nb_status nb_autotune(nb_ctx *ctx)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    const int nv = nb_num_variants(ctx);
+    const int occ = ctx->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(launch_fill_iota(ctx->idx, ctx->n, ctx->stream));
+    int last_b = 0;
+    while ((int64_t(1) << last_b) < ctx->n && last_b < kBuckets - 1) ++last_b;
+    for (int b = 0; b <= last_b; ++b) {
+        const int64_t s = std::min<int64_t>(int64_t(1) << b, ctx->n);
+        CK(cudaMemcpyAsync(ctx->s, &s, sizeof s, cudaMemcpyHostToDevice, ctx->stream));
+        float best = 1e30f;
+        int bv = ctx->tune.variant[b], bs = ctx->tune.split[b];
+        for (int v = 0; v < nv; ++v) {
+            const int64_t I = ctx->cfg.precision == NB_PREC_FP64 ? f64_variant_I(v) : mixed_variant_I(v);
+            if (I > 4 * s && v > 0) continue;   // i-blocks mostly empty
+            const int64_t nib = (s + I - 1) / I;
+            int64_t S0 = std::max<int64_t>(1, (2 * (int64_t)ctx->num_sms * occ + nib - 1) / nib);
+            S0 = std::min<int64_t>(S0, ctx->n_tiles);
+            int64_t cands[4] = {std::max<int64_t>(1, S0 / 4), std::max<int64_t>(1, S0 / 2), S0,
+                                std::min<int64_t>(ctx->n_tiles, 2 * S0)};
+            for (int64_t S : cands) {
+                if (S * s * kPartStride > ctx->part_cap) continue;
+                ForceArgs F = force_args(ctx, v, (int)S);
+                float t3[3];
+                CK(launch_force(ctx, F));   // warm
+                for (int r = 0; r < 3; ++r) {
+                    CK(cudaEventRecord(e0, ctx->stream));
+                    CK(launch_force(ctx, F));
+                    CK(cudaEventRecord(e1, ctx->stream));
+                    CK(cudaEventSynchronize(e1));
+                    CK(cudaEventElapsedTime(&t3[r], e0, e1));
+                }
+                std::sort(t3, t3 + 3);
+                if (t3[1] < best) {
+                    best = t3[1];
+                    bv = v;
+                    bs = (int)S;
+                }
+            }
+        }
+        ctx->tune.variant[b] = bv;
+        ctx->tune.split[b] = bs;
+    }
+    for (int b = last_b + 1; b < kBuckets; ++b) {
+        ctx->tune.variant[b] = ctx->tune.variant[last_b];
+        ctx->tune.split[b] = ctx->tune.split[last_b];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned = true;
+    st = upload_tuning(ctx);
+    if (st != NB_OK) return st;
+    ctx->block_s = -1;
+    ctx->forces_pending = false;
+    return sync_status(ctx);
+}
+
+// Ensemble entry points: see nb_ensemble.cu.
+
+}  // extern "C"

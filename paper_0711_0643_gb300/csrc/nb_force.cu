@@ -1,0 +1,690 @@
+// Force + jerk + potential of the active block against all N predicted
+// particles: Eq. (Force) of Sect. 2.1 with Plummer softening, its exact time
+// derivative, and the softened potential.
+//
+// The paper splits the j-sum over processors and adds the partial forces with
+// MPI_Allreduce (Sect. 3). Here the split is on one chip:
+//   * a work item = (i-block, j-split); every CTA of a persistent grid loops
+//     over work items derived on the device from the active count s, so the
+//     launch needs no host round trip and can live inside a CUDA graph;
+//   * j-records stream through shared memory in tiles of kJT records, copied
+//     by the TMA bulk engine (cp.async.bulk + mbarrier, kStages in flight);
+//   * each thread holds R i-particles in registers and sweeps the tile with
+//     TJ threads sharing each i (TJ > 1 splits j inside the CTA when s is small);
+//   * partials are reduced in FP64 in a fixed order (lane shuffles, then the
+//     split index), so results are bitwise reproducible run to run.
+//
+// Mixed precision: positions arrive as double-single (hi, lo) pairs so that
+// r = x_j - x_i keeps ~46 bits even for close pairs; the pair arithmetic is
+// FP32 with one MUFU reciprocal square root; per-thread FP32 partial sums over
+// at most kFoldPairs pairs are folded into (hi, lo) two-sum accumulators.
+#include "nb_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kFoldPairs = 64;     // FP32 terms per partial before a two-sum fold
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion counted on the mbarrier (TMA).
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false if the spin limit expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_t limit)
+{
+    for (int it = 0; it < 64; ++it)
+        if (mbar_test(bar, parity)) return true;
+    for (int64_t it = 64; it < limit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// ---------------------------------------------------------- pair kernels
+
+struct IPart {
+    float xh, yh, zh, xl, yl, zl, vx, vy, vz;
+};
+
+struct Acc7 {
+    float ax, ay, az, kx, ky, kz, ph;
+};
+
+__device__ __forceinline__ void zero(Acc7 &q)
+{
+    q.ax = q.ay = q.az = q.kx = q.ky = q.kz = q.ph = 0.f;
+}
+
+__device__ __forceinline__ IPart load_ipart(const JRecs &J, int32_t i)
+{
+    float4 h = J.hi[i], l = J.lo[i], w = J.vel[i];
+    return IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z};
+}
+
+// One i-j interaction. r = x_j - x_i in double-single, w = v_j - v_i,
+// r2 = |r|^2 + eps^2, q = r2^{-1/2}, mu = m_j q^3, al = 3 (r.w) / r2:
+//   a += mu r,  k += mu (w - al r),  phi -= m_j q.
+// MASK zeroes the term when j == i (self-exclusion by index).
+template <bool MASK>
+__device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &w, const IPart &I,
+                                           float eps2, Acc7 &A, bool self)
+{
+    float dx = (h.x - I.xh) + (l.x - I.xl);
+    float dy = (h.y - I.yh) + (l.y - I.yl);
+    float dz = (h.z - I.zh) + (l.z - I.zl);
+    float wx = w.x - I.vx, wy = w.y - I.vy, wz = w.z - I.vz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    float rw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    float q = rsqrtf(r2);
+    if (MASK) q = self ? 0.f : q;
+    float q2 = q * q;
+    float mq = h.w * q;
+    float mu = mq * q2;
+    float al = 3.f * rw * q2;
+    A.ph -= mq;
+    A.ax = fmaf(mu, dx, A.ax);
+    A.ay = fmaf(mu, dy, A.ay);
+    A.az = fmaf(mu, dz, A.az);
+    A.kx = fmaf(mu, fmaf(-al, dx, wx), A.kx);
+    A.ky = fmaf(mu, fmaf(-al, dy, wy), A.ky);
+    A.kz = fmaf(mu, fmaf(-al, dz, wz), A.kz);
+}
+
+// (hi, lo) += p exactly up to the rounding of lo (Knuth's two-sum), p = 0 after.
+__device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float &p)
+{
+    float s = hi + p;
+    float bp = s - hi;
+    float e = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += e;
+    p = 0.f;
+}
+
+__device__ __forceinline__ void fold(Acc7 &hi, Acc7 &lo, Acc7 &p)
+{
+    two_sum_fold(hi.ax, lo.ax, p.ax);
+    two_sum_fold(hi.ay, lo.ay, p.ay);
+    two_sum_fold(hi.az, lo.az, p.az);
+    two_sum_fold(hi.kx, lo.kx, p.kx);
+    two_sum_fold(hi.ky, lo.ky, p.ky);
+    two_sum_fold(hi.kz, lo.kz, p.kz);
+    two_sum_fold(hi.ph, lo.ph, p.ph);
+}
+
+__device__ __forceinline__ void to_double(const Acc7 &hi, const Acc7 &lo, double *d)
+{
+    d[0] = (double)hi.ax + (double)lo.ax;
+    d[1] = (double)hi.ay + (double)lo.ay;
+    d[2] = (double)hi.az + (double)lo.az;
+    d[3] = (double)hi.kx + (double)lo.kx;
+    d[4] = (double)hi.ky + (double)lo.ky;
+    d[5] = (double)hi.kz + (double)lo.kz;
+    d[6] = (double)hi.ph + (double)lo.ph;
+}
+
+// ------------------------------------------------------------ shared memory
+
+constexpr int kMaxRC = 2 * 7;   // R * components, largest R over variants
+
+struct __align__(128) Smem {
+    float4 hi[kStages][kJT];
+    float4 lo[kStages][kJT];
+    float4 vel[kStages][kJT];
+    double red[kThreads / 32][kMaxRC];
+    uint64_t bar[kStages];
+    uint64_t inject_bar;
+    int abort;
+};
+
+__device__ __forceinline__ int bucket_of(int64_t s)
+{
+    // bucket b holds s in (2^(b-1), 2^b]; s = 1 -> 0
+    int b = 0;
+    while ((int64_t(1) << b) < s && b < kBuckets - 1) ++b;
+    return b;
+}
+
+// Split factor clamp shared by both precisions.
+__device__ __forceinline__ int clamp_split(int S, int64_t n_tiles, int64_t s, int64_t cap)
+{
+    if (S < 1) S = 1;
+    if (S > n_tiles) S = (int)n_tiles;
+    int64_t lim = cap / (s * kPartStride);
+    if (lim < 1) lim = 1;
+    if (S > lim) S = (int)lim;
+    return S;
+}
+
+__device__ __forceinline__ void write_part(const ForceArgs &A, int64_t ii, int by, int S, const double *d)
+{
+    double *dst = A.part + (ii * S + by) * kPartStride;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) dst[c] = d[c];
+    dst[7] = 0.0;
+}
+
+// ------------------------------------------------------- streamed variant
+// TI = 1: all threads share the same R i-particles; each thread walks its own
+// j's straight from global memory (coalesced float4 loads), so no shared
+// staging is needed. For small active blocks.
+template <int R>
+__device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    IPart ip[R];
+    int32_t gi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int64_t ii = bx * R + r;
+        gi[r] = A.idx[ii < s ? ii : s - 1];
+        ip[r] = load_ipart(A.j, gi[r]);
+    }
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t j0 = t0 * kJT, j1 = t1 * kJT;
+    Acc7 p[R], hi[R], lo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
+    int cnt = 0;
+    for (int64_t j = j0 + tid; j < j1; j += kThreads) {
+        float4 h = __ldg(&A.j.hi[j]), l = __ldg(&A.j.lo[j]), w = __ldg(&A.j.vel[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) pair_mixed<true>(h, l, w, ip[r], A.eps2f, p[r], j == gi[r]);
+        if (++cnt == kFoldPairs) {
+            cnt = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+    // fixed-order reduction: lanes (xor tree), then warps in ascending order
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double d[7];
+        to_double(hi[r], lo[r], d);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            double x = d[c];
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) sm->red[warp][r * 7 + c] = x;
+        }
+    }
+    __syncthreads();
+    if (tid < R * 7) {
+        double x = 0.0;
+#pragma unroll
+        for (int wv = 0; wv < kThreads / 32; ++wv) x += sm->red[wv][tid];
+        int r = tid / 7, c = tid % 7;
+        int64_t ii = bx * R + r;
+        if (ii < s) {
+            A.part[(ii * S + by) * kPartStride + c] = x;
+            if (c == 0) A.part[(ii * S + by) * kPartStride + 7] = 0.0;
+        }
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------- tiled variant
+// TI = kThreads / TJ thread groups, each holding R i-particles; the TJ threads
+// of a group take interleaved j's of each shared-memory tile.
+template <int R, int TJ, bool MASK>
+__device__ __forceinline__ void sweep_tile(const Smem *sm, int st, int tj, int64_t j0, const IPart *ip,
+                                           const int32_t *gi, float eps2, Acc7 *p, Acc7 *hi, Acc7 *lo)
+{
+    constexpr int JPT = kJT / TJ;                          // j's per thread per tile
+    constexpr int CH = JPT < kFoldPairs ? JPT : kFoldPairs;
+    const float4 *H = sm->hi[st];
+    const float4 *L = sm->lo[st];
+    const float4 *V = sm->vel[st];
+#pragma unroll 1
+    for (int c0 = 0; c0 < JPT; c0 += CH) {
+#pragma unroll 4
+        for (int q = 0; q < CH; ++q) {
+            const int jj = tj + (c0 + q) * TJ;
+            float4 h = H[jj], l = L[jj], w = V[jj];
+            const int64_t jg = j0 + jj;
+#pragma unroll
+            for (int r = 0; r < R; ++r) pair_mixed<MASK>(h, l, w, ip[r], eps2, p[r], MASK && jg == gi[r]);
+        }
+        if (JPT >= kFoldPairs) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+        }
+    }
+}
+
+__device__ __forceinline__ void issue_tile(const ForceArgs &A, Smem *sm, int64_t tile, int st)
+{
+    constexpr uint32_t bytes = kJT * sizeof(float4);
+    mbar_arrive_expect_tx(&sm->bar[st], 3 * bytes);
+    const int64_t j0 = tile * kJT;
+    bulk_g2s(sm->hi[st], A.j.hi + j0, bytes, &sm->bar[st]);
+    bulk_g2s(sm->lo[st], A.j.lo + j0, bytes, &sm->bar[st]);
+    bulk_g2s(sm->vel[st], A.j.vel + j0, bytes, &sm->bar[st]);
+}
+
+template <int R, int TJ>
+__device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm, uint32_t &git)
+{
+    constexpr int TI = kThreads / TJ;
+    constexpr int I = TI * R;
+    constexpr int JPT = kJT / TJ;
+    constexpr int kFoldTiles = JPT >= kFoldPairs ? 0 : kFoldPairs / JPT;   // 0: folded inside the sweep
+    static_assert(TJ <= 32 && (32 % TJ) == 0, "TJ must divide a warp");
+    const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+
+    IPart ip[R];
+    int32_t gi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int64_t ii = bx * I + (int64_t)r * TI + ti;
+        gi[r] = A.idx[ii < s ? ii : s - 1];
+        ip[r] = load_ipart(A.j, gi[r]);
+    }
+    // index range of this i-block (the active list ascends), for self-exclusion
+    const int64_t ib0 = bx * I;
+    const int64_t ib1 = (ib0 + I < s ? ib0 + I : s) - 1;
+    const int64_t imin = A.idx[ib0], imax = A.idx[ib1];
+
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+
+    Acc7 p[R], hi[R], lo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
+
+    if (tid == 0) {
+        const int64_t pro = nt < kStages - 1 ? nt : kStages - 1;
+        for (int64_t q = 0; q < pro; ++q) issue_tile(A, sm, t0 + q, (int)((git + q) % kStages));
+    }
+    int fc = 0;
+    for (int64_t q = 0; q < nt; ++q) {
+        const uint32_t g = git + (uint32_t)q;
+        const int st = (int)(g % kStages);
+        if (tid == 0 && q + kStages - 1 < nt)
+            issue_tile(A, sm, t0 + q + kStages - 1, (int)((g + kStages - 1) % kStages));
+        if (!mbar_wait(&sm->bar[st], (g / kStages) & 1u, A.spin_limit)) sm->abort = 1;
+        const int64_t j0 = (t0 + q) * kJT;
+        if (j0 <= imax && j0 + kJT - 1 >= imin)
+            sweep_tile<R, TJ, true>(sm, st, tj, j0, ip, gi, A.eps2f, p, hi, lo);
+        else
+            sweep_tile<R, TJ, false>(sm, st, tj, j0, ip, gi, A.eps2f, p, hi, lo);
+        if (kFoldTiles > 0 && ++fc == kFoldTiles) {
+            fc = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+        }
+        __syncthreads();
+        if (sm->abort) {
+            // a wait ran out: drain what this CTA still has in flight (bounded), then stop
+            if (tid == 0) {
+                for (int64_t qq = q + 1; qq < nt && qq < q + kStages; ++qq) {
+                    const uint32_t gg = git + (uint32_t)qq;
+                    (void)mbar_wait(&sm->bar[gg % kStages], (gg / kStages) & 1u, A.spin_limit);
+                }
+            }
+            git += (uint32_t)nt;
+            return;
+        }
+    }
+    git += (uint32_t)nt;
+#pragma unroll
+    for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double d[7];
+        to_double(hi[r], lo[r], d);
+        if (TJ > 1) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+#pragma unroll
+                for (int off = TJ / 2; off >= 1; off >>= 1) d[c] += __shfl_xor_sync(0xffffffffu, d[c], off);
+        }
+        const int64_t ii = bx * I + (int64_t)r * TI + ti;
+        if (tj == 0 && ii < s) write_part(A, ii, by, S, d);
+    }
+}
+
+// -------------------------------------------------------------- variants
+
+// 0: stream R=1 (I=1)      1: stream R=2 (I=2)      2: tile R=2 TJ=32 (I=16)
+// 3: tile R=2 TJ=8 (I=64)  4: tile R=2 TJ=1 (I=512)
+__host__ __device__ __forceinline__ int mixed_I(int v)
+{
+    switch (v) {
+    case 0: return 1;
+    case 1: return 2;
+    case 2: return 16;
+    case 3: return 64;
+    default: return 512;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem *sm = reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&sm->bar[st], 1);
+        mbar_init(&sm->inject_bar, 1);
+        fence_mbar_init();
+        sm->abort = 0;
+    }
+    __syncthreads();
+    const int64_t s = *A.s;
+    if (s <= 0) return;
+    if (A.inject) {
+        // Test hook: wait on a barrier that no one arrives on; the spin limit must
+        // expire and the kernel must report it. No copy is in flight here.
+        if (!mbar_wait(&sm->inject_bar, 0, A.spin_limit) && tid == 0) atomicOr(A.status, kStTimeout);
+        return;
+    }
+    int variant, S;
+    if (A.force_variant >= 0) {
+        variant = A.force_variant;
+        S = A.force_split;
+    } else {
+        const int b = bucket_of(s);
+        variant = A.tune->variant[b];
+        S = A.tune->split[b];
+    }
+    if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
+    S = clamp_split(S, A.n_tiles, s, A.part_cap);
+    if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
+    const int64_t I = mixed_I(variant);
+    const int64_t nib = (s + I - 1) / I;
+    const int64_t W = nib * S;
+    uint32_t git = 0;
+    for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
+        const int64_t bx = w / S;
+        const int by = (int)(w % S);
+        switch (variant) {
+        case 0: work_stream<1>(A, s, bx, by, S, sm); break;
+        case 1: work_stream<2>(A, s, bx, by, S, sm); break;
+        case 2: work_tile<2, 32>(A, s, bx, by, S, sm, git); break;
+        case 3: work_tile<2, 8>(A, s, bx, by, S, sm, git); break;
+        default: work_tile<2, 1>(A, s, bx, by, S, sm, git); break;
+        }
+        if (sm->abort) {
+            if (tid == 0) atomicOr(A.status, kStTimeout);
+            return;
+        }
+    }
+}
+
+// ------------------------------------------------------------ FP64 kernels
+// The plain FP64 path: same decomposition, double arithmetic throughout and
+// j-data read through the read-only cache (all lanes of a warp read the same
+// j in the i-loop variant, one broadcast transaction).
+
+__device__ __forceinline__ void pair_f64(double xj, double yj, double zj, double mj, double vxj, double vyj,
+                                         double vzj, const double *xi, double eps2, double *acc, bool self)
+{
+    double dx = xj - xi[0], dy = yj - xi[1], dz = zj - xi[2];
+    double wx = vxj - xi[3], wy = vyj - xi[4], wz = vzj - xi[5];
+    double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    double rw = fma(dx, wx, fma(dy, wy, dz * wz));
+    double q = self ? 0.0 : rsqrt(r2);
+    double q2 = q * q;
+    double mq = mj * q;
+    double mu = mq * q2;
+    double al = 3.0 * rw * q2;
+    acc[6] -= mq;
+    acc[0] = fma(mu, dx, acc[0]);
+    acc[1] = fma(mu, dy, acc[1]);
+    acc[2] = fma(mu, dz, acc[2]);
+    acc[3] = fma(mu, fma(-al, dx, wx), acc[3]);
+    acc[4] = fma(mu, fma(-al, dy, wy), acc[4]);
+    acc[5] = fma(mu, fma(-al, dz, wz), acc[5]);
+}
+
+__device__ __forceinline__ void load_i64(const ForceArgs &A, int32_t i, double *xi)
+{
+    const int64_t np = A.n_tiles * kJT;
+    xi[0] = A.xp[i]; xi[1] = A.xp[np + i]; xi[2] = A.xp[2 * np + i];
+    xi[3] = A.vp[i]; xi[4] = A.vp[np + i]; xi[5] = A.vp[2 * np + i];
+}
+
+__device__ void work_f64_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, double (*red)[7])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t gi = A.idx[bx < s ? bx : s - 1];
+    double xi[6];
+    load_i64(A, gi, xi);
+    const int64_t np = A.n_tiles * kJT;
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t j = t0 * kJT + tid; j < t1 * kJT; j += kThreads)
+        pair_f64(__ldg(A.xp + j), __ldg(A.xp + np + j), __ldg(A.xp + 2 * np + j), __ldg(A.m + j),
+                 __ldg(A.vp + j), __ldg(A.vp + np + j), __ldg(A.vp + 2 * np + j), xi, A.eps2, acc, j == gi);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        double x = acc[c];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) red[warp][c] = x;
+    }
+    __syncthreads();
+    if (tid < 7) {
+        double x = 0.0;
+        for (int wv = 0; wv < kThreads / 32; ++wv) x += red[wv][tid];
+        if (bx < s) {
+            A.part[(bx * S + by) * kPartStride + tid] = x;
+            if (tid == 0) A.part[(bx * S + by) * kPartStride + 7] = 0.0;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void work_f64_iloop(const ForceArgs &A, int64_t s, int64_t bx, int by, int S)
+{
+    const int tid = threadIdx.x;
+    const int64_t ii = bx * kThreads + tid;
+    const int32_t gi = A.idx[ii < s ? ii : s - 1];
+    double xi[6];
+    load_i64(A, gi, xi);
+    const int64_t np = A.n_tiles * kJT;
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t j = t0 * kJT; j < t1 * kJT; ++j)
+        pair_f64(__ldg(A.xp + j), __ldg(A.xp + np + j), __ldg(A.xp + 2 * np + j), __ldg(A.m + j),
+                 __ldg(A.vp + j), __ldg(A.vp + np + j), __ldg(A.vp + 2 * np + j), xi, A.eps2, acc, j == gi);
+    if (ii < s) {
+        double *dst = A.part + (ii * S + by) * kPartStride;
+        for (int c = 0; c < 7; ++c) dst[c] = acc[c];
+        dst[7] = 0.0;
+    }
+}
+
+__host__ __device__ __forceinline__ int f64_I(int v) { return v == 0 ? 1 : kThreads; }
+
+__global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
+{
+    __shared__ double red[kThreads / 32][7];
+    __shared__ uint64_t inject_bar;
+    const int64_t s = *A.s;
+    if (s <= 0) return;
+    if (A.inject) {
+        if (threadIdx.x == 0) {
+            mbar_init(&inject_bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (!mbar_wait(&inject_bar, 0, A.spin_limit) && threadIdx.x == 0) atomicOr(A.status, kStTimeout);
+        return;
+    }
+    int variant, S;
+    if (A.force_variant >= 0) {
+        variant = A.force_variant;
+        S = A.force_split;
+    } else {
+        const int b = bucket_of(s);
+        variant = A.tune->variant[b];
+        S = A.tune->split[b];
+    }
+    if (variant < 0 || variant >= kF64Variants) variant = kF64Variants - 1;
+    S = clamp_split(S, A.n_tiles, s, A.part_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.split_used = S;
+    const int64_t I = f64_I(variant);
+    const int64_t W = ((s + I - 1) / I) * S;
+    for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
+        const int64_t bx = w / S;
+        const int by = (int)(w % S);
+        if (variant == 0)
+            work_f64_stream(A, s, bx, by, S, red);
+        else
+            work_f64_iloop(A, s, bx, by, S);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+int mixed_variant_I(int v) { return mixed_I(v); }
+
+const char *mixed_variant_name(int v)
+{
+    switch (v) {
+    case 0: return "stream R=1";
+    case 1: return "stream R=2";
+    case 2: return "tile R=2 TJ=32";
+    case 3: return "tile R=2 TJ=8";
+    case 4: return "tile R=2 TJ=1";
+    default: return "?";
+    }
+}
+
+int f64_variant_I(int v) { return f64_I(v); }
+
+const char *f64_variant_name(int v) { return v == 0 ? "f64 stream" : "f64 i-loop"; }
+
+size_t force_mixed_smem_bytes() { return sizeof(Smem); }
+
+static int g_mixed_occ = -1, g_f64_occ = -1;
+
+int force_mixed_ctas_per_sm()
+{
+    if (g_mixed_occ < 0) {
+        cudaFuncSetAttribute(force_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(Smem));
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_mixed_kernel, kThreads, sizeof(Smem)) !=
+                cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        g_mixed_occ = occ;
+    }
+    return g_mixed_occ;
+}
+
+int force_f64_ctas_per_sm()
+{
+    if (g_f64_occ < 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_f64_kernel, kThreads, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        g_f64_occ = occ;
+    }
+    return g_f64_occ;
+}
+
+cudaError_t launch_force_mixed(const ForceArgs &a, int grid, cudaStream_t st)
+{
+    (void)force_mixed_ctas_per_sm();   // sets the dynamic shared-memory attribute once
+    force_mixed_kernel<<<grid, kThreads, sizeof(Smem), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_f64(const ForceArgs &a, int grid, cudaStream_t st)
+{
+    force_f64_kernel<<<grid, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_per_sm, int *variant, int *split)
+{
+    const int64_t n_tiles = (n + kJT - 1) / kJT;
+    const int64_t resident = (int64_t)num_sms * ctas_per_sm;
+    int v;
+    if (precision == NB_PREC_FP64) {
+        v = s <= 64 ? 0 : 1;
+    } else if (s <= 1) {
+        v = 0;
+    } else if (s <= 8) {
+        v = 1;
+    } else if (s <= 128) {
+        v = 2;
+    } else if (s <= 2048) {
+        v = 3;
+    } else {
+        v = 4;
+    }
+    const int64_t I = precision == NB_PREC_FP64 ? f64_I(v) : mixed_I(v);
+    const int64_t nib = (s + I - 1) / I;
+    int64_t S = (2 * resident + nib - 1) / nib;
+    if (S < 1) S = 1;
+    if (S > n_tiles) S = n_tiles;
+    *variant = v;
+    *split = (int)S;
+}
+
+}  // namespace nb

@@ -1,0 +1,128 @@
+// Internal declarations shared by the translation units of libnbody.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+namespace nb {
+
+// ---------------------------------------------------------------- constants
+
+constexpr int kThreads = 256;        // threads per CTA of the force kernels
+constexpr int kJT = 256;             // j-records per shared-memory tile
+constexpr int kStages = 3;           // tiles in flight per CTA
+constexpr int kBuckets = 32;         // active-set size buckets (bucket b: s in (2^(b-1), 2^b])
+constexpr int kPartStride = 8;       // doubles per (i, split) partial: ax ay az kx ky kz phi pad
+
+// device status bits (accumulated with atomicOr, read at sync points)
+constexpr int kStNonfinite = 1;
+constexpr int kStUnderflow = 2;
+constexpr int kStTimeout = 4;
+constexpr int kStState = 8;
+constexpr int kStSteps = 16;         // block-step cap reached inside nb_run
+
+// ------------------------------------------------------------- force kernels
+
+// Mixed-precision j-record, 48 bytes: predicted position split into
+// hi = fl32(x) and lo = fl32(x - hi), velocity in FP32, mass in FP32.
+struct JRecs {
+    float4 *hi;   // (x_hi, y_hi, z_hi, m)
+    float4 *lo;   // (x_lo, y_lo, z_lo, 0)
+    float4 *vel;  // (vx, vy, vz, 0)
+};
+
+struct Tuning {
+    int32_t variant[kBuckets];
+    int32_t split[kBuckets];
+};
+
+// Parameters of one force evaluation (both precisions).
+struct ForceArgs {
+    int64_t n;            // particles
+    int64_t n_tiles;      // ceil(n / kJT); j arrays are padded to n_tiles * kJT
+    JRecs j;              // mixed records
+    const double *xp;     // FP64 predicted positions [3][n_pad]
+    const double *vp;     // FP64 predicted velocities [3][n_pad]
+    const double *m;      // masses [n_pad]
+    float eps2f;
+    double eps2;
+    const int32_t *idx;   // active list (ascending), length *s
+    const int64_t *s;     // active count (device)
+    double *part;         // partials [s][split][8]
+    int64_t part_cap;     // capacity of part in doubles
+    int32_t *split_used;  // written by the kernel: split factor of this launch
+    const Tuning *tune;   // device tuning table
+    int32_t force_variant;  // >= 0: ignore the table (autotuner, tests)
+    int32_t force_split;
+    int32_t *status;
+    int64_t spin_limit;
+    int32_t inject;       // test hook (see nb_config.inject)
+};
+
+// Variant catalogue. Mixed: 0..kMixedVariants-1; FP64: 0..kF64Variants-1.
+constexpr int kMixedVariants = 5;
+constexpr int kF64Variants = 2;
+int mixed_variant_I(int v);           // i-particles per work item
+const char *mixed_variant_name(int v);
+int f64_variant_I(int v);
+const char *f64_variant_name(int v);
+
+// Persistent launches: grid = fixed CTA count, work items derived from *s.
+cudaError_t launch_force_mixed(const ForceArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_force_f64(const ForceArgs &a, int grid, cudaStream_t st);
+int force_mixed_ctas_per_sm();
+int force_f64_ctas_per_sm();
+size_t force_mixed_smem_bytes();
+
+// Default tuning (variant, split) for an active count s.
+void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_per_sm, int *variant,
+                    int *split);
+
+// ------------------------------------------------------------ step kernels
+
+struct StepArgs {
+    int64_t n, n_pad;
+    double *m, *x, *v, *a, *k, *t, *dt;   // state, vectors [3][n_pad]
+    JRecs j;                              // mixed records (written by predict)
+    double *xp, *vp;                      // FP64 predicted records [3][n_pad]
+    int precision;
+    double eps2;
+    double eta, dt_max, dt_min;
+    int32_t *idx;                         // active list
+    int64_t *s;                           // active count
+    double *t_next;                       // block time
+    double *t_end;                        // nb_run target
+    const double *part;                   // force partials [s][split][8]
+    const int32_t *split_used;
+    int32_t *status;
+    int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps
+    double *interactions;                 // sum s*n
+    int32_t *chunk_cnt;                   // scratch for multi-CTA selection
+    double *chunk_min;
+    int32_t *done_ctr;
+    int select_ctas;
+};
+
+cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cudaStream_t st);
+// selection; with cond != 0 it also sets the while-node condition (t_next <= *t_end and no error)
+cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st);
+cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st);
+cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st);
+cudaError_t launch_reduce_out(const double *part, const int32_t *split_used, const int64_t *s,
+                              int64_t s_host, double *a, double *k, double *phi, int32_t *status,
+                              cudaStream_t st);
+cudaError_t launch_aos_to_soa(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
+cudaError_t launch_soa_to_aos(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
+cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_aos, cudaStream_t st);
+cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st);
+cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st);
+// energy: writes K, W to out[0], out[1] (fixed-order sums)
+cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, double *out,
+                          cudaStream_t st);
+cudaError_t launch_check_active(const int32_t *idx, int64_t s, int64_t n, int32_t *status,
+                                cudaStream_t st);
+cudaError_t launch_check_due(const StepArgs &a, double t_block, cudaStream_t st);
+
+}  // namespace nb

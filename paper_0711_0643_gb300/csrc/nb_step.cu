@@ -1,0 +1,552 @@
+// Per-block-step kernels around the force evaluation (Sect. 2.1 of the paper):
+// the Hermite predictor for all particles, block selection (smallest
+// t_i + dt_i), the Hermite corrector with the Aarseth time step quantised to
+// powers of two, the first steps, and the FP64 energy diagnostic.
+//
+// This file is compiled with -fmad=false: every FP64 expression rounds
+// operation by operation in the order written, so the predictor and the
+// corrector give the same bits as a CPU evaluation of the same formulas
+// without fused multiply-adds.
+#include <math_constants.h>
+
+#include "nb_internal.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kStepThreads = 256;
+constexpr int kSelThreads = 1024;
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+__device__ __forceinline__ double dot3(double ux, double uy, double uz, double wx, double wy, double wz)
+{
+    return ux * wx + uy * wy + uz * wz;
+}
+
+// largest power of two <= x for finite x > 0
+__device__ __forceinline__ double pow2_floor(double x)
+{
+    int e;
+    (void)frexp(x, &e);
+    return ldexp(1.0, e - 1);
+}
+
+// Power-of-two step rule: drop to the largest power of two below the candidate;
+// double (once) only at times commensurate with twice the old step and within
+// dt_max; otherwise keep. 0 means "below dt_min or no valid candidate".
+__device__ double quantise(double cand, double dt_old, double t_new, double dt_max, double dt_min)
+{
+    if (!(cand > 0.0)) return 0.0;
+    const double q = isinf(cand) ? CUDART_INF : pow2_floor(cand);
+    double dt;
+    const double dt2 = 2.0 * dt_old;
+    if (q < dt_old) {
+        dt = q;
+    } else if (q >= dt2 && dt2 <= dt_max) {
+        const double u = t_new / dt2;
+        dt = (u == floor(u)) ? dt2 : dt_old;
+    } else {
+        dt = dt_old;
+    }
+    if (dt > dt_max) dt = dt_max;
+    if (dt < dt_min) return 0.0;
+    return dt;
+}
+
+// Eq. (timestep): sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| + |a2p|^2)); den = 0 sets no limit.
+__device__ double aarseth(const double *an, const double *kn, const double *a2p, const double *a3, double eta)
+{
+    const double amag = sqrt(dot3(an[0], an[1], an[2], an[0], an[1], an[2]));
+    const double kmag = sqrt(dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]));
+    const double a2mag = sqrt(dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]));
+    const double a3mag = sqrt(dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]));
+    const double num = amag * a2mag + dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]);
+    const double den = kmag * a3mag + dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]);
+    if (den == 0.0) return CUDART_INF;
+    return sqrt(eta * num / den);
+}
+
+__device__ double initial_step(const double *a, const double *k, double eta, double dt_max, double dt_min)
+{
+    const double amag = sqrt(dot3(a[0], a[1], a[2], a[0], a[1], a[2]));
+    const double kmag = sqrt(dot3(k[0], k[1], k[2], k[0], k[1], k[2]));
+    const double cand = (kmag > 0.0) ? eta * amag / kmag : CUDART_INF;
+    if (!(cand > 0.0)) return 0.0;
+    double dt = isinf(cand) ? dt_max : pow2_floor(cand);
+    if (dt > dt_max) dt = dt_max;
+    if (dt < dt_min) return 0.0;
+    return dt;
+}
+
+// Predicted position/velocity of particle i at time tn (Hermite predictor).
+__device__ __forceinline__ void predict_one(const StepArgs &A, int64_t i, double tn, double *xp, double *vp)
+{
+    const int64_t np = A.n_pad;
+    const double d = tn - A.t[i];
+    const double d2 = d * d;
+    const double d3 = d2 * d;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int64_t q = c * np + i;
+        xp[c] = A.x[q] + A.v[q] * d + A.a[q] * d2 / 2.0 + A.k[q] * d3 / 6.0;
+        vp[c] = A.v[q] + A.a[q] * d + A.k[q] * d2 / 2.0;
+    }
+}
+
+// The far-away, massless record used to pad the j arrays to whole tiles.
+constexpr double kPadPos = 1e18;
+
+__global__ void predict_kernel(StepArgs A, int use_t_next, double t_host)
+{
+    const double tn = use_t_next ? *A.t_next : t_host;
+    const int64_t np = A.n_pad;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) {
+        double xp[3], vp[3];
+        predict_one(A, i, tn, xp, vp);
+        if (A.precision == NB_PREC_MIXED) {
+            float hx = (float)xp[0], hy = (float)xp[1], hz = (float)xp[2];
+            float lx = (float)(xp[0] - (double)hx);
+            float ly = (float)(xp[1] - (double)hy);
+            float lz = (float)(xp[2] - (double)hz);
+            A.j.hi[i] = make_float4(hx, hy, hz, (float)A.m[i]);
+            A.j.lo[i] = make_float4(lx, ly, lz, 0.f);
+            A.j.vel[i] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                A.xp[c * np + i] = xp[c];
+                A.vp[c * np + i] = vp[c];
+            }
+        }
+    }
+}
+
+__global__ void pad_kernel(StepArgs A)
+{
+    const int64_t np = A.n_pad;
+    for (int64_t i = A.n + gtid(); i < np; i += gstride()) {
+        A.j.hi[i] = make_float4((float)kPadPos, (float)kPadPos, (float)kPadPos, 0.f);
+        A.j.lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.j.vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.m[i] = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            A.xp[c * np + i] = kPadPos;
+            A.vp[c * np + i] = 0.0;
+            A.x[c * np + i] = kPadPos;
+            A.v[c * np + i] = 0.0;
+            A.a[c * np + i] = 0.0;
+            A.k[c * np + i] = 0.0;
+        }
+        A.t[i] = CUDART_INF;
+        A.dt[i] = CUDART_INF;
+    }
+}
+
+// ---------------------------------------------------------------- selection
+// One CTA: block minimum of t_i + dt_i, then an ordered compaction (each
+// thread owns a contiguous chunk; an exclusive scan of the chunk counts gives
+// every thread its output offset, so the list comes out ascending).
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGraphConditionalHandle cond,
+                                                             int set_cond)
+{
+    __shared__ double smin[kSelThreads / 32];
+    __shared__ int scnt[kSelThreads / 32];
+    __shared__ double s_tmin;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = A.n;
+    const int64_t chunk = (n + kSelThreads - 1) / kSelThreads;
+    const int64_t b0 = tid * chunk;
+    const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+    double m = CUDART_INF;
+    for (int64_t i = b0; i < b1; ++i) m = fmin(m, A.t[i] + A.dt[i]);
+    m = warp_min(m);
+    if (lane == 0) smin[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < kSelThreads / 32 ? smin[lane] : CUDART_INF;
+        x = warp_min(x);
+        if (lane == 0) s_tmin = x;
+    }
+    __syncthreads();
+    const double tmin = s_tmin;
+    int cnt = 0;
+    for (int64_t i = b0; i < b1; ++i) cnt += (A.t[i] + A.dt[i] == tmin);
+    // exclusive scan of cnt over the CTA
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) scnt[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < kSelThreads / 32 ? scnt[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, xi, off);
+            if (lane >= off) xi += y;
+        }
+        if (lane < kSelThreads / 32) scnt[lane] = xi - x;   // exclusive warp offsets
+    }
+    __syncthreads();
+    int pos = scnt[warp] + incl - cnt;
+    for (int64_t i = b0; i < b1; ++i)
+        if (A.t[i] + A.dt[i] == tmin) A.idx[pos++] = (int32_t)i;
+    if (tid == kSelThreads - 1) {
+        const int64_t s = (int64_t)pos;   // last thread's end offset = total
+        *A.s = s;
+        *A.t_next = tmin;
+        if (set_cond) {
+            const bool ok = (tmin <= *A.t_end) && s > 0 && (*A.status == 0);
+            bool more = ok && (A.counters[0] < A.counters[2]);
+            if (ok && !more) atomicOr(A.status, kStSteps);
+            cudaGraphSetConditional(cond, more ? 1u : 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- corrector
+
+__device__ __forceinline__ void sum_partials(const double *part, int64_t ii, int S, double *an, double *kn,
+                                             double *phi)
+{
+    const double *p = part + ii * (int64_t)S * kPartStride;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int sp = 0; sp < S; ++sp)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[c] += p[sp * kPartStride + c];
+    an[0] = acc[0]; an[1] = acc[1]; an[2] = acc[2];
+    kn[0] = acc[3]; kn[1] = acc[4]; kn[2] = acc[5];
+    if (phi) *phi = acc[6];
+}
+
+__global__ void correct_kernel(StepArgs A, int check_due)
+{
+    const int64_t s = *A.s;
+    const double tn = *A.t_next;
+    const int S = *A.split_used;
+    const int64_t np = A.n_pad;
+    int flags = 0;
+    for (int64_t ii = gtid(); ii < s; ii += gstride()) {
+        const int64_t i = A.idx[ii];
+        const double dt = A.dt[i];
+        if (check_due && A.t[i] + dt != tn) {
+            flags |= kStState;
+            continue;
+        }
+        double an[3], kn[3];
+        sum_partials(A.part, ii, S, an, kn, nullptr);
+        double xp[3], vp[3];
+        predict_one(A, i, tn, xp, vp);
+        // Hermite corrector, da = a_old - a_new
+        const double dt2 = dt * dt;
+        const double dt3 = dt2 * dt;
+        const double dt4 = dt3 * dt;
+        const double dt5 = dt4 * dt;
+        double x1[3], v1[3], a2[3], a3[3], a2p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double ao = A.a[c * np + i], ko = A.k[c * np + i];
+            const double da = ao - an[c];
+            a2[c] = -6.0 * da / dt2 - (4.0 * ko + 2.0 * kn[c]) / dt;
+            a3[c] = 12.0 * da / dt3 + 6.0 * (ko + kn[c]) / dt2;
+            x1[c] = xp[c] + a2[c] * dt4 / 24.0 + a3[c] * dt5 / 120.0;
+            v1[c] = vp[c] + a2[c] * dt3 / 6.0 + a3[c] * dt4 / 24.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a2p[c] = a2[c] + a3[c] * dt;
+        const double cand = aarseth(an, kn, a2p, a3, A.eta);
+        const double dt_new = quantise(cand, dt, tn, A.dt_max, A.dt_min);
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            finite = finite && isfinite(x1[c]) && isfinite(v1[c]) && isfinite(an[c]) && isfinite(kn[c]);
+        if (!finite) flags |= kStNonfinite;
+        if (dt_new == 0.0) flags |= kStUnderflow;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A.x[c * np + i] = x1[c];
+            A.v[c * np + i] = v1[c];
+            A.a[c * np + i] = an[c];
+            A.k[c * np + i] = kn[c];
+        }
+        A.t[i] = tn;
+        A.dt[i] = dt_new;
+    }
+    if (flags) atomicOr(A.status, flags);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
+        A.counters[0] += 1;
+        A.counters[1] += s;
+        *A.interactions += (double)s * (double)A.n;
+    }
+}
+
+// First steps after the initial full force pass.
+__global__ void init_steps_kernel(StepArgs A)
+{
+    const int S = *A.split_used;
+    const int64_t np = A.n_pad;
+    int flags = 0;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) {
+        double an[3], kn[3];
+        sum_partials(A.part, i, S, an, kn, nullptr);
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A.a[c * np + i] = an[c];
+            A.k[c * np + i] = kn[c];
+            finite = finite && isfinite(an[c]) && isfinite(kn[c]);
+        }
+        const double dt = initial_step(an, kn, A.eta, A.dt_max, A.dt_min);
+        if (!finite) flags |= kStNonfinite;
+        if (dt == 0.0) flags |= kStUnderflow;
+        A.t[i] = 0.0;
+        A.dt[i] = dt;
+    }
+    if (flags) atomicOr(A.status, flags);
+}
+
+// Split-sum of the force partials into caller layouts a[s][3], k[s][3], phi[s].
+__global__ void reduce_out_kernel(const double *part, const int32_t *split_used, const int64_t *s_dev,
+                                  int64_t s_host, double *a, double *k, double *phi, int32_t *status)
+{
+    const int64_t s = s_dev ? *s_dev : s_host;
+    const int S = *split_used;
+    int flags = 0;
+    for (int64_t ii = gtid(); ii < s; ii += gstride()) {
+        double an[3], kn[3], ph;
+        sum_partials(part, ii, S, an, kn, &ph);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (a) a[ii * 3 + c] = an[c];
+            if (k) k[ii * 3 + c] = kn[c];
+            if (!isfinite(an[c]) || !isfinite(kn[c])) flags |= kStNonfinite;
+        }
+        if (phi) phi[ii] = ph;
+        if (!isfinite(ph)) flags |= kStNonfinite;
+    }
+    if (flags) atomicOr(status, flags);
+}
+
+__global__ void check_due_kernel(StepArgs A, double t_block)
+{
+    const int64_t s = *A.s;
+    int flags = 0;
+    for (int64_t ii = gtid(); ii < s; ii += gstride()) {
+        const int64_t i = A.idx[ii];
+        if (A.t[i] + A.dt[i] != t_block) flags |= kStState;
+    }
+    if (flags) atomicOr(A.status, flags);
+}
+
+__global__ void aos_to_soa_kernel(const double *src, double *dst, int64_t n, int64_t np)
+{
+    for (int64_t q = gtid(); q < 3 * n; q += gstride()) {
+        const int64_t i = q / 3, c = q % 3;
+        dst[c * np + i] = src[q];
+    }
+}
+
+__global__ void soa_to_aos_kernel(const double *src, double *dst, int64_t n, int64_t np)
+{
+    for (int64_t q = gtid(); q < 3 * n; q += gstride()) {
+        const int64_t i = q / 3, c = q % 3;
+        dst[q] = src[c * np + i];
+    }
+}
+
+// Predicted records back to [n][3] doubles (mixed: hi + lo and the FP32 velocity).
+__global__ void records_to_aos_kernel(StepArgs A, double *xo, double *vo)
+{
+    const int64_t np = A.n_pad;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) {
+        if (A.precision == NB_PREC_MIXED) {
+            const float4 h = A.j.hi[i], l = A.j.lo[i], w = A.j.vel[i];
+            if (xo) {
+                xo[3 * i + 0] = (double)h.x + (double)l.x;
+                xo[3 * i + 1] = (double)h.y + (double)l.y;
+                xo[3 * i + 2] = (double)h.z + (double)l.z;
+            }
+            if (vo) {
+                vo[3 * i + 0] = (double)w.x;
+                vo[3 * i + 1] = (double)w.y;
+                vo[3 * i + 2] = (double)w.z;
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                if (xo) xo[3 * i + c] = A.xp[c * np + i];
+                if (vo) vo[3 * i + c] = A.vp[c * np + i];
+            }
+        }
+    }
+}
+
+__global__ void iota_kernel(int32_t *idx, int64_t n)
+{
+    for (int64_t i = gtid(); i < n; i += gstride()) idx[i] = (int32_t)i;
+}
+
+// ------------------------------------------------------------------- energy
+// K = sum m v^2 / 2, W = sum m_i phi_i / 2 with the softened FP64 potential.
+// Each CTA sums its particles in a fixed order into scratch[cta][2]; a single
+// thread then adds the CTA sums in index order.
+constexpr int kEnThreads = 128;
+
+__global__ void __launch_bounds__(kEnThreads) energy_kernel(StepArgs A, double *scratch)
+{
+    __shared__ double sk[kEnThreads], sw[kEnThreads];
+    const int64_t np = A.n_pad;
+    const int64_t i = (int64_t)blockIdx.x * kEnThreads + threadIdx.x;
+    double ek = 0.0, ew = 0.0;
+    if (i < A.n) {
+        const double xi = A.x[i], yi = A.x[np + i], zi = A.x[2 * np + i];
+        double phi = 0.0;
+        for (int64_t j = 0; j < A.n; ++j) {
+            const double dx = __ldg(A.x + j) - xi;
+            const double dy = __ldg(A.x + np + j) - yi;
+            const double dz = __ldg(A.x + 2 * np + j) - zi;
+            const double r2 = dx * dx + dy * dy + dz * dz + A.eps2;
+            const double q = (j == i) ? 0.0 : rsqrt(r2);
+            phi -= __ldg(A.m + j) * q;
+        }
+        const double vx = A.v[i], vy = A.v[np + i], vz = A.v[2 * np + i];
+        ek = 0.5 * A.m[i] * (vx * vx + vy * vy + vz * vz);
+        ew = 0.5 * A.m[i] * phi;
+    }
+    sk[threadIdx.x] = ek;
+    sw[threadIdx.x] = ew;
+    __syncthreads();
+    for (int h = kEnThreads / 2; h >= 1; h >>= 1) {
+        if (threadIdx.x < h) {
+            sk[threadIdx.x] += sk[threadIdx.x + h];
+            sw[threadIdx.x] += sw[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        scratch[2 * blockIdx.x] = sk[0];
+        scratch[2 * blockIdx.x + 1] = sw[0];
+    }
+}
+
+__global__ void energy_final_kernel(const double *scratch, int nb, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double K = 0.0, W = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            K += scratch[2 * b];
+            W += scratch[2 * b + 1];
+        }
+        out[0] = K;
+        out[1] = W;
+    }
+}
+
+int grid_for(int64_t n, int threads, int max_grid = 4096)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > max_grid) g = max_grid;
+    return (int)g;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------- launchers
+
+cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cudaStream_t st)
+{
+    predict_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a, use_t_next ? 1 : 0, t_host);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st)
+{
+    if (a.n_pad > a.n) pad_kernel<<<grid_for(a.n_pad - a.n, kStepThreads), kStepThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st)
+{
+    select_kernel<<<1, kSelThreads, 0, st>>>(a, (cudaGraphConditionalHandle)cond, set_cond ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st)
+{
+    // the grid covers the largest possible block; threads past s exit at once
+    correct_kernel<<<grid_for(a.n, kStepThreads, 1024), kStepThreads, 0, st>>>(a, check_due ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st)
+{
+    init_steps_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_out(const double *part, const int32_t *split_used, const int64_t *s, int64_t s_host,
+                              double *a, double *k, double *phi, int32_t *status, cudaStream_t st)
+{
+    reduce_out_kernel<<<grid_for(s_host > 0 ? s_host : 1, kStepThreads), kStepThreads, 0, st>>>(
+        part, split_used, s, s_host, a, k, phi, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(const double *src, double *dst, int64_t n, int64_t np, cudaStream_t st)
+{
+    aos_to_soa_kernel<<<grid_for(3 * n, kStepThreads), kStepThreads, 0, st>>>(src, dst, n, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soa_to_aos(const double *src, double *dst, int64_t n, int64_t np, cudaStream_t st)
+{
+    soa_to_aos_kernel<<<grid_for(3 * n, kStepThreads), kStepThreads, 0, st>>>(src, dst, n, np);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_aos, cudaStream_t st)
+{
+    records_to_aos_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a, xp_aos, vp_aos);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st)
+{
+    iota_kernel<<<grid_for(n, kStepThreads), kStepThreads, 0, st>>>(idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, double *out, cudaStream_t st)
+{
+    const int nb = (int)((a.n + kEnThreads - 1) / kEnThreads);
+    if (nb > scratch_ctas) return cudaErrorInvalidValue;
+    energy_kernel<<<nb, kEnThreads, 0, st>>>(a, scratch);
+    energy_final_kernel<<<1, 32, 0, st>>>(scratch, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_due(const StepArgs &a, double t_block, cudaStream_t st)
+{
+    check_due_kernel<<<grid_for(a.n, kStepThreads, 1024), kStepThreads, 0, st>>>(a, t_block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_active(const int32_t *, int64_t, int64_t, int32_t *, cudaStream_t)
+{
+    return cudaSuccess;   // host-side validation is used for host index lists
+}
+
+}  // namespace nb

@@ -1,0 +1,348 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Forces: every kernel variant, several split factors, ragged sizes; mixed
+precision within 1e-6 and FP64 within 1e-12 (per-particle relative error,
+normalised by the sum of magnitudes where the sum nearly cancels).
+Predictor, corrector, time steps and block selection: bit-exact against the
+oracle given the same inputs. Integration: identical block schedules for the
+first 16 steps and |dE/E| at t = 1 within 2x the oracle's.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+import ics
+from tests.nbtools import condition_scales, rel_errors, stats
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-6, 1: 1e-12}   # precision -> relative force/jerk tolerance
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody
+    nbody.load()
+    return nbody
+
+
+def _forces_vs_oracle(nb, orc, c, snap, idx, t=None):
+    """GPU forces on idx (after predicting to t, default: state time) vs the oracle on the
+    same predicted records; returns error stats."""
+    if t is not None:
+        nb.nb_predict(c.ctx, t)
+    xp, vp = nb.nb_get_predicted(c.ctx, snap.n)
+    a, k, phi = nb.nb_force_jerk(c.ctx, idx)
+    ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, idx, nthreads=orc.default_threads())
+    A, K = condition_scales(snap.m, xp, vp, snap.eps2, idx)
+    ea = rel_errors(a, ar, A)
+    ek = rel_errors(k, kr, K)
+    ep = np.abs(phi - pr) / np.abs(pr)
+    return ea, ek, ep
+
+
+SIZES = [(1, 0.01), (2, 0.0), (7, 0.05), (300, 0.01), (1000, 1.0 / 64), (2049, 1.0 / 256)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,eps", SIZES)
+def test_force_all_variants(nb, orc, prec, n, eps):
+    snap = ics.random_state(n, seed=100 + n, eps=eps) if n < 300 else ics.plummer(n, seed=n, eps=eps)
+    rng = ics.SplitMix64(n)
+    subsets = [np.arange(n), np.array([n - 1]), np.sort(rng.next_u64(min(n, 37)) % n)]
+    with nb.Context(precision=prec) as c:
+        c.init(snap)
+        nb.nb_predict(c.ctx, 0.0)
+        for v in range(nb.nb_num_variants(c.ctx)):
+            for split in (1, 3, 64):
+                for b in range(32):
+                    nb.nb_set_tuning(c.ctx, b, v, split)
+                for sub in subsets:
+                    idx = np.unique(sub).astype(np.int32)
+                    ea, ek, ep = _forces_vs_oracle(nb, orc, c, snap, idx)
+                    tol = TOL[prec]
+                    assert ea.max() < tol and ek.max() < tol and ep.max() < tol, \
+                        (nb.nb_variant_name(c.ctx, v), split, idx.size, stats(ea), stats(ek), stats(ep))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_force_plummer_16k_all_blocks(nb, orc, prec):
+    """Plummer N = 16384 (eps = 1/1024): tuned launch configuration, s = 1 .. N."""
+    snap = ics.config(2)
+    with nb.Context(precision=prec) as c:
+        c.init(snap)
+        nb.nb_predict(c.ctx, 0.0)
+        rng = ics.SplitMix64(77)
+        for s in (1, 5, 64, 1000, 4096, snap.n):
+            idx = np.sort(rng.next_u64(s * 2) % snap.n)
+            idx = np.unique(idx)[:s].astype(np.int32) if s < snap.n else np.arange(snap.n, dtype=np.int32)
+            sample = idx if idx.size <= 512 else idx[:: idx.size // 512]
+            xp, vp = nb.nb_get_predicted(c.ctx, snap.n)
+            a, k, phi = nb.nb_force_jerk(c.ctx, idx)
+            pos = np.searchsorted(idx, sample)
+            ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, sample, nthreads=orc.default_threads())
+            A, K = condition_scales(snap.m, xp, vp, snap.eps2, sample)
+            ea = rel_errors(a[pos], ar, A); ek = rel_errors(k[pos], kr, K)
+            ep = np.abs(phi[pos] - pr) / np.abs(pr)
+            print(f"prec {prec} s {s}: a {stats(ea)} k {stats(ek)} phi {stats(ep)}")
+            assert ea.max() < TOL[prec] and ek.max() < TOL[prec] and ep.max() < TOL[prec]
+
+
+def test_predictor_bit_exact(nb, orc):
+    """FP64 predicted records equal the oracle's predictor bit for bit; the mixed records
+    are the FP64 prediction split into hi + lo (exact to 2^-48 relative)."""
+    snap = ics.config(1)
+    for prec in (1, 0):
+        with nb.Context(precision=prec) as c:
+            c.init(snap)
+            for _ in range(5):
+                nb.nb_step(c.ctx)
+            st = c.state()
+            t_new = float(np.max(st["t"] + st["dt"]) / 2 + np.min(st["t"]) / 2)
+            nb.nb_predict(c.ctx, t_new)
+            xp, vp = nb.nb_get_predicted(c.ctx, snap.n)
+            xr, vr = orc.predict(st["x"], st["v"], st["a"], st["k"], st["t"], t_new)
+            if prec == 1:
+                np.testing.assert_array_equal(xp, xr)
+                np.testing.assert_array_equal(vp, vr)
+            else:
+                assert np.max(np.abs(xp - xr) / np.maximum(np.abs(xr), 1e-30)) < 2.0 ** -46
+                assert np.max(np.abs(vp - vr) / np.maximum(np.abs(vr), 1e-30)) < 2.0 ** -23
+
+
+def test_corrector_and_steps_bit_exact(nb, orc):
+    """Given the GPU's own new forces, the corrected x, v and the new quantised steps equal
+    the oracle's corrector + Aarseth + quantisation bit for bit (both precisions)."""
+    snap = ics.config(1)
+    for prec in (1, 0):
+        with nb.Context(precision=prec) as c:
+            c.init(snap)
+            for _ in range(7):
+                nb.nb_step(c.ctx)
+            before = c.state()
+            tn, s = nb.nb_next_block(c.ctx)
+            idx = nb.nb_get_active(c.ctx, s)
+            nb.nb_predict(c.ctx, tn)
+            a_new, k_new, _ = nb.nb_force_jerk(c.ctx, idx)
+            nb.nb_correct(c.ctx, tn)
+            after = c.state()
+            xr, vr = orc.predict(before["x"], before["v"], before["a"], before["k"], before["t"], tn)
+            for q, i in enumerate(idx):
+                dt = before["dt"][i]
+                x1, v1, cand = orc.correct_particle(xr[i], vr[i], before["a"][i], before["k"][i],
+                                                    a_new[q], k_new[q], dt, 0.01)
+                dtn = orc.quantise(cand, dt, tn)
+                np.testing.assert_array_equal(after["x"][i], x1)
+                np.testing.assert_array_equal(after["v"][i], v1)
+                np.testing.assert_array_equal(after["a"][i], a_new[q])
+                assert after["dt"][i] == dtn and after["t"][i] == tn
+            others = np.setdiff1d(np.arange(snap.n), idx)
+            np.testing.assert_array_equal(after["x"][others], before["x"][others])
+
+
+def test_initial_steps_and_selection_exact(nb, orc):
+    """nb_init's first steps equal the oracle's start rule on the GPU forces; selection
+    equals the oracle's definition on the GPU state."""
+    snap = ics.config(1)
+    with nb.Context(precision=1) as c:
+        c.init(snap)
+        st = c.state()
+        for i in range(snap.n):
+            assert st["dt"][i] == orc.initial_dt(st["a"][i], st["k"][i])
+        for _ in range(20):
+            tn, s = nb.nb_next_block(c.ctx)
+            idx = nb.nb_get_active(c.ctx, s)
+            st = c.state()
+            tr, ir = orc.next_block(st["t"], st["dt"])
+            assert tn == tr
+            np.testing.assert_array_equal(idx, ir)
+            nb.nb_step(c.ctx)
+
+
+def _schedule(nb, c, steps):
+    rows = []
+    for _ in range(steps):
+        tn, s = nb.nb_next_block(c.ctx)
+        idx = nb.nb_get_active(c.ctx, s)
+        rows.append((tn, s, zlib.crc32(np.ascontiguousarray(idx, dtype=np.int32).tobytes())))
+        nb.nb_predict(c.ctx, tn)
+        nb.nb_force_jerk(c.ctx, None, s, want=(False, False, False))
+        nb.nb_correct(c.ctx, tn)
+    return rows
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_block_schedule_matches_golden(nb, prec):
+    """First 16 block steps of the Plummer N = 1024 workload: (t_next, s, active list)
+    identical to the oracle's stored schedule."""
+    from tests.test_golden_schedule import load_schedule
+    gold = load_schedule()
+    snap = ics.config(1)
+    with nb.Context(precision=prec) as c:
+        c.init(snap)
+        rows = _schedule(nb, c, len(gold))
+    for (k, tn, s, crc), got in zip(gold, rows):
+        assert got == (tn, s, crc), (k, got, (tn, s, crc))
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_block_schedule_matches_oracle_16k(nb, orc, prec):
+    """Plummer N = 16384: first 16 block steps identical to the oracle's."""
+    snap = ics.config(2)
+    sysr = orc.System(snap.m, snap.x, snap.v, snap.eps2, nthreads=orc.default_threads())
+    with nb.Context(precision=prec) as c:
+        c.init(snap)
+        rows = _schedule(nb, c, 16)
+    for k, got in enumerate(rows):
+        st, tn, idx = sysr.step()
+        want = (tn, idx.size, zlib.crc32(np.ascontiguousarray(idx, dtype=np.int32).tobytes()))
+        assert got == want, (k, got, want)
+
+
+def test_energy_matches_oracle(nb, orc):
+    snap = ics.config(2)
+    K, W = orc.energy(snap.m, snap.x, snap.v, snap.eps2, nthreads=orc.default_threads())
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        E, Kg, Wg = nb.nb_energy(c.ctx)
+    assert abs(Kg - K) < 1e-14 and abs(Wg - W) < 1e-12 * abs(W)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_energy_conservation_plummer_1k(nb, orc, prec):
+    """Plummer N = 1024 to t = 1: |dE/E| within 2x the oracle's (and all particles at t = 1)."""
+    snap = ics.config(1)
+    sysr = orc.System(snap.m, snap.x, snap.v, snap.eps2, nthreads=orc.default_threads())
+    E0r = sysr.energy()
+    assert sysr.run(1.0) == 0
+    dEr = abs(sysr.energy() - E0r) / abs(E0r)
+    with nb.Context(precision=prec) as c:
+        c.init(snap)
+        E0, _, _ = nb.nb_energy(c.ctx)
+        nb.nb_run(c.ctx, 1.0)
+        E1, _, _ = nb.nb_energy(c.ctx)
+        st = c.state()
+        cnt = nb.nb_stats(c.ctx)
+    dE = abs(E1 - E0) / abs(E0)
+    print(f"prec {prec}: |dE/E| gpu {dE:.3e} oracle {dEr:.3e}; steps gpu {cnt['block_steps']} "
+          f"oracle {sysr.counters['block_steps']}")
+    assert np.all(st["t"] == 1.0)
+    assert dE <= 2 * dEr + 1e-15, (dE, dEr)
+
+
+def test_run_step_and_timed_paths_agree(nb):
+    """The graph loop (nb_run), host-driven nb_step and nb_run_timed give the same state bitwise."""
+    snap = ics.plummer(3000, seed=5, eps=1.0 / 128)
+    states = []
+    for mode in ("run", "timed", "step"):
+        with nb.Context(precision=0) as c:
+            c.init(snap)
+            if mode == "run":
+                nb.nb_run(c.ctx, 1.0 / 16)
+            elif mode == "timed":
+                ms, nl = nb.nb_run_timed(c.ctx, 1.0 / 16)
+                assert nl > 0 and ms > 0
+            else:
+                while True:
+                    tn, s = nb.nb_next_block(c.ctx)
+                    if tn > 1.0 / 16:
+                        break
+                    nb.nb_step(c.ctx)
+            states.append((c.state(), nb.nb_stats(c.ctx)))
+    for st, cnt in states[1:]:
+        for key in ("x", "v", "a", "k", "t", "dt"):
+            np.testing.assert_array_equal(st[key], states[0][0][key])
+        assert cnt["block_steps"] == states[0][1]["block_steps"]
+
+
+def test_deterministic_and_resume_bitwise(nb):
+    """Two runs agree bitwise; a run checkpointed at t = 1/16 and resumed in a new context
+    ends bitwise equal to an uninterrupted run."""
+    snap = ics.plummer(2000, seed=9, eps=1.0 / 128)
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        nb.nb_run(c.ctx, 1.0 / 16)
+        mid = c.state()
+        nb.nb_run(c.ctx, 1.0 / 8)
+        ref = c.state()
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        nb.nb_run(c.ctx, 1.0 / 8)
+        again = c.state()
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        nb.nb_set_state(c.ctx, mid)
+        nb.nb_run(c.ctx, 1.0 / 8)
+        resumed = c.state()
+    for key in ("x", "v", "t", "dt"):
+        np.testing.assert_array_equal(again[key], ref[key])
+        np.testing.assert_array_equal(resumed[key], ref[key])
+
+
+def test_error_paths(nb):
+    """Host-made failures: bad arguments, calls out of order, coincident bodies with eps = 0,
+    a step underflow, and a device wait whose spin limit runs out (the context stays usable)."""
+    snap = ics.plummer(500, seed=3, eps=0.01)
+    with nb.Context() as c:
+        c.init(snap)
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_force_jerk(c.ctx, np.array([3, 2], dtype=np.int32))
+        assert e.value.status == nb.NB_ERR_ARG
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_force_jerk(c.ctx, np.array([0, 500], dtype=np.int32))
+        assert e.value.status == nb.NB_ERR_ARG
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_correct(c.ctx, 0.5)
+        assert e.value.status == nb.NB_ERR_STATE
+        tn, s = nb.nb_next_block(c.ctx)
+        nb.nb_predict(c.ctx, tn)
+        nb.nb_force_jerk(c.ctx, None, s, want=(False, False, False))
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_correct(c.ctx, tn * 3)          # members are not due then
+        assert e.value.status == nb.NB_ERR_STATE
+    m = np.array([0.5, 0.5]); x = np.zeros((2, 3)); v = np.zeros((2, 3))
+    with nb.Context() as c:
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_init(c.ctx, m, x, v, 0.0)
+        assert e.value.status == nb.NB_ERR_NONFINITE
+    with nb.Context(dt_min=2.0 ** -5) as c:
+        with pytest.raises(nb.NbError) as e:
+            c.init(snap)
+        assert e.value.status == nb.NB_ERR_DT_UNDERFLOW
+    for prec in (0, 1):
+        with nb.Context(precision=prec, inject=1, spin_limit=20000) as c:
+            with pytest.raises(nb.NbError) as e:
+                c.init(snap)
+            assert e.value.status == nb.NB_ERR_TIMEOUT
+            c.init(snap)                            # the context and the GPU stay usable
+            nb.nb_run(c.ctx, 1.0 / 32)
+            assert np.isfinite(nb.nb_energy(c.ctx)[0])
+
+
+def test_dev_entry_points_match_host(nb):
+    torch = pytest.importorskip("torch")
+    snap = ics.plummer(1500, seed=4, eps=1.0 / 128)
+    dev = torch.device("cuda:0")
+    m = torch.tensor(snap.m, device=dev); x = torch.tensor(snap.x, device=dev); v = torch.tensor(snap.v, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    with nb.Context(stream=stream) as c:
+        nb.nb_init_dev(c.ctx, snap.n, m.data_ptr(), x.data_ptr(), v.data_ptr(), snap.eps2)
+        c.n = snap.n
+        idx = np.arange(0, snap.n, 7, dtype=np.int32)
+        a_h, k_h, p_h = nb.nb_force_jerk(c.ctx, idx)
+        idx_d = torch.tensor(idx, device=dev)
+        a_d = torch.zeros((idx.size, 3), dtype=torch.float64, device=dev)
+        k_d = torch.zeros_like(a_d); p_d = torch.zeros(idx.size, dtype=torch.float64, device=dev)
+        nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), idx.size, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
+        nb.nb_sync(c.ctx)
+        np.testing.assert_array_equal(a_d.cpu().numpy(), a_h)
+        np.testing.assert_array_equal(k_d.cpu().numpy(), k_h)
+        np.testing.assert_array_equal(p_d.cpu().numpy(), p_h)
+    with nb.Context() as c:
+        c.init(snap)
+        st_host = c.state()
+    np.testing.assert_array_equal(st_host["dt"], st_host["dt"])
