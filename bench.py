@@ -448,11 +448,16 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ref-t-end", type=float, default=1.0 / 16,
                     help="integration horizon of one oracle sample (bounded CPU work)")
+    ap.add_argument("--t-end", type=float, default=1.0,
+                    help="integration horizon of one step (default 1; shorter only for profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
                     help="full-N force sweep on King N=2^20 (default on)")
     args = ap.parse_args(argv)
+    global T_END  # noqa: PLW0603
+    T_END = args.t_end
+    WORKLOAD["t_end"] = T_END
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

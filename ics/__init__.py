@@ -254,15 +254,21 @@ def king(n: int, seed: int, w0: float, eps: float, name: str = "king") -> Snapsh
     x = _isotropic(rng, r)
     w_at = np.maximum(np.interp(r, r_grid, w_grid), 0.0)
     vesc = np.sqrt(2.0 * w_at)
-    bound = np.where(w_at >= 1.0, 2.0 * np.exp(w_at - 1.0), 2.0 * w_at)
+    # bound of g(v) = v^2 (e^{W - v^2/2} - 1) on [0, sqrt(2W)]: g <= 2 e^{W-1} (W >= 1) or 2W,
+    # and g <= e^W max_y y (W - y/2) = e^W W^2 / 2 (from e^x - 1 <= x e^x); take the smaller
+    b1 = np.where(w_at >= 1.0, 2.0 * np.exp(w_at - 1.0), 2.0 * w_at)
+    bound = np.minimum(b1, np.exp(w_at) * w_at * w_at / 2.0)
     speed = np.zeros(n)
     todo = np.nonzero(vesc > 0.0)[0]
     while todo.size:
-        vv = vesc[todo] * rng.uniform(todo.size)
-        g = vv * vv * (np.exp(w_at[todo] - 0.5 * vv * vv) - 1.0)
-        ok = rng.uniform(todo.size) * bound[todo] < g
-        speed[todo[ok]] = vv[ok]
-        todo = todo[~ok]
+        kk = int(min(64, max(1, (1 << 18) // todo.size)))       # candidates per particle this round
+        vv = vesc[todo, None] * rng.uniform(todo.size * kk).reshape(todo.size, kk)
+        g = vv * vv * (np.exp(w_at[todo, None] - 0.5 * vv * vv) - 1.0)
+        ok = rng.uniform(todo.size * kk).reshape(todo.size, kk) * bound[todo, None] < g
+        hit = ok.any(axis=1)
+        first = np.argmax(ok, axis=1)
+        speed[todo[hit]] = vv[np.nonzero(hit)[0], first[hit]]
+        todo = todo[~hit]
     v = _isotropic(rng, speed)
     m = np.full(n, 1.0 / n)
     # continuum energy of the unit-mass model: W = -int F dF / r

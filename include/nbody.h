@@ -164,8 +164,10 @@ nb_status nb_step(nb_ctx *ctx);
 nb_status nb_run(nb_ctx *ctx, double t_end);
 
 /* Same trajectory as nb_run, driven from the host one block step at a time, with
- * CUDA events around every force launch. *force_ms = summed force-kernel time,
- * *launches = number of force launches (NULL allowed). For measurement. */
+ * CUDA events around every force launch (a short, time-bounded wait kernel
+ * precedes the start event so that it is processed only once the launch is
+ * queued). *force_ms = summed force-kernel time, *launches = number of force
+ * launches (NULL allowed). For measurement; slower than nb_run. */
 nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches);
 
 /* Kinetic, potential (softened, W = sum m_i phi_i / 2) and total energy of the

@@ -15,9 +15,12 @@
 //     split index), so results are bitwise reproducible run to run.
 //
 // Mixed precision: positions arrive as double-single (hi, lo) pairs so that
-// r = x_j - x_i keeps ~46 bits even for close pairs; the pair arithmetic is
-// FP32 with one MUFU reciprocal square root; per-thread FP32 partial sums over
-// at most kFoldPairs pairs are folded into (hi, lo) two-sum accumulators.
+// r = x_j - x_i keeps ~46 bits even for close pairs (velocities are FP32: the
+// jerk error is set by the FP32 pair arithmetic, not by w); the pair
+// arithmetic is FP32 with one MUFU reciprocal square root; per-thread FP32 partial sums over at most kFoldPairs
+// pairs are folded into (hi, lo) two-sum accumulators, and the cross-thread
+// reductions combine (hi, lo) pairs with two-sums too (FP64 is a narrow pipe on
+// this part; only the final per-split partial is converted to double).
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -168,6 +171,54 @@ __device__ __forceinline__ void to_double(const Acc7 &hi, const Acc7 &lo, double
     d[6] = (double)hi.ph + (double)lo.ph;
 }
 
+// (hi, lo) + (hi2, lo2) with a two-sum on the high parts.
+__device__ __forceinline__ void ds_add(float &hi, float &lo, float hi2, float lo2)
+{
+    float s = hi + hi2;
+    float bp = s - hi;
+    float e = (hi - (s - bp)) + (hi2 - bp);
+    e += lo + lo2;
+    hi = s + e;                 // renormalise (fast two-sum)
+    lo = e - (hi - s);
+}
+
+// xor-butterfly over the lanes of one group of G consecutive lanes (G | 32)
+template <int G>
+__device__ __forceinline__ void ds_group_reduce(float &hi, float &lo)
+{
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+        ds_add(hi, lo, h2, l2);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void ds_group_reduce7(Acc7 &hi, Acc7 &lo)
+{
+    ds_group_reduce<G>(hi.ax, lo.ax);
+    ds_group_reduce<G>(hi.ay, lo.ay);
+    ds_group_reduce<G>(hi.az, lo.az);
+    ds_group_reduce<G>(hi.kx, lo.kx);
+    ds_group_reduce<G>(hi.ky, lo.ky);
+    ds_group_reduce<G>(hi.kz, lo.kz);
+    ds_group_reduce<G>(hi.ph, lo.ph);
+}
+
+__device__ __forceinline__ float acc_get(const Acc7 &q, int c)
+{
+    switch (c) {
+    case 0: return q.ax;
+    case 1: return q.ay;
+    case 2: return q.az;
+    case 3: return q.kx;
+    case 4: return q.ky;
+    case 5: return q.kz;
+    default: return q.ph;
+    }
+}
+
 // ------------------------------------------------------------ shared memory
 
 constexpr int kMaxRC = 2 * 7;   // R * components, largest R over variants
@@ -176,7 +227,7 @@ struct __align__(128) Smem {
     float4 hi[kStages][kJT];
     float4 lo[kStages][kJT];
     float4 vel[kStages][kJT];
-    double red[kThreads / 32][kMaxRC];
+    float2 red[kThreads / 32][kMaxRC];
     uint64_t bar[kStages];
     uint64_t inject_bar;
     int abort;
@@ -245,28 +296,24 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
-    // fixed-order reduction: lanes (xor tree), then warps in ascending order
+    // fixed-order reduction: lanes (xor tree of two-sums), then warps in ascending order
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        double d[7];
-        to_double(hi[r], lo[r], d);
+        ds_group_reduce7<32>(hi[r], lo[r]);
+        if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < 7; ++c) {
-            double x = d[c];
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == 0) sm->red[warp][r * 7 + c] = x;
+            for (int c = 0; c < 7; ++c) sm->red[warp][r * 7 + c] = make_float2(acc_get(hi[r], c), acc_get(lo[r], c));
         }
     }
     __syncthreads();
     if (tid < R * 7) {
-        double x = 0.0;
+        float h = sm->red[0][tid].x, l = sm->red[0][tid].y;
 #pragma unroll
-        for (int wv = 0; wv < kThreads / 32; ++wv) x += sm->red[wv][tid];
+        for (int wv = 1; wv < kThreads / 32; ++wv) ds_add(h, l, sm->red[wv][tid].x, sm->red[wv][tid].y);
         int r = tid / 7, c = tid % 7;
         int64_t ii = bx * R + r;
         if (ii < s) {
-            A.part[(ii * S + by) * kPartStride + c] = x;
+            A.part[(ii * S + by) * kPartStride + c] = (double)h + (double)l;
             if (c == 0) A.part[(ii * S + by) * kPartStride + 7] = 0.0;
         }
     }
@@ -384,16 +431,13 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        double d[7];
-        to_double(hi[r], lo[r], d);
-        if (TJ > 1) {
-#pragma unroll
-            for (int c = 0; c < 7; ++c)
-#pragma unroll
-                for (int off = TJ / 2; off >= 1; off >>= 1) d[c] += __shfl_xor_sync(0xffffffffu, d[c], off);
-        }
+        if (TJ > 1) ds_group_reduce7<TJ>(hi[r], lo[r]);
         const int64_t ii = bx * I + (int64_t)r * TI + ti;
-        if (tj == 0 && ii < s) write_part(A, ii, by, S, d);
+        if (tj == 0 && ii < s) {
+            double d[7];
+            to_double(hi[r], lo[r], d);
+            write_part(A, ii, by, S, d);
+        }
     }
 }
 

@@ -26,7 +26,7 @@ constexpr int kStSteps = 16;         // block-step cap reached inside nb_run
 // ------------------------------------------------------------- force kernels
 
 // Mixed-precision j-record, 48 bytes: predicted position split into
-// hi = fl32(x) and lo = fl32(x - hi), velocity in FP32, mass in FP32.
+// hi = fl32(x) and lo = fl32(x - hi) (double-single), velocity and mass in FP32.
 struct JRecs {
     float4 *hi;   // (x_hi, y_hi, z_hi, m)
     float4 *lo;   // (x_lo, y_lo, z_lo, 0)
@@ -124,5 +124,6 @@ cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, 
 cudaError_t launch_check_active(const int32_t *idx, int64_t s, int64_t n, int32_t *status,
                                 cudaStream_t st);
 cudaError_t launch_check_due(const StepArgs &a, double t_block, cudaStream_t st);
+cudaError_t launch_delay(uint64_t ns, cudaStream_t st);
 
 }  // namespace nb

@@ -454,6 +454,21 @@ __global__ void energy_final_kernel(const double *scratch, int nb, double *out)
     }
 }
 
+// Keeps the stream busy for about ns nanoseconds (bounded by time and by an
+// iteration cap), so that work enqueued behind it is already queued when it
+// ends. Used only by the measurement loop.
+__global__ void delay_kernel(uint64_t ns)
+{
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < 200000; ++it) {
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= ns) break;
+        __nanosleep(256);
+    }
+}
+
 int grid_for(int64_t n, int threads, int max_grid = 4096)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -535,6 +550,12 @@ cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, 
     if (nb > scratch_ctas) return cudaErrorInvalidValue;
     energy_kernel<<<nb, kEnThreads, 0, st>>>(a, scratch);
     energy_final_kernel<<<1, 32, 0, st>>>(scratch, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delay(uint64_t ns, cudaStream_t st)
+{
+    delay_kernel<<<1, 1, 0, st>>>(ns);
     return cudaGetLastError();
 }
 

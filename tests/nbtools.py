@@ -32,7 +32,14 @@ def rel_errors(x_gpu, x_ref, scale, cancel=1e-3):
     d = np.linalg.norm(np.atleast_2d(x_gpu - x_ref).reshape(len(scale), -1), axis=1)
     nr = np.linalg.norm(np.atleast_2d(x_ref).reshape(len(scale), -1), axis=1)
     den = np.where(nr >= cancel * scale, nr, scale)
-    return d / den
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(d == 0.0, 0.0, d / den)   # an exact zero matches an exact zero
+
+
+def rel_scalar(x_gpu, x_ref):
+    d = np.abs(x_gpu - x_ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(d == 0.0, 0.0, d / np.abs(x_ref))
 
 
 def stats(e):
