@@ -248,7 +248,10 @@ def main_gpu(args):
     m_d = torch.tensor(snap.m, device=dev)
     x_d = torch.tensor(snap.x, device=dev)
     v_d = torch.tensor(snap.v, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library and the CUDA events must share it (torch's legacy
+    # default stream has handle 0, which the C ABI reads as "create your own")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -397,24 +400,30 @@ def main_gpu(args):
     return 0
 
 
-def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz):
+def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
+                precision=None):
     """King W0 = 6, N = 1,048,576, eps = 1e-3: one mixed force evaluation per active-set
     size s in {1, 64, 1024, 16384, N} (active = first s of a seeded permutation, ascending),
     split factor autotuned; interactions/s and FP32 roofline fraction per s."""
     import ics
-    snap = ics.config(5)
+    snap = ics.config(5, n=n_override)
     n = snap.n
     m_d = torch.tensor(snap.m, device=dev)
     x_d = torch.tensor(snap.x, device=dev)
     v_d = torch.tensor(snap.v, device=dev)
-    c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+    prec = nb.NB_PREC_MIXED if precision is None else precision
+    c = nb.Context(precision=prec, device=0, stream=sptr)
     nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
     nb.nb_predict(c.ctx, 0.0)
-    nb.nb_autotune(c.ctx)
+    if autotune:
+        nb.nb_autotune(c.ctx)
     perm = np.argsort(ics.SplitMix64(ics.BASE_SEED + 5).uniform(n))
-    out = {"workload": "king W0=6 N=1048576 eps=1e-3, single evaluation", "points": []}
+    out = {"workload": f"king W0=6 N={n} eps=1e-3, single evaluation", "points": [],
+           "precision": "fp64" if prec == nb.NB_PREC_FP64 else "mixed"}
     stream = torch.cuda.current_stream(dev)
-    for s in (1, 64, 1024, 16384, n):
+    assert stream.cuda_stream == sptr
+    for s in (s_list or (1, 64, 1024, 16384, n)):
+        s = min(int(s), n)
         idx = np.sort(perm[:s]).astype(np.int32)
         idx_d = torch.tensor(idx, device=dev)
         a_d = torch.empty((s, 3), dtype=torch.float64, device=dev)
@@ -454,6 +463,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
                     help="full-N force sweep on King N=2^20 (default on)")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="run only the force sweep and print it (profiling and kernel studies)")
+    ap.add_argument("--sweep-n", type=int, default=None, help="particle count of --sweep-only")
+    ap.add_argument("--sweep-s", type=str, default=None, help="comma-separated active counts of --sweep-only")
+    ap.add_argument("--sweep-fp64", action="store_true", help="--sweep-only with the FP64 kernels")
+    ap.add_argument("--no-autotune", action="store_true", help="--sweep-only with the default tuning table")
     args = ap.parse_args(argv)
     global T_END  # noqa: PLW0603
     T_END = args.t_end
@@ -462,7 +477,36 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep_only:
+        return main_sweep(args)
     return main_gpu(args)
+
+
+def main_sweep(args):
+    """Only the force sweep, printed as one JSON line (not a bench line)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = ClockSampler(0).start()
+    s_list = [int(q) for q in args.sweep_s.split(",")] if args.sweep_s else None
+    out = force_sweep(nb, torch, dev, stream.cuda_stream, num_sms, None, n_override=args.sweep_n, s_list=s_list,
+                      autotune=not args.no_autotune,
+                      precision=nb.NB_PREC_FP64 if args.sweep_fp64 else nb.NB_PREC_MIXED)
+    clk = clocks.stop()
+    if clk["sm_mhz"]:
+        peak = fp32_peak_tflops(num_sms, clk["sm_mhz"])
+        for p in out["points"]:
+            p["frac_fp32_peak"] = p["tflops"] / peak
+    out["clocks"] = clk
+    print(json.dumps(out))
+    return 0
 
 
 if __name__ == "__main__":

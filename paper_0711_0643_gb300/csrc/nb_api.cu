@@ -41,6 +41,9 @@ struct nb_ctx {
     double *t_next = nullptr, *t_end = nullptr;
     double *part = nullptr;
     int64_t part_cap = 0;
+    double *fin = nullptr;          // final force sums [n_pad][8]
+    int32_t *tickets = nullptr;     // per i-block arrival counters
+    double *tn = nullptr;           // t + dt
     int32_t *split_used = nullptr;
     Tuning *tune_dev = nullptr;
     Tuning tune{};
@@ -107,13 +110,14 @@ StepArgs step_args(nb_ctx *c)
     A.n = c->n;
     A.n_pad = c->n_pad;
     A.m = c->m; A.x = c->x; A.v = c->v; A.a = c->a; A.k = c->k; A.t = c->t; A.dt = c->dt;
+    A.tn = c->tn;
     A.j = c->j;
     A.xp = c->xp; A.vp = c->vp;
     A.precision = c->cfg.precision;
     A.eps2 = c->eps2;
     A.eta = c->cfg.eta; A.dt_max = c->cfg.dt_max; A.dt_min = c->cfg.dt_min;
     A.idx = c->idx; A.s = c->s; A.t_next = c->t_next; A.t_end = c->t_end;
-    A.part = c->part; A.split_used = c->split_used;
+    A.fin = c->fin;
     A.status = c->status; A.counters = c->counters; A.interactions = c->interactions;
     A.chunk_cnt = c->sel_cnt; A.chunk_min = c->sel_min; A.done_ctr = c->done_ctr;
     A.select_ctas = 1;
@@ -133,6 +137,8 @@ ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
     F.s = c->s;
     F.part = c->part;
     F.part_cap = c->part_cap;
+    F.fin = c->fin;
+    F.tickets = c->tickets;
     F.split_used = c->split_used;
     F.tune = c->tune_dev;
     F.force_variant = variant;
@@ -173,13 +179,17 @@ void free_system(nb_ctx *c)
         c->run_exec = nullptr;
     }
     void *ptrs[] = {c->m, c->x, c->v, c->a, c->k, c->t, c->dt, c->j.hi, c->j.lo, c->j.vel, c->xp, c->vp,
-                    c->stage, c->idx, c->part, c->en_scratch, c->out_a, c->out_k, c->out_phi};
+                    c->stage, c->idx, c->part, c->fin, c->tickets, c->tn, c->en_scratch, c->out_a, c->out_k,
+                    c->out_phi};
     for (void *p : ptrs) dfree(p);
     c->m = c->x = c->v = c->a = c->k = c->t = c->dt = nullptr;
     c->j = JRecs{};
     c->xp = c->vp = c->stage = nullptr;
     c->idx = nullptr;
     c->part = nullptr;
+    c->fin = nullptr;
+    c->tickets = nullptr;
+    c->tn = nullptr;
     c->en_scratch = nullptr;
     c->out_a = c->out_k = c->out_phi = nullptr;
     c->n = c->n_pad = c->n_tiles = 0;
@@ -212,6 +222,10 @@ nb_status alloc_system(nb_ctx *ctx, int64_t n)
     // partials: room for s * split * 8 doubles; at least 4 splits of a full block
     ctx->part_cap = std::max<int64_t>(4 * np * kPartStride, int64_t(1) << 23);
     CK(dalloc(&ctx->part, ctx->part_cap));
+    CK(dalloc(&ctx->fin, kPartStride * np));
+    CK(dalloc(&ctx->tickets, np + 1));
+    CK(dalloc(&ctx->tn, np));
+    CK(cudaMemsetAsync(ctx->tickets, 0, (np + 1) * sizeof(int32_t), ctx->stream));
     ctx->en_ctas = (int)((n + 127) / 128);
     CK(dalloc(&ctx->en_scratch, 2 * (size_t)ctx->en_ctas));
     CK(dalloc(&ctx->out_a, 3 * np));
@@ -250,6 +264,8 @@ nb_status sync_status(nb_ctx *ctx)
     CK(cudaMemcpy(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost));
     if (st == 0) return NB_OK;
     CK(cudaMemset(ctx->status, 0, sizeof(int32_t)));
+    if ((st & kStTimeout) && ctx->tickets)   // an aborted force launch may leave tickets armed
+        CK(cudaMemset(ctx->tickets, 0, (ctx->n_pad + 1) * sizeof(int32_t)));
     if (st & kStTimeout) return fail(ctx, NB_ERR_TIMEOUT, "a device-side wait exceeded the spin limit");
     if (st & kStNonfinite) return fail(ctx, NB_ERR_NONFINITE, "non-finite force, position or velocity");
     if (st & kStUnderflow) return fail(ctx, NB_ERR_DT_UNDERFLOW, "time step below dt_min");
@@ -565,8 +581,7 @@ nb_status nb_get_predicted(nb_ctx *ctx, double *xp, double *vp)
 static nb_status force_common(nb_ctx *ctx, int64_t s, double *a_dev, double *k_dev, double *phi_dev)
 {
     CK(launch_force_ctx(ctx));
-    CK(launch_reduce_out(ctx->part, ctx->split_used, nullptr, s, a_dev, k_dev, phi_dev, ctx->status,
-                         ctx->stream));
+    CK(launch_reduce_out(ctx->fin, nullptr, s, a_dev, k_dev, phi_dev, ctx->status, ctx->stream));
     ctx->forces_pending = true;
     ctx->block_s = s;
     return NB_OK;
@@ -756,6 +771,15 @@ nb_status nb_set_state(nb_ctx *ctx, const nb_state_view *view)
     if (!view || view->n != ctx->n) return fail(ctx, NB_ERR_ARG, "state view size mismatch");
     if (!view->m || !view->x || !view->v || !view->a || !view->k || !view->t || !view->dt)
         return fail(ctx, NB_ERR_ARG, "set_state needs every array");
+    for (int64_t i = 0; i < ctx->n; ++i) {
+        // steps must be powers of two within [dt_min, dt_max] and times multiples of them
+        int e;
+        const double dti = view->dt[i], ti = view->t[i];
+        if (!(dti >= ctx->cfg.dt_min && dti <= ctx->cfg.dt_max) || std::frexp(dti, &e) != 0.5 ||
+            !(ti >= 0.0) || !std::isfinite(ti) || std::floor(ti / dti) * dti != ti)
+            return fail(ctx, NB_ERR_ARG, "state %lld: t = %g, dt = %g is not a valid block-step state",
+                        (long long)i, ti, dti);
+    }
     const int64_t n = ctx->n, np = ctx->n_pad;
     CK(cudaStreamSynchronize(ctx->stream));
     auto vec = [&](const double *src, double *dst) -> nb_status {
@@ -771,6 +795,7 @@ nb_status nb_set_state(nb_ctx *ctx, const nb_state_view *view)
     if ((st = vec(view->v, ctx->v)) != NB_OK) return st;
     if ((st = vec(view->a, ctx->a)) != NB_OK) return st;
     if ((st = vec(view->k, ctx->k)) != NB_OK) return st;
+    CK(launch_tnext(step_args(ctx), ctx->stream));
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);

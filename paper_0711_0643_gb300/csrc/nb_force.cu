@@ -11,8 +11,10 @@
 //     by the TMA bulk engine (cp.async.bulk + mbarrier, kStages in flight);
 //   * each thread holds R i-particles in registers and sweeps the tile with
 //     TJ threads sharing each i (TJ > 1 splits j inside the CTA when s is small);
-//   * partials are reduced in FP64 in a fixed order (lane shuffles, then the
-//     split index), so results are bitwise reproducible run to run.
+//   * partials are reduced in a fixed order (lane shuffles, then the split
+//     index): the last CTA to finish an i-block (an arrival ticket, no waiting)
+//     sums that block's split partials in ascending split order, so results
+//     are bitwise reproducible run to run.
 //
 // Mixed precision: positions arrive as double-single (hi, lo) pairs so that
 // r = x_j - x_i keeps ~46 bits even for close pairs (velocities are FP32: the
@@ -160,17 +162,6 @@ __device__ __forceinline__ void fold(Acc7 &hi, Acc7 &lo, Acc7 &p)
     two_sum_fold(hi.ph, lo.ph, p.ph);
 }
 
-__device__ __forceinline__ void to_double(const Acc7 &hi, const Acc7 &lo, double *d)
-{
-    d[0] = (double)hi.ax + (double)lo.ax;
-    d[1] = (double)hi.ay + (double)lo.ay;
-    d[2] = (double)hi.az + (double)lo.az;
-    d[3] = (double)hi.kx + (double)lo.kx;
-    d[4] = (double)hi.ky + (double)lo.ky;
-    d[5] = (double)hi.kz + (double)lo.kz;
-    d[6] = (double)hi.ph + (double)lo.ph;
-}
-
 // (hi, lo) + (hi2, lo2) with a two-sum on the high parts.
 __device__ __forceinline__ void ds_add(float &hi, float &lo, float hi2, float lo2)
 {
@@ -231,6 +222,7 @@ struct __align__(128) Smem {
     uint64_t bar[kStages];
     uint64_t inject_bar;
     int abort;
+    int last;
 };
 
 __device__ __forceinline__ int bucket_of(int64_t s)
@@ -252,12 +244,51 @@ __device__ __forceinline__ int clamp_split(int S, int64_t n_tiles, int64_t s, in
     return S;
 }
 
-__device__ __forceinline__ void write_part(const ForceArgs &A, int64_t ii, int by, int S, const double *d)
+// Split partial of active particle ii from split by, as (hi, lo) float pairs.
+__device__ __forceinline__ float2 *part2(const ForceArgs &A, int64_t ii, int by, int S)
 {
-    double *dst = A.part + (ii * S + by) * kPartStride;
+    return reinterpret_cast<float2 *>(A.part) + (ii * S + by) * kPartStride;
+}
+
+__device__ __forceinline__ void write_part(const ForceArgs &A, int64_t ii, int by, int S, const Acc7 &hi,
+                                           const Acc7 &lo)
+{
+    float2 *dst = part2(A, ii, by, S);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) dst[c] = d[c];
-    dst[7] = 0.0;
+    for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+}
+
+// Called by every thread after a work item has written its partials. The CTA
+// that completes the i-block (ticket S - 1) adds the block's S partials in split
+// order with two-sums and writes the FP64 results; it then re-arms the ticket.
+__device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, int64_t I, Smem *sm)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int t = atomicAdd(&A.tickets[bx], 1);
+        sm->last = (t == S - 1);
+    }
+    __syncthreads();
+    if (sm->last) {
+        __threadfence();
+        const int64_t ib0 = bx * I;
+        const int64_t ib1 = ib0 + I < s ? ib0 + I : s;
+        const int64_t cnt = (ib1 - ib0) * 7;
+        for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
+            const int64_t ii = ib0 + q / 7;
+            const int c = (int)(q % 7);
+            const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
+            float h = 0.f, l = 0.f;
+            for (int sp = 0; sp < S; ++sp) {
+                const float2 v = __ldcg(src + sp * kPartStride);
+                ds_add(h, l, v.x, v.y);
+            }
+            A.fin[ii * kPartStride + c] = (double)h + (double)l;
+        }
+        if (threadIdx.x == 0) A.tickets[bx] = 0;
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------- streamed variant
@@ -312,10 +343,7 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
         for (int wv = 1; wv < kThreads / 32; ++wv) ds_add(h, l, sm->red[wv][tid].x, sm->red[wv][tid].y);
         int r = tid / 7, c = tid % 7;
         int64_t ii = bx * R + r;
-        if (ii < s) {
-            A.part[(ii * S + by) * kPartStride + c] = (double)h + (double)l;
-            if (c == 0) A.part[(ii * S + by) * kPartStride + 7] = 0.0;
-        }
+        if (ii < s) part2(A, ii, by, S)[c] = make_float2(h, l);
     }
     __syncthreads();
 }
@@ -433,11 +461,7 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     for (int r = 0; r < R; ++r) {
         if (TJ > 1) ds_group_reduce7<TJ>(hi[r], lo[r]);
         const int64_t ii = bx * I + (int64_t)r * TI + ti;
-        if (tj == 0 && ii < s) {
-            double d[7];
-            to_double(hi[r], lo[r], d);
-            write_part(A, ii, by, S, d);
-        }
+        if (tj == 0 && ii < s) write_part(A, ii, by, S, hi[r], lo[r]);
     }
 }
 
@@ -506,6 +530,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
             if (tid == 0) atomicOr(A.status, kStTimeout);
             return;
         }
+        finish_item(A, s, bx, S, I, sm);
     }
 }
 
@@ -567,10 +592,7 @@ __device__ void work_f64_stream(const ForceArgs &A, int64_t s, int64_t bx, int b
     if (tid < 7) {
         double x = 0.0;
         for (int wv = 0; wv < kThreads / 32; ++wv) x += red[wv][tid];
-        if (bx < s) {
-            A.part[(bx * S + by) * kPartStride + tid] = x;
-            if (tid == 0) A.part[(bx * S + by) * kPartStride + 7] = 0.0;
-        }
+        if (bx < s) A.part[(bx * S + by) * kPartStride + tid] = x;
     }
     __syncthreads();
 }
@@ -593,8 +615,34 @@ __device__ void work_f64_iloop(const ForceArgs &A, int64_t s, int64_t bx, int by
     if (ii < s) {
         double *dst = A.part + (ii * S + by) * kPartStride;
         for (int c = 0; c < 7; ++c) dst[c] = acc[c];
-        dst[7] = 0.0;
     }
+}
+
+// FP64 counterpart of finish_item: FP64 sums in split order.
+__device__ void finish_item_f64(const ForceArgs &A, int64_t s, int64_t bx, int S, int64_t I, int *last)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int t = atomicAdd(&A.tickets[bx], 1);
+        *last = (t == S - 1);
+    }
+    __syncthreads();
+    if (*last) {
+        __threadfence();
+        const int64_t ib0 = bx * I;
+        const int64_t ib1 = ib0 + I < s ? ib0 + I : s;
+        const int64_t cnt = (ib1 - ib0) * 7;
+        for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
+            const int64_t ii = ib0 + q / 7;
+            const int c = (int)(q % 7);
+            double x = 0.0;
+            for (int sp = 0; sp < S; ++sp) x += __ldcg(A.part + (ii * S + sp) * kPartStride + c);
+            A.fin[ii * kPartStride + c] = x;
+        }
+        if (threadIdx.x == 0) A.tickets[bx] = 0;
+    }
+    __syncthreads();
 }
 
 __host__ __device__ __forceinline__ int f64_I(int v) { return v == 0 ? 1 : kThreads; }
@@ -603,6 +651,7 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
 {
     __shared__ double red[kThreads / 32][7];
     __shared__ uint64_t inject_bar;
+    __shared__ int last;
     const int64_t s = *A.s;
     if (s <= 0) return;
     if (A.inject) {
@@ -635,6 +684,7 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
             work_f64_stream(A, s, bx, by, S, red);
         else
             work_f64_iloop(A, s, bx, by, S);
+        finish_item_f64(A, s, bx, S, I, &last);
     }
 }
 

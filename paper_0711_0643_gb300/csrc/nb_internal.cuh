@@ -50,8 +50,10 @@ struct ForceArgs {
     double eps2;
     const int32_t *idx;   // active list (ascending), length *s
     const int64_t *s;     // active count (device)
-    double *part;         // partials [s][split][8]
-    int64_t part_cap;     // capacity of part in doubles
+    double *part;         // split partials [s][split][8] (mixed: float2 (hi, lo) pairs)
+    int64_t part_cap;     // capacity of part in 8-byte words
+    double *fin;          // final sums [s][8]: ax ay az kx ky kz phi pad
+    int32_t *tickets;     // per i-block arrival counters (zero between launches)
     int32_t *split_used;  // written by the kernel: split factor of this launch
     const Tuning *tune;   // device tuning table
     int32_t force_variant;  // >= 0: ignore the table (autotuner, tests)
@@ -85,6 +87,7 @@ void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_p
 struct StepArgs {
     int64_t n, n_pad;
     double *m, *x, *v, *a, *k, *t, *dt;   // state, vectors [3][n_pad]
+    double *tn;                           // t + dt per particle (the block-selection key)
     JRecs j;                              // mixed records (written by predict)
     double *xp, *vp;                      // FP64 predicted records [3][n_pad]
     int precision;
@@ -94,8 +97,7 @@ struct StepArgs {
     int64_t *s;                           // active count
     double *t_next;                       // block time
     double *t_end;                        // nb_run target
-    const double *part;                   // force partials [s][split][8]
-    const int32_t *split_used;
+    const double *fin;                    // final force sums [s][8]
     int32_t *status;
     int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps
     double *interactions;                 // sum s*n
@@ -110,9 +112,9 @@ cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cu
 cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st);
 cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st);
 cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st);
-cudaError_t launch_reduce_out(const double *part, const int32_t *split_used, const int64_t *s,
-                              int64_t s_host, double *a, double *k, double *phi, int32_t *status,
-                              cudaStream_t st);
+cudaError_t launch_reduce_out(const double *fin, const int64_t *s, int64_t s_host, double *a, double *k,
+                              double *phi, int32_t *status, cudaStream_t st);
+cudaError_t launch_tnext(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
 cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_aos, cudaStream_t st);

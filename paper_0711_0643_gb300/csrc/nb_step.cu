@@ -142,45 +142,60 @@ __global__ void pad_kernel(StepArgs A)
         }
         A.t[i] = CUDART_INF;
         A.dt[i] = CUDART_INF;
+        A.tn[i] = CUDART_INF;
     }
 }
 
+__global__ void tnext_kernel(StepArgs A)
+{
+    for (int64_t i = gtid(); i < A.n; i += gstride()) A.tn[i] = A.t[i] + A.dt[i];
+}
+
 // ---------------------------------------------------------------- selection
-// One CTA: block minimum of t_i + dt_i, then an ordered compaction (each
+// One CTA: block minimum of tn_i = t_i + dt_i, then an ordered compaction (each
 // thread owns a contiguous chunk; an exclusive scan of the chunk counts gives
-// every thread its output offset, so the list comes out ascending).
-__device__ __forceinline__ double warp_min(double v)
+// every thread its output offset, so the list comes out ascending). The keys
+// are non-negative doubles (or +inf for padding), whose bit patterns order
+// like the values, so the comparisons run on the integer pipe.
+__device__ __forceinline__ long long warp_min_ll(long long v)
 {
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    for (int off = 16; off >= 1; off >>= 1) {
+        const long long o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o < v ? o : v;
+    }
     return v;
 }
 
 __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGraphConditionalHandle cond,
                                                              int set_cond)
 {
-    __shared__ double smin[kSelThreads / 32];
+    __shared__ long long smin[kSelThreads / 32];
     __shared__ int scnt[kSelThreads / 32];
-    __shared__ double s_tmin;
+    __shared__ long long s_kmin;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = A.n;
     const int64_t chunk = (n + kSelThreads - 1) / kSelThreads;
     const int64_t b0 = tid * chunk;
     const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-    double m = CUDART_INF;
-    for (int64_t i = b0; i < b1; ++i) m = fmin(m, A.t[i] + A.dt[i]);
-    m = warp_min(m);
+    const long long *key = reinterpret_cast<const long long *>(A.tn);
+    long long m = 0x7ff0000000000000LL;   // +inf
+    for (int64_t i = b0; i < b1; ++i) {
+        const long long k = key[i];
+        m = k < m ? k : m;
+    }
+    m = warp_min_ll(m);
     if (lane == 0) smin[warp] = m;
     __syncthreads();
     if (warp == 0) {
-        double x = lane < kSelThreads / 32 ? smin[lane] : CUDART_INF;
-        x = warp_min(x);
-        if (lane == 0) s_tmin = x;
+        long long x = lane < kSelThreads / 32 ? smin[lane] : 0x7ff0000000000000LL;
+        x = warp_min_ll(x);
+        if (lane == 0) s_kmin = x;
     }
     __syncthreads();
-    const double tmin = s_tmin;
+    const long long kmin = s_kmin;
     int cnt = 0;
-    for (int64_t i = b0; i < b1; ++i) cnt += (A.t[i] + A.dt[i] == tmin);
+    for (int64_t i = b0; i < b1; ++i) cnt += (key[i] == kmin);
     // exclusive scan of cnt over the CTA
     int incl = cnt;
 #pragma unroll
@@ -203,9 +218,10 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     __syncthreads();
     int pos = scnt[warp] + incl - cnt;
     for (int64_t i = b0; i < b1; ++i)
-        if (A.t[i] + A.dt[i] == tmin) A.idx[pos++] = (int32_t)i;
+        if (key[i] == kmin) A.idx[pos++] = (int32_t)i;
     if (tid == kSelThreads - 1) {
         const int64_t s = (int64_t)pos;   // last thread's end offset = total
+        const double tmin = __longlong_as_double(kmin);
         *A.s = s;
         *A.t_next = tmin;
         if (set_cond) {
@@ -219,49 +235,47 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
 
 // ---------------------------------------------------------------- corrector
 
-__device__ __forceinline__ void sum_partials(const double *part, int64_t ii, int S, double *an, double *kn,
-                                             double *phi)
+__device__ __forceinline__ void load_fin(const double *fin, int64_t ii, double *an, double *kn, double *phi)
 {
-    const double *p = part + ii * (int64_t)S * kPartStride;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int sp = 0; sp < S; ++sp)
-#pragma unroll
-        for (int c = 0; c < 7; ++c) acc[c] += p[sp * kPartStride + c];
-    an[0] = acc[0]; an[1] = acc[1]; an[2] = acc[2];
-    kn[0] = acc[3]; kn[1] = acc[4]; kn[2] = acc[5];
-    if (phi) *phi = acc[6];
+    const double *p = fin + ii * kPartStride;
+    an[0] = p[0]; an[1] = p[1]; an[2] = p[2];
+    kn[0] = p[3]; kn[1] = p[4]; kn[2] = p[5];
+    if (phi) *phi = p[6];
 }
 
 __global__ void correct_kernel(StepArgs A, int check_due)
 {
     const int64_t s = *A.s;
     const double tn = *A.t_next;
-    const int S = *A.split_used;
     const int64_t np = A.n_pad;
     int flags = 0;
     for (int64_t ii = gtid(); ii < s; ii += gstride()) {
         const int64_t i = A.idx[ii];
         const double dt = A.dt[i];
-        if (check_due && A.t[i] + dt != tn) {
+        if (check_due && A.tn[i] != tn) {
             flags |= kStState;
             continue;
         }
         double an[3], kn[3];
-        sum_partials(A.part, ii, S, an, kn, nullptr);
+        load_fin(A.fin, ii, an, kn, nullptr);
         double xp[3], vp[3];
         predict_one(A, i, tn, xp, vp);
-        // Hermite corrector, da = a_old - a_new
+        // Hermite corrector, da = a_old - a_new. dt is a power of two, so dividing by
+        // dt, dt^2, dt^3 is the same exact scaling as multiplying by their reciprocals.
         const double dt2 = dt * dt;
         const double dt3 = dt2 * dt;
         const double dt4 = dt3 * dt;
         const double dt5 = dt4 * dt;
+        const double idt = 1.0 / dt;
+        const double idt2 = idt * idt;
+        const double idt3 = idt2 * idt;
         double x1[3], v1[3], a2[3], a3[3], a2p[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double ao = A.a[c * np + i], ko = A.k[c * np + i];
             const double da = ao - an[c];
-            a2[c] = -6.0 * da / dt2 - (4.0 * ko + 2.0 * kn[c]) / dt;
-            a3[c] = 12.0 * da / dt3 + 6.0 * (ko + kn[c]) / dt2;
+            a2[c] = -6.0 * da * idt2 - (4.0 * ko + 2.0 * kn[c]) * idt;
+            a3[c] = 12.0 * da * idt3 + 6.0 * (ko + kn[c]) * idt2;
             x1[c] = xp[c] + a2[c] * dt4 / 24.0 + a3[c] * dt5 / 120.0;
             v1[c] = vp[c] + a2[c] * dt3 / 6.0 + a3[c] * dt4 / 24.0;
         }
@@ -284,6 +298,7 @@ __global__ void correct_kernel(StepArgs A, int check_due)
         }
         A.t[i] = tn;
         A.dt[i] = dt_new;
+        A.tn[i] = tn + dt_new;
     }
     if (flags) atomicOr(A.status, flags);
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
@@ -296,12 +311,11 @@ __global__ void correct_kernel(StepArgs A, int check_due)
 // First steps after the initial full force pass.
 __global__ void init_steps_kernel(StepArgs A)
 {
-    const int S = *A.split_used;
     const int64_t np = A.n_pad;
     int flags = 0;
     for (int64_t i = gtid(); i < A.n; i += gstride()) {
         double an[3], kn[3];
-        sum_partials(A.part, i, S, an, kn, nullptr);
+        load_fin(A.fin, i, an, kn, nullptr);
         bool finite = true;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -314,20 +328,20 @@ __global__ void init_steps_kernel(StepArgs A)
         if (dt == 0.0) flags |= kStUnderflow;
         A.t[i] = 0.0;
         A.dt[i] = dt;
+        A.tn[i] = 0.0 + dt;
     }
     if (flags) atomicOr(A.status, flags);
 }
 
-// Split-sum of the force partials into caller layouts a[s][3], k[s][3], phi[s].
-__global__ void reduce_out_kernel(const double *part, const int32_t *split_used, const int64_t *s_dev,
-                                  int64_t s_host, double *a, double *k, double *phi, int32_t *status)
+// Final force sums into caller layouts a[s][3], k[s][3], phi[s].
+__global__ void reduce_out_kernel(const double *fin, const int64_t *s_dev, int64_t s_host, double *a, double *k,
+                                  double *phi, int32_t *status)
 {
     const int64_t s = s_dev ? *s_dev : s_host;
-    const int S = *split_used;
     int flags = 0;
     for (int64_t ii = gtid(); ii < s; ii += gstride()) {
         double an[3], kn[3], ph;
-        sum_partials(part, ii, S, an, kn, &ph);
+        load_fin(fin, ii, an, kn, &ph);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             if (a) a[ii * 3 + c] = an[c];
@@ -346,7 +360,7 @@ __global__ void check_due_kernel(StepArgs A, double t_block)
     int flags = 0;
     for (int64_t ii = gtid(); ii < s; ii += gstride()) {
         const int64_t i = A.idx[ii];
-        if (A.t[i] + A.dt[i] != t_block) flags |= kStState;
+        if (A.tn[i] != t_block) flags |= kStState;
     }
     if (flags) atomicOr(A.status, flags);
 }
@@ -483,7 +497,14 @@ int grid_for(int64_t n, int threads, int max_grid = 4096)
 
 cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cudaStream_t st)
 {
-    predict_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a, use_t_next ? 1 : 0, t_host);
+    // FP64-heavy: small CTAs so that the work spreads over every SM
+    predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, use_t_next ? 1 : 0, t_host);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tnext(const StepArgs &a, cudaStream_t st)
+{
+    tnext_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -502,7 +523,7 @@ cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_c
 cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st)
 {
     // the grid covers the largest possible block; threads past s exit at once
-    correct_kernel<<<grid_for(a.n, kStepThreads, 1024), kStepThreads, 0, st>>>(a, check_due ? 1 : 0);
+    correct_kernel<<<grid_for(a.n, 64, 2048), 64, 0, st>>>(a, check_due ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -512,11 +533,11 @@ cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_out(const double *part, const int32_t *split_used, const int64_t *s, int64_t s_host,
-                              double *a, double *k, double *phi, int32_t *status, cudaStream_t st)
+cudaError_t launch_reduce_out(const double *fin, const int64_t *s, int64_t s_host, double *a, double *k,
+                              double *phi, int32_t *status, cudaStream_t st)
 {
-    reduce_out_kernel<<<grid_for(s_host > 0 ? s_host : 1, kStepThreads), kStepThreads, 0, st>>>(
-        part, split_used, s, s_host, a, k, phi, status);
+    reduce_out_kernel<<<grid_for(s_host > 0 ? s_host : 1, kStepThreads), kStepThreads, 0, st>>>(fin, s, s_host, a,
+                                                                                               k, phi, status);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,9 @@ def _errors(prec, a, k, phi, ar, kr, pr, A, K):
     """(e_a, e_k, e_phi, forward e_k): the errors the tolerance applies to."""
     ea = rel_errors(a, ar, A)
     ek_fwd = rel_errors(k, kr, K)
-    ek = ek_fwd if prec == 1 else np.linalg.norm(k - kr, axis=1) / K
+    dk = np.linalg.norm(k - kr, axis=1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ek = ek_fwd if prec == 1 else np.where(dk == 0.0, 0.0, dk / K)
     ep = rel_scalar(phi, pr)
     return ea, ek, ep, ek_fwd
 
