@@ -198,6 +198,35 @@ nb_status nb_get_tuning(nb_ctx *ctx, int32_t *variant, int32_t *split);
 int32_t nb_num_variants(const nb_ctx *ctx);
 const char *nb_variant_name(const nb_ctx *ctx, int32_t variant);
 
+/* Largest particle count accepted by nb_force_jerk_static. */
+#define NB_STATIC_MAX_N 65536
+
+/* The mixed-precision force evaluation of nb_force_jerk (same arithmetic and
+ * kernel) for callers that must not allocate device memory: code inside a host
+ * framework that owns the GPU's memory budget through its own pool, plugins
+ * running in another application's CUDA context, and latency-critical loops
+ * that cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart; this is a deployment variant of Eq. (Force).
+ *
+ * No context and no allocation: the caller passes device pointers on the
+ * current device -- m_dev[n], the predicted state x_dev[n][3], v_dev[n][3]
+ * (FP64), the active list idx_dev[s] (int32, strictly ascending, each < n, not
+ * checked) and the outputs a_dev[s][3], k_dev[s][3], phi_dev[s] (any output may
+ * be NULL) -- and a stream (NULL = the legacy default stream). All scratch lives
+ * in one fixed __device__ array of the library (about 11 MiB, held by every GPU
+ * that loads the library until exit), so n is limited to NB_STATIC_MAX_N
+ * (a larger n returns NB_ERR_ARG); the j-split factor is lowered as needed so
+ * that the split partials (s x split entries) fit in 2^16 slots.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make this first call before any stream capture.
+ * Every call reuses the same array and leaves its contents behind, so calls
+ * that overlap on the GPU (other streams, other host threads) race: serialise
+ * them. The call returns after the outputs are written (it synchronises the
+ * stream) and reports NB_ERR_NONFINITE, NB_ERR_TIMEOUT or NB_ERR_CUDA. */
+nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const double *x_dev, const double *v_dev,
+                               double eps2, const int32_t *idx_dev, int64_t s, double *a_dev, double *k_dev,
+                               double *phi_dev, void *stream);
+
 /* Batched ensemble of nc independent systems (Sect. 2.1 applied to each):
  * offsets[nc+1] delimit each system's particles in the concatenated arrays
  * m[N], x[N][3], v[N][3] (host, N = offsets[nc]); eps2[nc] per system. Each

@@ -26,6 +26,7 @@ SOURCES = [
     ("nb_step.cu", ["-fmad=false"]),
     ("nb_api.cu", []),
     ("nb_ensemble.cu", ["-ftz=true"]),
+    ("nb_static.cu", ["-ftz=true"]),
 ]
 
 

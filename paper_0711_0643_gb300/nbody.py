@@ -81,6 +81,7 @@ _SIGS = [
     ("nb_get_tuning", C.c_int, [_P, _P, _P]),
     ("nb_num_variants", C.c_int32, [_P]),
     ("nb_variant_name", C.c_char_p, [_P, _I32]),
+    ("nb_force_jerk_static", C.c_int, [_I64, _P, _P, _P, _D, _P, _I64, _P, _P, _P, _P]),
     ("nb_ensemble_init", C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     ("nb_ensemble_run", C.c_int, [_P, _D]),
     ("nb_ensemble_energy", C.c_int, [_P, _P]),
@@ -275,6 +276,18 @@ def nb_num_variants(ctx) -> int:
 
 def nb_variant_name(ctx, v) -> str:
     return load().nb_variant_name(ctx, int(v)).decode()
+
+
+NB_STATIC_MAX_N = 65536
+
+
+def nb_force_jerk_static(n, m_dev, x_dev, v_dev, eps2, idx_dev, s, a_dev=0, k_dev=0, phi_dev=0, stream=0):
+    """Force evaluation that allocates nothing (device pointers in and out); returns the
+    nb_status code (0 = NB_OK) instead of raising, since there is no context to describe it."""
+    return int(load().nb_force_jerk_static(int(n), C.c_void_p(m_dev), C.c_void_p(x_dev), C.c_void_p(v_dev),
+                                           float(eps2), C.c_void_p(idx_dev or None), int(s),
+                                           C.c_void_p(a_dev or None), C.c_void_p(k_dev or None),
+                                           C.c_void_p(phi_dev or None), C.c_void_p(stream or None)))
 
 
 def nb_ensemble_init(ctx, offsets, m, x, v, eps2):
