@@ -358,6 +358,11 @@ def main_gpu(args):
                 "block_steps": st64["block_steps"]}
         c64.close()
 
+    # ---- batched ensemble: 256 Plummer clusters, one persistent cluster launch to t = 1
+    ens = None
+    if args.ensemble and rank == 0:
+        ens = ensemble_bench(nb, torch, dev, sptr, stream)
+
     # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed, one evaluation per s
     sweep = None
     if args.sweep and rank == 0:
@@ -393,11 +398,54 @@ def main_gpu(args):
             "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / len(e2e_ms)},
             "fp64_gpu": fp64,
+            "ensemble": ens,
             "force_sweep": sweep,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     return 0
+
+
+def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
+    """256 independent Plummer clusters, N_c = round(exp(U[ln 256, ln 8192])) (seeded),
+    eps = 4/N_c, equal masses, each with its own block schedule, advanced to t = 1 by
+    one persistent launch of thread-block clusters (mixed precision)."""
+    import ics
+    members = ics.ensemble(nc, ics.BASE_SEED + 4, n_lo=n_lo, n_hi=n_hi)
+    off = np.zeros(nc + 1, dtype=np.int64)
+    off[1:] = np.cumsum([c.n for c in members])
+    m = np.concatenate([c.m for c in members])
+    x = np.concatenate([c.x for c in members])
+    v = np.concatenate([c.v for c in members])
+    e2 = np.array([c.eps2 for c in members])
+    c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+    # warm-up on a small ensemble (module load, cluster-occupancy query)
+    nb.nb_ensemble_init(c.ctx, off[:3], m[:off[2]], x[:off[2]], v[:off[2]], e2[:2])
+    nb.nb_ensemble_run(c.ctx, 1.0 / 64)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e2v = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+    e1.record(stream)
+    E0 = nb.nb_ensemble_energy(c.ctx, nc)
+    nb.nb_ensemble_run(c.ctx, T_END)
+    e2v.record(stream)
+    torch.cuda.synchronize(dev)
+    E1 = nb.nb_ensemble_energy(c.ctx, nc)
+    bs, ps, inter = nb.nb_ensemble_stats(c.ctx, nc)
+    c.close()
+    run_s = e1.elapsed_time(e2v) / 1e3
+    init_s = e0.elapsed_time(e1) / 1e3
+    dE = np.abs(E1 - E0) / np.abs(E0)
+    total_inter = float(inter.sum()) + float(np.sum(np.diff(off).astype(float) ** 2))
+    return {"workload": f"{nc} Plummer clusters, N log-uniform in [{n_lo}, {n_hi}] (total {int(off[-1])}), eps=4/N, "
+                        f"t=0->{T_END}, one persistent cluster launch",
+            "run_ms": run_s * 1e3, "init_ms": init_s * 1e3,
+            "interactions_per_s": total_inter / (run_s + init_s),
+            "block_steps_per_s": float(bs.sum()) / run_s, "block_steps": int(bs.sum()),
+            "worst_abs_dE_over_E": float(dE.max()), "median_abs_dE_over_E": float(np.median(dE)),
+            "n_min": int(np.diff(off).min()), "n_max": int(np.diff(off).max())}
 
 
 def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
@@ -461,8 +509,14 @@ def main(argv=None):
                     help="integration horizon of one step (default 1; shorter only for profiling runs)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ensemble", action=argparse.BooleanOptionalAction, default=True,
+                    help="batched ensemble of 256 clusters (default on)")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
                     help="full-N force sweep on King N=2^20 (default on)")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="run only the ensemble workload and print it (profiling)")
+    ap.add_argument("--ens-nc", type=int, default=256, help="systems of --ensemble-only")
+    ap.add_argument("--ens-nmax", type=int, default=8192, help="largest system of --ensemble-only")
     ap.add_argument("--sweep-only", action="store_true",
                     help="run only the force sweep and print it (profiling and kernel studies)")
     ap.add_argument("--sweep-n", type=int, default=None, help="particle count of --sweep-only")
@@ -479,7 +533,25 @@ def main(argv=None):
         return run_reference(args)
     if args.sweep_only:
         return main_sweep(args)
+    if args.ensemble_only:
+        return main_ensemble(args)
     return main_gpu(args)
+
+
+def main_ensemble(args):
+    """Only the batched ensemble, printed as one JSON line (not a bench line)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+    out = ensemble_bench(nb, torch, dev, stream.cuda_stream, stream, nc=args.ens_nc, n_hi=args.ens_nmax)
+    print(json.dumps(out))
+    return 0
 
 
 def main_sweep(args):

@@ -160,7 +160,7 @@ nb_status nb_step(nb_ctx *ctx);
 /* Block steps until the next block time exceeds t_end (t_end must be a multiple
  * of dt_max for every particle to land on it). One CUDA-graph launch whose
  * while-node repeats predict -> force -> correct -> select on the device.
- * One call runs at most 2^24 block steps (then NB_ERR_STATE, "block-step cap"). */
+ * One call runs at most 2^22 block steps (then NB_ERR_STATE, "block-step cap"). */
 nb_status nb_run(nb_ctx *ctx, double t_end);
 
 /* Same trajectory as nb_run, driven from the host one block step at a time, with
@@ -229,16 +229,29 @@ nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const double *x_d
 
 /* Batched ensemble of nc independent systems (Sect. 2.1 applied to each):
  * offsets[nc+1] delimit each system's particles in the concatenated arrays
- * m[N], x[N][3], v[N][3] (host, N = offsets[nc]); eps2[nc] per system. Each
- * system keeps its own block schedule. Replaces any single-system state. */
+ * m[N], x[N][3], v[N][3] (host, N = offsets[nc]); eps2[nc] per system, each
+ * system at most 2^19 particles (one thread-block cluster works on a system at
+ * a time). Each system keeps its own block schedule. Computes the
+ * initial forces, first steps and energies (t = 0) on the device. Replaces any
+ * previous ensemble of the context (the single-system state is independent). */
 nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, const double *m,
                            const double *x, const double *v, const double *eps2);
 
-/* Advances every system of the ensemble to t_end in one persistent launch. */
+/* Advances every system of the ensemble to t_end in one persistent launch of
+ * thread-block clusters: each cluster takes whole systems from a queue (largest
+ * first) and runs their block steps with cluster barriers and distributed
+ * shared memory. At most 2^20 block steps per system and call. */
 nb_status nb_ensemble_run(nb_ctx *ctx, double t_end);
 
-/* Per-system energies (E[nc], host) and counters summed over the ensemble. */
+/* Per-system total energies E[nc] (host), computed at the end of the last
+ * nb_ensemble_init (t = 0) or nb_ensemble_run. */
 nb_status nb_ensemble_energy(nb_ctx *ctx, double *E);
+
+/* Per-system counters since nb_ensemble_init (host arrays of length nc, any may
+ * be NULL): block steps, particle steps (sum of s), interactions (sum of s*N). */
+nb_status nb_ensemble_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *particle_steps, double *interactions);
+
+/* Full concatenated state of all systems (view->n = offsets[nc]). */
 nb_status nb_ensemble_get_state(nb_ctx *ctx, nb_state_view *view);
 
 #ifdef __cplusplus

@@ -25,7 +25,7 @@ SOURCES = [
     ("nb_force.cu", ["-ftz=true"]),
     ("nb_step.cu", ["-fmad=false"]),
     ("nb_api.cu", []),
-    ("nb_ensemble.cu", ["-ftz=true"]),
+    ("nb_ensemble.cu", ["-fmad=false", "-ftz=true"]),
     ("nb_static.cu", ["-ftz=true"]),
 ]
 

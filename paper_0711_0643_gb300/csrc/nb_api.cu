@@ -21,6 +21,11 @@
 
 using namespace nb;
 
+struct nb_ensemble;
+namespace nb {
+void ensemble_free(nb_ensemble *e);
+}
+
 struct nb_ctx {
     nb_config cfg{};
     int device = 0;
@@ -44,6 +49,7 @@ struct nb_ctx {
     double *fin = nullptr;          // final force sums [n_pad][8]
     int32_t *tickets = nullptr;     // per i-block arrival counters
     double *tn = nullptr;           // t + dt
+    float2 *x2 = nullptr, *v2 = nullptr, *a2 = nullptr, *k2 = nullptr;   // double-single state copies
     int32_t *split_used = nullptr;
     Tuning *tune_dev = nullptr;
     Tuning tune{};
@@ -68,11 +74,30 @@ struct nb_ctx {
 
     std::string err;
     int inject_pending = 0;
+    nb_ensemble *ens = nullptr;   // batched ensemble state (nb_ensemble.cu)
 };
+
+// Accessors used by the ensemble translation unit.
+nb_ensemble *nb_ctx_ensemble(nb_ctx *ctx) { return ctx->ens; }
+void nb_ctx_set_ensemble(nb_ctx *ctx, nb_ensemble *e)
+{
+    if (ctx->ens && ctx->ens != e) {
+        cudaStreamSynchronize(ctx->stream);
+        nb::ensemble_free(ctx->ens);
+    }
+    ctx->ens = e;
+}
+cudaStream_t nb_ctx_stream(nb_ctx *ctx) { return ctx->stream; }
+const nb_config *nb_ctx_config(nb_ctx *ctx) { return &ctx->cfg; }
+nb_status nb_ctx_fail(nb_ctx *ctx, nb_status st, const char *msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
 
 namespace {
 
-constexpr int64_t kMaxRunSteps = int64_t(1) << 24;   // block steps per nb_run call
+constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
 
 nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
 {
@@ -111,6 +136,7 @@ StepArgs step_args(nb_ctx *c)
     A.n_pad = c->n_pad;
     A.m = c->m; A.x = c->x; A.v = c->v; A.a = c->a; A.k = c->k; A.t = c->t; A.dt = c->dt;
     A.tn = c->tn;
+    A.x2 = c->x2; A.v2 = c->v2; A.a2 = c->a2; A.k2 = c->k2;
     A.j = c->j;
     A.xp = c->xp; A.vp = c->vp;
     A.precision = c->cfg.precision;
@@ -178,9 +204,9 @@ void free_system(nb_ctx *c)
         cudaGraphExecDestroy(c->run_exec);
         c->run_exec = nullptr;
     }
-    void *ptrs[] = {c->m, c->x, c->v, c->a, c->k, c->t, c->dt, c->j.hi, c->j.lo, c->j.vel, c->xp, c->vp,
-                    c->stage, c->idx, c->part, c->fin, c->tickets, c->tn, c->en_scratch, c->out_a, c->out_k,
-                    c->out_phi};
+    void *ptrs[] = {c->m, c->x, c->v, c->a, c->k, c->t, c->dt, c->j.p, c->xp, c->vp,
+                    c->stage, c->idx, c->part, c->fin, c->tickets, c->tn, c->x2, c->v2, c->a2, c->k2, c->en_scratch,
+                    c->out_a, c->out_k, c->out_phi};
     for (void *p : ptrs) dfree(p);
     c->m = c->x = c->v = c->a = c->k = c->t = c->dt = nullptr;
     c->j = JRecs{};
@@ -190,6 +216,7 @@ void free_system(nb_ctx *c)
     c->fin = nullptr;
     c->tickets = nullptr;
     c->tn = nullptr;
+    c->x2 = c->v2 = c->a2 = c->k2 = nullptr;
     c->en_scratch = nullptr;
     c->out_a = c->out_k = c->out_phi = nullptr;
     c->n = c->n_pad = c->n_tiles = 0;
@@ -212,9 +239,7 @@ nb_status alloc_system(nb_ctx *ctx, int64_t n)
     CK(dalloc(&ctx->k, 3 * np));
     CK(dalloc(&ctx->t, np));
     CK(dalloc(&ctx->dt, np));
-    CK(dalloc(&ctx->j.hi, np));
-    CK(dalloc(&ctx->j.lo, np));
-    CK(dalloc(&ctx->j.vel, np));
+    CK(dalloc(&ctx->j.p, np / 2));
     CK(dalloc(&ctx->xp, 3 * np));
     CK(dalloc(&ctx->vp, 3 * np));
     CK(dalloc(&ctx->stage, 3 * np));
@@ -225,6 +250,10 @@ nb_status alloc_system(nb_ctx *ctx, int64_t n)
     CK(dalloc(&ctx->fin, kPartStride * np));
     CK(dalloc(&ctx->tickets, np + 1));
     CK(dalloc(&ctx->tn, np));
+    CK(dalloc(&ctx->x2, 3 * np));
+    CK(dalloc(&ctx->v2, 3 * np));
+    CK(dalloc(&ctx->a2, 3 * np));
+    CK(dalloc(&ctx->k2, 3 * np));
     CK(cudaMemsetAsync(ctx->tickets, 0, (np + 1) * sizeof(int32_t), ctx->stream));
     ctx->en_ctas = (int)((n + 127) / 128);
     CK(dalloc(&ctx->en_scratch, 2 * (size_t)ctx->en_ctas));
@@ -299,6 +328,7 @@ nb_status init_forces(nb_ctx *ctx)
 {
     StepArgs A = step_args(ctx);
     CK(launch_pad_records(A, ctx->stream));
+    CK(launch_state_to_ds(A, ctx->stream));
     CK(launch_predict(A, false, 0.0, ctx->stream));    // t = 0, a = k = 0: records = positions
     CK(launch_fill_iota(ctx->idx, ctx->n, ctx->stream));
     CK(cudaMemcpyAsync(ctx->s, &ctx->n, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -481,6 +511,7 @@ void nb_destroy(nb_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_system(ctx);
+    nb_ctx_set_ensemble(ctx, nullptr);
     void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
                     ctx->counters, ctx->interactions, ctx->en_out, ctx->sel_cnt, ctx->sel_min, ctx->done_ctr};
     for (void *p : ptrs) dfree(p);
@@ -796,6 +827,7 @@ nb_status nb_set_state(nb_ctx *ctx, const nb_state_view *view)
     if ((st = vec(view->a, ctx->a)) != NB_OK) return st;
     if ((st = vec(view->k, ctx->k)) != NB_OK) return st;
     CK(launch_tnext(step_args(ctx), ctx->stream));
+    CK(launch_state_to_ds(step_args(ctx), ctx->stream));
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);

@@ -1,0 +1,86 @@
+// Double-single (float hi + float lo) arithmetic for the mixed-precision
+// predictor: the error-free transformations two-sum (Knuth) and two-product
+// (Dekker, with a fused multiply-add) give ~48-bit sums and products on the
+// FP32 pipe. Including translation units are compiled with -fmad=false, so no
+// a*b+c pattern below is contracted behind our back; every fused multiply-add
+// is an explicit fmaf.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nb {
+
+struct DS {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DS ds_split(double x)
+{
+    const float h = (float)x;
+    return DS{h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ float2 ds_pack(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+// hi + lo renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ DS ds_norm(float s, float e)
+{
+    const float h = s + e;
+    return DS{h, e - (h - s)};
+}
+
+__device__ __forceinline__ DS ds_add(DS x, DS y)
+{
+    const float s = x.hi + y.hi;
+    const float bp = s - x.hi;
+    float e = (x.hi - (s - bp)) + (y.hi - bp);
+    e += x.lo + y.lo;
+    return ds_norm(s, e);
+}
+
+__device__ __forceinline__ DS ds_mul(DS x, DS y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return ds_norm(p, e);
+}
+
+__device__ __forceinline__ DS ds_scale2(DS x, float pow2) { return DS{x.hi * pow2, x.lo * pow2}; }
+
+// Hermite predictor of one particle in double-single for the mixed j-record:
+// xp = x + d (v + d (a/2 + d k/6)) per component (the same polynomial as
+// x + v d + a d^2/2 + k d^3/6, in Horner form), vp = v + d (a + d k/2) in FP32.
+// x2, v2, a2, k2: double-single state [3][np] as float2 (hi, lo).
+__device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, const float2 *a2, const float2 *k2,
+                                           int64_t np, int64_t i, double d64, float4 &hi, float4 &lo, float4 &vel,
+                                           float m)
+{
+    const DS d = ds_split(d64);
+    const DS sixth = {0.166666671633720398f, -4.967053879e-09f};   // 1/6 = hi + lo to ~2^-53
+    const DS d6 = ds_mul(d, sixth);
+    float ph[3], pl[3], pv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 X = x2[c * np + i], V = v2[c * np + i], A = a2[c * np + i], K = k2[c * np + i];
+        DS t = ds_mul(DS{K.x, K.y}, d6);
+        t = ds_add(ds_scale2(DS{A.x, A.y}, 0.5f), t);
+        t = ds_mul(t, d);
+        t = ds_add(DS{V.x, V.y}, t);
+        t = ds_mul(t, d);
+        const DS xp = ds_add(DS{X.x, X.y}, t);
+        ph[c] = xp.hi;
+        pl[c] = xp.lo;
+        pv[c] = (V.x + d.hi * (A.x + d.hi * (0.5f * K.x))) + V.y;
+    }
+    hi = make_float4(ph[0], ph[1], ph[2], m);
+    lo = make_float4(pl[0], pl[1], pl[2], 0.f);
+    vel = make_float4(pv[0], pv[1], pv[2], 0.f);
+}
+
+}  // namespace nb

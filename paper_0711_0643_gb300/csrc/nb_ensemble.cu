@@ -1,19 +1,805 @@
-// Batched ensembles of independent systems (placeholder until the persistent
-// ensemble kernel lands: every entry point reports NB_ERR_STATE).
+// Batched ensembles of independent systems, each with its own block-step
+// schedule (Sect. 2.1 applied to every member), advanced in one persistent
+// launch.
+//
+// Design: the kernel is launched with thread-block clusters of C CTAs (16 where
+// the device allows it, else 8) and one cluster per slot of the GPU. A cluster
+// takes a whole system from an atomic queue (largest first: the host orders
+// the members by N^2) and runs that system's integration to t_end on its own:
+// selection, prediction, force, correction, repeated, with the cluster's CTAs
+// sharing the particles. Cross-CTA exchanges (minimum of t+dt, active counts,
+// error flags) go through distributed shared memory; phases are separated by
+// hardware cluster barriers. Control flow is uniform over the cluster by
+// construction (every decision is taken from values that all CTAs read the
+// same way), so every CTA reaches every barrier; no software spin-wait exists.
+//
+// Force work per block step: with many active particles (s > 1024) each CTA
+// takes a share of them against all of the system's j (no reduction needed);
+// otherwise every CTA takes all of them against a 1/C share of the j, which
+// keeps every CTA's i-blocks full, and the partials are summed in rank order by
+// the CTA that owns each active particle.
+//
+// This file is compiled with -fmad=false (the FP64 corrector must round like
+// the CPU oracle); the FP32 pair arithmetic uses explicit fused multiply-adds.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "nb_ds.cuh"
+#include "nb_hermite.cuh"
 #include "nb_internal.cuh"
+#include "nb_pair.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace nb {
+namespace {
+
+constexpr int kEnsThreads = 256;
+constexpr int kEnsTile = 256;
+constexpr int kEnsSplitMax = 1024;        // j-split (every CTA takes all active i) when s <= this
+constexpr int kEnsPartPerCluster = 16 * kEnsSplitMax;   // C * s_max entries of 8 float2
+constexpr int64_t kEnsMaxN = int64_t(1) << 19;          // largest system one cluster takes
+
+struct EnsArgs {
+    int32_t nc;
+    const int64_t *off;      // [nc + 1]
+    const double *eps2;      // [nc]
+    const int32_t *order;    // [nc] members, largest first
+    int64_t np;              // stride of the SoA vectors (total particles)
+    double *m, *x, *v, *a, *k, *t, *dt, *tn;
+    float2 *x2, *v2, *a2, *k2;   // double-single copies of x, v, a, k
+    float4 *jh, *jl, *jv;    // predicted records
+    int32_t *idx;            // active lists, member segments
+    float2 *part;            // j-split partials, per cluster
+    int32_t *queue;          // next member to take
+    int32_t *ready;          // [nc] 1 once forces and first steps exist
+    int32_t *status;         // [nc] status bits
+    int64_t *steps;          // [nc][2] block steps, particle steps
+    double *inter;           // [nc] interactions
+    double *energy;          // [nc][16][2] K, W per cluster rank after the last launch
+    double t_end, eta, dt_max, dt_min;
+    int64_t max_steps;       // per member and launch
+};
+
+struct EnsSmem {
+    float4 hi[kEnsTile], lo[kEnsTile], vel[kEnsTile];
+    float2 red[kEnsThreads / 32][14];
+    double dred[kEnsThreads / 32][2];
+    long long kmin;
+    int cnt;
+    int err;
+    int member;
+    int wcnt[kEnsThreads / 32];
+    long long wmin[kEnsThreads / 32];
+};
+
+// ------------------------------------------------------------- force (CTA)
+
+// Records of j in [j0, j1) of one member into shared memory, far-away massless
+// padding past j1.
+__device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_t jt, int64_t j1, EnsSmem *sm)
+{
+    const int q = threadIdx.x;
+    const int64_t j = jt + q;
+    if (j < j1) {
+        sm->hi[q] = E.jh[base + j];
+        sm->lo[q] = E.jl[base + j];
+        sm->vel[q] = E.jv[base + j];
+    } else {
+        sm->hi[q] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
+        sm->lo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sm->vel[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+enum { kModeInit = 0, kModeFinal = 1, kModePartial = 2 };
+
+// Forces on the active positions [p0, p1) of list act (member-relative particle
+// indices, ascending) from the member's j in [j0, j1). MODE: kModeInit writes
+// a, k and the first step; kModeFinal runs the corrector; kModePartial stores
+// (hi, lo) partials for rank `rank` in the cluster's partial buffer.
+template <int R, int TJ, int MODE>
+__device__ void cta_force(const EnsArgs &E, int mem, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
+                          int64_t j0, int64_t j1, float eps2f, double tblock, float2 *part, int rank, int64_t s,
+                          EnsSmem *sm, int &flags)
+{
+    constexpr int TI = kEnsThreads / TJ;
+    constexpr int I = TI * R;
+    constexpr int JPT = kEnsTile / TJ;
+    constexpr int CH = JPT < kFoldPairs ? JPT : kFoldPairs;
+    constexpr int kFoldTiles = JPT >= kFoldPairs ? 0 : kFoldPairs / JPT;
+    const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+    for (int64_t pb = p0; pb < p1; pb += I) {
+        const int64_t pe = pb + I < p1 ? pb + I : p1;
+        IPart ip[R];
+        int32_t gi[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t p = pb + (int64_t)r * TI + ti;
+            gi[r] = act[p < pe ? p : pe - 1];
+            float4 h = E.jh[base + gi[r]], l = E.jl[base + gi[r]], w = E.jv[base + gi[r]];
+            ip[r] = IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z};
+        }
+        const int64_t imin = act[pb], imax = act[pe - 1];
+        Acc7 p[R], hi[R], lo[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
+        int fc = 0;
+        for (int64_t jt = j0; jt < j1; jt += kEnsTile) {
+            __syncthreads();
+            load_tile(E, base, jt, j1, sm);
+            __syncthreads();
+            const bool masked = jt <= imax && jt + kEnsTile - 1 >= imin;
+#pragma unroll 1
+            for (int c0 = 0; c0 < JPT; c0 += CH) {
+                if (masked) {
+#pragma unroll 4
+                    for (int q = 0; q < CH; ++q) {
+                        const int jj = tj + (c0 + q) * TJ;
+                        const float4 h = sm->hi[jj], l = sm->lo[jj], w = sm->vel[jj];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) pair_mixed<true>(h, l, w, ip[r], eps2f, p[r], jt + jj == gi[r]);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int q = 0; q < CH; ++q) {
+                        const int jj = tj + (c0 + q) * TJ;
+                        const float4 h = sm->hi[jj], l = sm->lo[jj], w = sm->vel[jj];
+#pragma unroll
+                        for (int r = 0; r < R; ++r) pair_mixed<false>(h, l, w, ip[r], eps2f, p[r], false);
+                    }
+                }
+                if (JPT >= kFoldPairs) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+                }
+            }
+            if (kFoldTiles > 0 && ++fc == kFoldTiles) {
+                fc = 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            fold(hi[r], lo[r], p[r]);
+            if (TJ > 1) ds_group_reduce7<TJ>(hi[r], lo[r]);
+        }
+        if (tj == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int64_t pp = pb + (int64_t)r * TI + ti;
+                if (pp >= pe) continue;
+                if (MODE == kModePartial) {
+                    float2 *dst = part + ((int64_t)rank * s + pp) * kPartStride;
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi[r], c), acc_get(lo[r], c));
+                } else {
+                    double an[3], kn[3];
+                    an[0] = (double)hi[r].ax + (double)lo[r].ax;
+                    an[1] = (double)hi[r].ay + (double)lo[r].ay;
+                    an[2] = (double)hi[r].az + (double)lo[r].az;
+                    kn[0] = (double)hi[r].kx + (double)lo[r].kx;
+                    kn[1] = (double)hi[r].ky + (double)lo[r].ky;
+                    kn[2] = (double)hi[r].kz + (double)lo[r].kz;
+                    const int64_t i = base + gi[r];
+                    if (MODE == kModeInit) {
+                        bool fin = true;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            E.a[c * E.np + i] = an[c];
+                            E.k[c * E.np + i] = kn[c];
+                            E.a2[c * E.np + i] = ds_pack(an[c]);
+                            E.k2[c * E.np + i] = ds_pack(kn[c]);
+                            fin = fin && isfinite(an[c]) && isfinite(kn[c]);
+                        }
+                        const double d0 = initial_step(an, kn, E.eta, E.dt_max, E.dt_min);
+                        if (!fin) flags |= kStNonfinite;
+                        if (d0 == 0.0) flags |= kStUnderflow;
+                        E.t[i] = 0.0;
+                        E.dt[i] = d0;
+                        E.tn[i] = 0.0 + d0;
+                    } else {
+                        flags |= hermite_correct(E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np,
+                                                 i, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Size-adapted dispatch of cta_force.
+template <int MODE>
+__device__ void cta_force_any(const EnsArgs &E, int mem, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
+                              int64_t j0, int64_t j1, float eps2f, double tblock, float2 *part, int rank, int64_t s,
+                              EnsSmem *sm, int &flags)
+{
+    const int64_t ni = p1 - p0;
+    if (ni <= 0) return;
+    if (ni <= 8)
+        cta_force<1, 32, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+    else if (ni <= 64)
+        cta_force<2, 8, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+    else if (ni <= 128)
+        cta_force<2, 4, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+    else if (ni <= 256)
+        cta_force<2, 2, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+    else
+        cta_force<2, 1, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+}
+
+// ---------------------------------------------------------------- phases
+
+__device__ __forceinline__ void predict_chunk(const EnsArgs &E, int64_t base, int64_t c0, int64_t c1, double tblock)
+{
+    for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
+        const int64_t i = base + q;
+        float4 h, l, w;
+        ds_predict(E.x2, E.v2, E.a2, E.k2, E.np, i, tblock - E.t[i], h, l, w, (float)E.m[i]);
+        E.jh[i] = h;
+        E.jl[i] = l;
+        E.jv[i] = w;
+    }
+}
+
+// K and W (softened, FP64) of the member's particles [c0, c1) summed by the CTA.
+__device__ void energy_chunk(const EnsArgs &E, int64_t base, int64_t N, int64_t c0, int64_t c1, double eps2,
+                             EnsSmem *sm, double &K, double &W)
+{
+    double ek = 0.0, ew = 0.0;
+    for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
+        const int64_t i = base + q;
+        const double xi = E.x[i], yi = E.x[E.np + i], zi = E.x[2 * E.np + i];
+        double phi = 0.0;
+        for (int64_t jj = 0; jj < N; ++jj) {
+            const int64_t j = base + jj;
+            const double dx = E.x[j] - xi, dy = E.x[E.np + j] - yi, dz = E.x[2 * E.np + j] - zi;
+            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            phi -= (jj == q) ? 0.0 : E.m[j] * rsqrt(r2);
+        }
+        const double vx = E.v[i], vy = E.v[E.np + i], vz = E.v[2 * E.np + i];
+        ek += 0.5 * E.m[i] * (vx * vx + vy * vy + vz * vz);
+        ew += 0.5 * E.m[i] * phi;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        ek += __shfl_xor_sync(0xffffffffu, ek, off);
+        ew += __shfl_xor_sync(0xffffffffu, ew, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sm->dred[warp][0] = ek;
+        sm->dred[warp][1] = ew;
+    }
+    __syncthreads();
+    K = 0.0;
+    W = 0.0;
+    for (int wv = 0; wv < kEnsThreads / 32; ++wv) {
+        K += sm->dred[wv][0];
+        W += sm->dred[wv][1];
+    }
+    __syncthreads();
+}
+
+__global__ void ens_aos_to_soa(const double *src, double *dst, int64_t n)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 3 * n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[(q % 3) * n + q / 3] = src[q];
+}
+
+__global__ void ens_to_ds(const double *src, float2 *dst, int64_t count)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = ds_pack(src[q]);
+}
+
+__global__ void ens_soa_to_aos(const double *src, double *dst, int64_t n)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 3 * n; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = src[(q % 3) * n + q / 3];
+}
+
+__device__ __forceinline__ long long min_ll(long long a, long long b) { return a < b ? a : b; }
+
+__global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
+{
+    __shared__ EnsSmem smem;
+    EnsSmem *sm = &smem;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 *part = E.part + (int64_t)(blockIdx.x / C) * kEnsPartPerCluster * kPartStride;
+    if (tid == 0) {
+        sm->err = 0;
+        sm->cnt = 0;
+        sm->kmin = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (rank == 0 && tid == 0) sm->member = atomicAdd(E.queue, 1);
+        cluster.sync();
+        const int slot = *cluster.map_shared_rank(&sm->member, 0);
+        cluster.sync();
+        if (slot >= E.nc) break;
+        const int mem = E.order[slot];
+        const int64_t base = E.off[mem];
+        const int64_t N = E.off[mem + 1] - base;
+        const double eps2 = E.eps2[mem];
+        const float eps2f = (float)eps2;
+        const int64_t chunk = (N + C - 1) / C;
+        const int64_t c0 = (int64_t)rank * chunk < N ? (int64_t)rank * chunk : N;
+        const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
+        int32_t *act = E.idx + base;
+        int flags = 0;
+
+        if (!E.ready[mem]) {
+            // initial forces (s = N), first steps, energy at t = 0
+            for (int64_t q = c0 + tid; q < c1; q += kEnsThreads) act[q] = (int32_t)q;
+            predict_chunk(E, base, c0, c1, 0.0);
+            __threadfence();
+            cluster.sync();
+            cta_force_any<kModeInit>(E, mem, base, act, c0, c1, 0, N, eps2f, 0.0, part, rank, N, sm, flags);
+            __threadfence();
+            cluster.sync();
+            if (rank == 0 && tid == 0) {
+                E.ready[mem] = 1;
+                E.steps[2 * mem] = 0;
+                E.steps[2 * mem + 1] = 0;
+                E.inter[mem] = 0.0;
+            }
+        }
+
+        int64_t nsteps = 0;
+        for (;;) {
+            // ---- select: cluster-wide minimum of t + dt, ordered active list
+            const long long *key = reinterpret_cast<const long long *>(E.tn) + base;
+            long long mloc = 0x7ff0000000000000LL;
+            const int64_t sub = (c1 - c0 + kEnsThreads - 1) / kEnsThreads;
+            const int64_t s0 = c0 + tid * sub < c1 ? c0 + tid * sub : c1;
+            const int64_t s1 = s0 + sub < c1 ? s0 + sub : c1;
+            for (int64_t q = s0; q < s1; ++q) mloc = min_ll(mloc, key[q]);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) mloc = min_ll(mloc, __shfl_xor_sync(0xffffffffu, mloc, off));
+            if (lane == 0) sm->wmin[warp] = mloc;
+            __syncthreads();
+            if (tid == 0) {
+                long long mm = sm->wmin[0];
+                for (int wv = 1; wv < kEnsThreads / 32; ++wv) mm = min_ll(mm, sm->wmin[wv]);
+                sm->kmin = mm;
+            }
+            // error flags of the previous step, OR-ed over the CTA
+            if (flags) atomicOr(&sm->err, flags);
+            flags = 0;
+            cluster.sync();
+            long long kmin = 0x7ff0000000000000LL;
+            int err = 0;
+            for (int q = 0; q < C; ++q) {
+                kmin = min_ll(kmin, *cluster.map_shared_rank(&sm->kmin, q));
+                err |= *cluster.map_shared_rank(&sm->err, q);
+            }
+            const double tblock = __longlong_as_double(kmin);
+            int cnt = 0;
+            for (int64_t q = s0; q < s1; ++q) cnt += (key[q] == kmin);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            if (lane == 31) sm->wcnt[warp] = incl;
+            __syncthreads();
+            int wbase = 0, total = 0;
+            for (int wv = 0; wv < kEnsThreads / 32; ++wv) {
+                if (wv < warp) wbase += sm->wcnt[wv];
+                total += sm->wcnt[wv];
+            }
+            if (tid == 0) sm->cnt = total;
+            cluster.sync();
+            int64_t offset = 0, s = 0;
+            for (int q = 0; q < C; ++q) {
+                const int cq = *cluster.map_shared_rank(&sm->cnt, q);
+                if (q < rank) offset += cq;
+                s += cq;
+            }
+            const bool go = (tblock <= E.t_end) && s > 0 && err == 0 && nsteps < E.max_steps;
+            if (!go) {
+                if (rank == 0 && tid == 0) {
+                    if (err) atomicOr(&E.status[mem], err);
+                    if (nsteps >= E.max_steps && tblock <= E.t_end) atomicOr(&E.status[mem], kStSteps);
+                }
+                break;
+            }
+            int pos = (int)offset + wbase + incl - cnt;
+            for (int64_t q = s0; q < s1; ++q)
+                if (key[q] == kmin) act[pos++] = (int32_t)q;
+            // ---- predict every particle of the member to the block time
+            predict_chunk(E, base, c0, c1, tblock);
+            __threadfence();
+            cluster.sync();
+            // ---- force and correction
+            if (s > kEnsSplitMax) {
+                const int64_t share = (s + C - 1) / C;
+                const int64_t p0 = (int64_t)rank * share < s ? (int64_t)rank * share : s;
+                const int64_t p1 = p0 + share < s ? p0 + share : s;
+                cta_force_any<kModeFinal>(E, mem, base, act, p0, p1, 0, N, eps2f, tblock, part, rank, s, sm, flags);
+            } else {
+                const int64_t jc = ((N + C - 1) / C + kEnsTile - 1) / kEnsTile * kEnsTile;
+                const int64_t j0 = (int64_t)rank * jc < N ? (int64_t)rank * jc : N;
+                const int64_t j1 = j0 + jc < N ? j0 + jc : N;
+                if (j1 > j0) {
+                    cta_force_any<kModePartial>(E, mem, base, act, 0, s, j0, j1, eps2f, tblock, part, rank, s, sm,
+                                                flags);
+                } else {
+                    for (int64_t q = tid; q < s * 7; q += kEnsThreads)
+                        part[((int64_t)rank * s + q / 7) * kPartStride + q % 7] = make_float2(0.f, 0.f);
+                }
+                __threadfence();
+                cluster.sync();
+                for (int64_t pp = rank + (int64_t)C * tid; pp < s; pp += (int64_t)C * kEnsThreads) {
+                    float h[7], l[7];
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) { h[c] = 0.f; l[c] = 0.f; }
+                    for (int q = 0; q < C; ++q) {
+                        const float2 *src = part + ((int64_t)q * s + pp) * kPartStride;
+#pragma unroll
+                        for (int c = 0; c < 7; ++c) {
+                            const float2 v = __ldcg(src + c);
+                            ds_add(h[c], l[c], v.x, v.y);
+                        }
+                    }
+                    double an[3], kn[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        an[c] = (double)h[c] + (double)l[c];
+                        kn[c] = (double)h[3 + c] + (double)l[3 + c];
+                    }
+                    flags |= hermite_correct(E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np,
+                                             base + act[pp], tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                }
+            }
+            if (rank == 0 && tid == 0) {
+                E.steps[2 * mem] += 1;
+                E.steps[2 * mem + 1] += s;
+                E.inter[mem] += (double)s * (double)N;
+            }
+            ++nsteps;
+            __threadfence();
+            cluster.sync();
+            if (tid == 0) sm->err = 0;
+        }
+        // ---- energy at the end of this launch
+        __threadfence();
+        cluster.sync();
+        double K, W;
+        energy_chunk(E, base, N, c0, c1, eps2, sm, K, W);
+        if (tid == 0) {
+            E.energy[(mem * 16 + rank) * 2] = K;
+            E.energy[(mem * 16 + rank) * 2 + 1] = W;
+        }
+        if (tid == 0) sm->err = 0;
+        cluster.sync();
+    }
+}
+
+}  // namespace
+}  // namespace nb
+
+// ============================================================== host side
+
+using namespace nb;
+
+struct nb_ensemble {
+    int32_t nc = 0;
+    int64_t ntot = 0;
+    int cluster = 0, nclusters = 0;
+    int64_t *off = nullptr;
+    double *eps2 = nullptr;
+    int32_t *order = nullptr;
+    double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr, *k = nullptr, *t = nullptr, *dt = nullptr,
+           *tn = nullptr;
+    float2 *x2 = nullptr, *v2 = nullptr, *a2 = nullptr, *k2 = nullptr;
+    float4 *jh = nullptr, *jl = nullptr, *jv = nullptr;
+    int32_t *idx = nullptr;
+    float2 *part = nullptr;
+    int32_t *queue = nullptr, *ready = nullptr, *status = nullptr;
+    int64_t *steps = nullptr;
+    double *inter = nullptr, *energy = nullptr;
+    double *stage = nullptr;
+    std::vector<int64_t> off_host;
+};
+
+namespace nb {
+
+void ensemble_free(nb_ensemble *e)
+{
+    if (!e) return;
+    void *ptrs[] = {e->off, e->eps2, e->order, e->m, e->x, e->v, e->a, e->k, e->t, e->dt, e->tn, e->x2, e->v2,
+                    e->a2, e->k2, e->jh, e->jl, e->jv,
+                    e->idx, e->part, e->queue, e->ready, e->status, e->steps, e->inter, e->energy, e->stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete e;
+}
+
+// Chooses the cluster size (16 when allowed, else 8) and the number of clusters
+// that are resident at once.
+static cudaError_t ensemble_shape(int *cluster, int *nclusters)
+{
+    static int c_cached = 0, n_cached = 0;
+    if (c_cached) {
+        *cluster = c_cached;
+        *nclusters = n_cached;
+        return cudaSuccess;
+    }
+    cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int C : {16, 8}) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C * 64);
+        cfg.blockDim = dim3(kEnsThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclu = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclu, ensemble_kernel, &cfg) == cudaSuccess && nclu > 0) {
+            c_cached = C;
+            n_cached = nclu;
+            *cluster = C;
+            *nclusters = nclu;
+            cudaGetLastError();
+            return cudaSuccess;
+        }
+        cudaGetLastError();
+    }
+    return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_max, double dt_min, cudaStream_t st)
+{
+    EnsArgs E{};
+    E.nc = e->nc;
+    E.off = e->off;
+    E.eps2 = e->eps2;
+    E.order = e->order;
+    E.np = e->ntot;
+    E.m = e->m; E.x = e->x; E.v = e->v; E.a = e->a; E.k = e->k; E.t = e->t; E.dt = e->dt; E.tn = e->tn;
+    E.x2 = e->x2; E.v2 = e->v2; E.a2 = e->a2; E.k2 = e->k2;
+    E.jh = e->jh; E.jl = e->jl; E.jv = e->jv;
+    E.idx = e->idx;
+    E.part = e->part;
+    E.queue = e->queue;
+    E.ready = e->ready;
+    E.status = e->status;
+    E.steps = e->steps;
+    E.inter = e->inter;
+    E.energy = e->energy;
+    E.t_end = t_end;
+    E.eta = eta;
+    E.dt_max = dt_max;
+    E.dt_min = dt_min;
+    E.max_steps = int64_t(1) << 20;
+    cudaError_t err = cudaMemsetAsync(e->queue, 0, sizeof(int32_t), st);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(e->energy, 0, 32 * (size_t)e->nc * sizeof(double), st);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = e->cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(e->cluster * e->nclusters);
+    cfg.blockDim = dim3(kEnsThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel, E);
+}
+
+}  // namespace nb
+
+// Glue with the context (defined in nb_api.cu).
+nb_ensemble *nb_ctx_ensemble(nb_ctx *ctx);
+void nb_ctx_set_ensemble(nb_ctx *ctx, nb_ensemble *e);
+cudaStream_t nb_ctx_stream(nb_ctx *ctx);
+const nb_config *nb_ctx_config(nb_ctx *ctx);
+nb_status nb_ctx_fail(nb_ctx *ctx, nb_status st, const char *msg);
+
+namespace nb_ens_host {
+
+template <class T>
+cudaError_t ealloc(T **p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+#define ECK(call)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            std::string m_ = std::string(#call) + ": " + cudaGetErrorString(e_);                      \
+            return nb_ctx_fail(ctx, NB_ERR_CUDA, m_.c_str());                                         \
+        }                                                                                             \
+    } while (0)
+
+nb_status ens_sync(nb_ctx *ctx, nb_ensemble *e)
+{
+    cudaStream_t st = nb_ctx_stream(ctx);
+    ECK(cudaStreamSynchronize(st));
+    std::vector<int32_t> status(e->nc);
+    ECK(cudaMemcpy(status.data(), e->status, e->nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int32_t any = 0;
+    for (int32_t s : status) any |= s;
+    if (!any) return NB_OK;
+    ECK(cudaMemset(e->status, 0, e->nc * sizeof(int32_t)));
+    if (any & kStNonfinite) return nb_ctx_fail(ctx, NB_ERR_NONFINITE, "ensemble: non-finite values");
+    if (any & kStUnderflow) return nb_ctx_fail(ctx, NB_ERR_DT_UNDERFLOW, "ensemble: time step below dt_min");
+    if (any & kStSteps) return nb_ctx_fail(ctx, NB_ERR_STATE, "ensemble: block-step cap reached");
+    return nb_ctx_fail(ctx, NB_ERR_CUDA, "ensemble: device error");
+}
+
+}  // namespace nb_ens_host
+
+using namespace nb_ens_host;
 
 extern "C" {
 
-nb_status nb_ensemble_init(nb_ctx *, int32_t, const int64_t *, const double *, const double *, const double *,
-                           const double *)
+nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, const double *m, const double *x,
+                           const double *v, const double *eps2)
 {
-    return NB_ERR_STATE;
+    if (!ctx) return NB_ERR_ARG;
+    if (nc < 1 || !offsets || !m || !x || !v || !eps2) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: bad arguments");
+    if (offsets[0] != 0) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: offsets[0] must be 0");
+    for (int32_t c = 0; c < nc; ++c) {
+        if (offsets[c + 1] <= offsets[c]) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: empty or unordered system");
+        if (!(eps2[c] >= 0.0) || !std::isfinite(eps2[c])) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: bad eps2");
+    }
+    const int64_t n = offsets[nc];
+    if (n > INT32_MAX) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: too many particles");
+    for (int32_t c = 0; c < nc; ++c)
+        if (offsets[c + 1] - offsets[c] > kEnsMaxN)
+            return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: system too large for one cluster");
+    nb_ctx_set_ensemble(ctx, nullptr);
+    nb_ensemble *e = new nb_ensemble();
+    nb_ctx_set_ensemble(ctx, e);
+    e->nc = nc;
+    e->ntot = n;
+    e->off_host.assign(offsets, offsets + nc + 1);
+    ECK(ensemble_shape(&e->cluster, &e->nclusters));
+    ECK(ealloc(&e->off, nc + 1));
+    ECK(ealloc(&e->eps2, nc));
+    ECK(ealloc(&e->order, nc));
+    ECK(ealloc(&e->m, n));
+    for (double **p : {&e->x, &e->v, &e->a, &e->k}) ECK(ealloc(p, 3 * n));
+    for (double **p : {&e->t, &e->dt, &e->tn}) ECK(ealloc(p, n));
+    for (float2 **p : {&e->x2, &e->v2, &e->a2, &e->k2}) ECK(ealloc(p, 3 * n));
+    for (float4 **p : {&e->jh, &e->jl, &e->jv}) ECK(ealloc(p, n));
+    ECK(ealloc(&e->idx, n));
+    ECK(ealloc(&e->part, (size_t)e->nclusters * kEnsPartPerCluster * kPartStride));
+    ECK(ealloc(&e->queue, 1));
+    ECK(ealloc(&e->ready, nc));
+    ECK(ealloc(&e->status, nc));
+    ECK(ealloc(&e->steps, 2 * nc));
+    ECK(ealloc(&e->inter, nc));
+    ECK(ealloc(&e->energy, 32 * (size_t)nc));
+    ECK(ealloc(&e->stage, 3 * n));
+    cudaStream_t st = nb_ctx_stream(ctx);
+    // longest first: order by N^2 (the force work), ties by index
+    std::vector<int32_t> order(nc);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t p, int32_t q) {
+        return offsets[p + 1] - offsets[p] > offsets[q + 1] - offsets[q];
+    });
+    ECK(cudaMemcpyAsync(e->off, offsets, (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    ECK(cudaMemcpyAsync(e->eps2, eps2, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    ECK(cudaMemcpyAsync(e->order, order.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    ECK(cudaMemcpyAsync(e->m, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    const int blocks = (int)std::min<int64_t>((3 * n + 255) / 256, 4096);
+    ECK(cudaMemcpyAsync(e->stage, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    ens_aos_to_soa<<<blocks, 256, 0, st>>>(e->stage, e->x, n);
+    ECK(cudaStreamSynchronize(st));
+    ECK(cudaMemcpyAsync(e->stage, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    ens_aos_to_soa<<<blocks, 256, 0, st>>>(e->stage, e->v, n);
+    ECK(cudaMemsetAsync(e->a, 0, 3 * n * sizeof(double), st));
+    ECK(cudaMemsetAsync(e->k, 0, 3 * n * sizeof(double), st));
+    ens_to_ds<<<blocks, 256, 0, st>>>(e->x, e->x2, 3 * n);
+    ens_to_ds<<<blocks, 256, 0, st>>>(e->v, e->v2, 3 * n);
+    ECK(cudaMemsetAsync(e->a2, 0, 3 * n * sizeof(float2), st));
+    ECK(cudaMemsetAsync(e->k2, 0, 3 * n * sizeof(float2), st));
+    ECK(cudaMemsetAsync(e->t, 0, n * sizeof(double), st));
+    ECK(cudaMemsetAsync(e->ready, 0, nc * sizeof(int32_t), st));
+    ECK(cudaMemsetAsync(e->status, 0, nc * sizeof(int32_t), st));
+    ECK(cudaMemsetAsync(e->steps, 0, 2 * nc * sizeof(int64_t), st));
+    ECK(cudaMemsetAsync(e->inter, 0, nc * sizeof(double), st));
+    // initial forces, first steps and energies at t = 0: a launch that takes no step
+    const nb_config *cfg = nb_ctx_config(ctx);
+    ECK(ensemble_launch(e, -1.0, cfg->eta, cfg->dt_max, cfg->dt_min, st));
+    return ens_sync(ctx, e);
 }
 
-nb_status nb_ensemble_run(nb_ctx *, double) { return NB_ERR_STATE; }
+nb_status nb_ensemble_run(nb_ctx *ctx, double t_end)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    if (!std::isfinite(t_end)) return nb_ctx_fail(ctx, NB_ERR_ARG, "t_end must be finite");
+    const nb_config *cfg = nb_ctx_config(ctx);
+    ECK(ensemble_launch(e, t_end, cfg->eta, cfg->dt_max, cfg->dt_min, nb_ctx_stream(ctx)));
+    return ens_sync(ctx, e);
+}
 
-nb_status nb_ensemble_energy(nb_ctx *, double *) { return NB_ERR_STATE; }
+nb_status nb_ensemble_energy(nb_ctx *ctx, double *E)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    if (!E) return nb_ctx_fail(ctx, NB_ERR_ARG, "null E");
+    std::vector<double> kw(32 * (size_t)e->nc);
+    ECK(cudaStreamSynchronize(nb_ctx_stream(ctx)));
+    ECK(cudaMemcpy(kw.data(), e->energy, kw.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int32_t c = 0; c < e->nc; ++c) {
+        double K = 0.0, W = 0.0;   // cluster ranks in order
+        for (int q = 0; q < 16; ++q) {
+            K += kw[(c * 16 + q) * 2];
+            W += kw[(c * 16 + q) * 2 + 1];
+        }
+        E[c] = K + W;
+    }
+    return NB_OK;
+}
 
-nb_status nb_ensemble_get_state(nb_ctx *, nb_state_view *) { return NB_ERR_STATE; }
+nb_status nb_ensemble_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *particle_steps, double *interactions)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    std::vector<int64_t> st(2 * e->nc);
+    ECK(cudaStreamSynchronize(nb_ctx_stream(ctx)));
+    ECK(cudaMemcpy(st.data(), e->steps, st.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    for (int32_t c = 0; c < e->nc; ++c) {
+        if (block_steps) block_steps[c] = st[2 * c];
+        if (particle_steps) particle_steps[c] = st[2 * c + 1];
+    }
+    if (interactions) ECK(cudaMemcpy(interactions, e->inter, e->nc * sizeof(double), cudaMemcpyDeviceToHost));
+    return NB_OK;
+}
+
+nb_status nb_ensemble_get_state(nb_ctx *ctx, nb_state_view *view)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    if (!view || view->n != e->ntot) return nb_ctx_fail(ctx, NB_ERR_ARG, "state view size mismatch");
+    cudaStream_t st = nb_ctx_stream(ctx);
+    const int64_t n = e->ntot;
+    const int blocks = (int)std::min<int64_t>((3 * n + 255) / 256, 4096);
+    ECK(cudaStreamSynchronize(st));
+    if (view->m) ECK(cudaMemcpy(view->m, e->m, n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (view->t) ECK(cudaMemcpy(view->t, e->t, n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (view->dt) ECK(cudaMemcpy(view->dt, e->dt, n * sizeof(double), cudaMemcpyDeviceToHost));
+    double *src[4] = {e->x, e->v, e->a, e->k};
+    double *dst[4] = {view->x, view->v, view->a, view->k};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        ens_soa_to_aos<<<blocks, 256, 0, st>>>(src[q], e->stage, n);
+        ECK(cudaMemcpyAsync(dst[q], e->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ECK(cudaStreamSynchronize(st));
+    }
+    return NB_OK;
+}
 
 }  // extern "C"

@@ -19,17 +19,18 @@
 // Mixed precision: positions arrive as double-single (hi, lo) pairs so that
 // r = x_j - x_i keeps ~46 bits even for close pairs (velocities are FP32: the
 // jerk error is set by the FP32 pair arithmetic, not by w); the pair
-// arithmetic is FP32 with one MUFU reciprocal square root; per-thread FP32 partial sums over at most kFoldPairs
+// arithmetic is FP32 on packed f32x2 instructions over the two particles of a
+// pair record, with one MUFU reciprocal square root per particle refined by a
+// Newton step; per-thread FP32 partial sums over at most kFoldPairs
 // pairs are folded into (hi, lo) two-sum accumulators, and the cross-thread
 // reductions combine (hi, lo) pairs with two-sums too (FP64 is a narrow pipe on
 // this part; only the final per-split partial is converted to double).
 #include "nb_internal.cuh"
+#include "nb_pair.cuh"
 
 namespace nb {
 
 namespace {
-
-constexpr int kFoldPairs = 64;     // FP32 terms per partial before a two-sum fold
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -90,134 +91,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_
     return false;
 }
 
-// ---------------------------------------------------------- pair kernels
-
-struct IPart {
-    float xh, yh, zh, xl, yl, zl, vx, vy, vz;
-};
-
-struct Acc7 {
-    float ax, ay, az, kx, ky, kz, ph;
-};
-
-__device__ __forceinline__ void zero(Acc7 &q)
-{
-    q.ax = q.ay = q.az = q.kx = q.ky = q.kz = q.ph = 0.f;
-}
-
-__device__ __forceinline__ IPart load_ipart(const JRecs &J, int32_t i)
-{
-    float4 h = J.hi[i], l = J.lo[i], w = J.vel[i];
-    return IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z};
-}
-
-// One i-j interaction. r = x_j - x_i in double-single, w = v_j - v_i,
-// r2 = |r|^2 + eps^2, q = r2^{-1/2}, mu = m_j q^3, al = 3 (r.w) / r2:
-//   a += mu r,  k += mu (w - al r),  phi -= m_j q.
-// MASK zeroes the term when j == i (self-exclusion by index).
-template <bool MASK>
-__device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &w, const IPart &I,
-                                           float eps2, Acc7 &A, bool self)
-{
-    float dx = (h.x - I.xh) + (l.x - I.xl);
-    float dy = (h.y - I.yh) + (l.y - I.yl);
-    float dz = (h.z - I.zh) + (l.z - I.zl);
-    float wx = w.x - I.vx, wy = w.y - I.vy, wz = w.z - I.vz;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float rw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
-    float q = rsqrtf(r2);
-    if (MASK) q = self ? 0.f : q;
-    float q2 = q * q;
-    float mq = h.w * q;
-    float mu = mq * q2;
-    float al = 3.f * rw * q2;
-    A.ph -= mq;
-    A.ax = fmaf(mu, dx, A.ax);
-    A.ay = fmaf(mu, dy, A.ay);
-    A.az = fmaf(mu, dz, A.az);
-    A.kx = fmaf(mu, fmaf(-al, dx, wx), A.kx);
-    A.ky = fmaf(mu, fmaf(-al, dy, wy), A.ky);
-    A.kz = fmaf(mu, fmaf(-al, dz, wz), A.kz);
-}
-
-// (hi, lo) += p exactly up to the rounding of lo (Knuth's two-sum), p = 0 after.
-__device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float &p)
-{
-    float s = hi + p;
-    float bp = s - hi;
-    float e = (hi - (s - bp)) + (p - bp);
-    hi = s;
-    lo += e;
-    p = 0.f;
-}
-
-__device__ __forceinline__ void fold(Acc7 &hi, Acc7 &lo, Acc7 &p)
-{
-    two_sum_fold(hi.ax, lo.ax, p.ax);
-    two_sum_fold(hi.ay, lo.ay, p.ay);
-    two_sum_fold(hi.az, lo.az, p.az);
-    two_sum_fold(hi.kx, lo.kx, p.kx);
-    two_sum_fold(hi.ky, lo.ky, p.ky);
-    two_sum_fold(hi.kz, lo.kz, p.kz);
-    two_sum_fold(hi.ph, lo.ph, p.ph);
-}
-
-// (hi, lo) + (hi2, lo2) with a two-sum on the high parts.
-__device__ __forceinline__ void ds_add(float &hi, float &lo, float hi2, float lo2)
-{
-    float s = hi + hi2;
-    float bp = s - hi;
-    float e = (hi - (s - bp)) + (hi2 - bp);
-    e += lo + lo2;
-    hi = s + e;                 // renormalise (fast two-sum)
-    lo = e - (hi - s);
-}
-
-// xor-butterfly over the lanes of one group of G consecutive lanes (G | 32)
-template <int G>
-__device__ __forceinline__ void ds_group_reduce(float &hi, float &lo)
-{
-#pragma unroll
-    for (int off = G / 2; off >= 1; off >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
-        ds_add(hi, lo, h2, l2);
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void ds_group_reduce7(Acc7 &hi, Acc7 &lo)
-{
-    ds_group_reduce<G>(hi.ax, lo.ax);
-    ds_group_reduce<G>(hi.ay, lo.ay);
-    ds_group_reduce<G>(hi.az, lo.az);
-    ds_group_reduce<G>(hi.kx, lo.kx);
-    ds_group_reduce<G>(hi.ky, lo.ky);
-    ds_group_reduce<G>(hi.kz, lo.kz);
-    ds_group_reduce<G>(hi.ph, lo.ph);
-}
-
-__device__ __forceinline__ float acc_get(const Acc7 &q, int c)
-{
-    switch (c) {
-    case 0: return q.ax;
-    case 1: return q.ay;
-    case 2: return q.az;
-    case 3: return q.kx;
-    case 4: return q.ky;
-    case 5: return q.kz;
-    default: return q.ph;
-    }
-}
-
 // ------------------------------------------------------------ shared memory
 
 constexpr int kMaxRC = 2 * 7;   // R * components, largest R over variants
 
+constexpr int kPT = kJT / 2;    // pair records per tile
+
 struct __align__(128) Smem {
-    float4 hi[kStages][kJT];
-    float4 lo[kStages][kJT];
-    float4 vel[kStages][kJT];
+    JPair tile[kStages][kPT];
     float2 red[kThreads / 32][kMaxRC];
     uint64_t bar[kStages];
     uint64_t inject_bar;
@@ -275,16 +156,35 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
         const int64_t ib0 = bx * I;
         const int64_t ib1 = ib0 + I < s ? ib0 + I : s;
         const int64_t cnt = (ib1 - ib0) * 7;
-        for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
-            const int64_t ii = ib0 + q / 7;
-            const int c = (int)(q % 7);
-            const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
-            float h = 0.f, l = 0.f;
-            for (int sp = 0; sp < S; ++sp) {
-                const float2 v = __ldcg(src + sp * kPartStride);
-                ds_add(h, l, v.x, v.y);
+        if (S <= 4) {
+            // few splits: one thread per (particle, component)
+            for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
+                const int64_t ii = ib0 + q / 7;
+                const int c = (int)(q % 7);
+                const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
+                float h = 0.f, l = 0.f;
+                for (int sp = 0; sp < S; ++sp) {
+                    const float2 v = __ldcg(src + sp * kPartStride);
+                    ds_add(h, l, v.x, v.y);
+                }
+                A.fin[ii * kPartStride + c] = (double)h + (double)l;
             }
-            A.fin[ii * kPartStride + c] = (double)h + (double)l;
+        } else {
+            // many splits: one warp per (particle, component); lanes stride over the
+            // splits and a fixed butterfly of two-sums combines them
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            for (int64_t q = warp; q < cnt; q += kThreads / 32) {
+                const int64_t ii = ib0 + q / 7;
+                const int c = (int)(q % 7);
+                const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
+                float h = 0.f, l = 0.f;
+                for (int sp = lane; sp < S; sp += 32) {
+                    const float2 v = __ldcg(src + sp * kPartStride);
+                    ds_add(h, l, v.x, v.y);
+                }
+                ds_group_reduce<32>(h, l);
+                if (lane == 0) A.fin[ii * kPartStride + c] = (double)h + (double)l;
+            }
         }
         if (threadIdx.x == 0) A.tickets[bx] = 0;
     }
@@ -293,33 +193,37 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
 
 // ------------------------------------------------------- streamed variant
 // TI = 1: all threads share the same R i-particles; each thread walks its own
-// j's straight from global memory (coalesced float4 loads), so no shared
-// staging is needed. For small active blocks.
+// pair records straight from global memory (coalesced float4 loads), so no
+// shared staging is needed. For small active blocks.
 template <int R>
 __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    IPart ip[R];
+    IPk ip[R];
     int32_t gi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int64_t ii = bx * R + r;
         gi[r] = A.idx[ii < s ? ii : s - 1];
-        ip[r] = load_ipart(A.j, gi[r]);
+        ip[r] = ipk_of(jrec_load(A.j.p, gi[r]));
     }
+    const float2 e2 = make_float2(A.eps2f, A.eps2f);
     const int64_t tper = (A.n_tiles + S - 1) / S;
     const int64_t t0 = (int64_t)by * tper;
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
-    const int64_t j0 = t0 * kJT, j1 = t1 * kJT;
-    Acc7 p[R], hi[R], lo[R];
+    const int64_t p0 = t0 * kPT, p1 = t1 * kPT;
+    AccPk p[R];
+    Acc7 hi[R], lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
     int cnt = 0;
-    for (int64_t j = j0 + tid; j < j1; j += kThreads) {
-        float4 h = __ldg(&A.j.hi[j]), l = __ldg(&A.j.lo[j]), w = __ldg(&A.j.vel[j]);
+    for (int64_t pp = p0 + tid; pp < p1; pp += kThreads) {
+        const float4 *q = A.j.p[pp].q;
+        const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3), q4 = __ldg(q + 4);
 #pragma unroll
-        for (int r = 0; r < R; ++r) pair_mixed<true>(h, l, w, ip[r], A.eps2f, p[r], j == gi[r]);
-        if (++cnt == kFoldPairs) {
+        for (int r = 0; r < R; ++r)
+            pair_packed<true>(q0, q1, q2, q3, q4, ip[r], e2, p[r], 2 * pp == gi[r], 2 * pp + 1 == gi[r]);
+        if (++cnt == kFoldPairs / 2) {
             cnt = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
@@ -350,27 +254,27 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
 
 // ----------------------------------------------------------- tiled variant
 // TI = kThreads / TJ thread groups, each holding R i-particles; the TJ threads
-// of a group take interleaved j's of each shared-memory tile.
+// of a group take interleaved pair records of each shared-memory tile.
 template <int R, int TJ, bool MASK>
-__device__ __forceinline__ void sweep_tile(const Smem *sm, int st, int tj, int64_t j0, const IPart *ip,
-                                           const int32_t *gi, float eps2, Acc7 *p, Acc7 *hi, Acc7 *lo)
+__device__ __forceinline__ void sweep_tile(const Smem *sm, int st, int tj, int64_t j0, const IPk *ip,
+                                           const int32_t *gi, float2 e2, AccPk *p, Acc7 *hi, Acc7 *lo)
 {
-    constexpr int JPT = kJT / TJ;                          // j's per thread per tile
-    constexpr int CH = JPT < kFoldPairs ? JPT : kFoldPairs;
-    const float4 *H = sm->hi[st];
-    const float4 *L = sm->lo[st];
-    const float4 *V = sm->vel[st];
+    constexpr int PPT = kPT / TJ;                           // pair records per thread per tile
+    constexpr int FP = kFoldPairs / 2;                      // records per fold
+    constexpr int CH = PPT < FP ? PPT : FP;
+    const JPair *T = sm->tile[st];
 #pragma unroll 1
-    for (int c0 = 0; c0 < JPT; c0 += CH) {
+    for (int c0 = 0; c0 < PPT; c0 += CH) {
 #pragma unroll 4
-        for (int q = 0; q < CH; ++q) {
-            const int jj = tj + (c0 + q) * TJ;
-            float4 h = H[jj], l = L[jj], w = V[jj];
-            const int64_t jg = j0 + jj;
+        for (int u = 0; u < CH; ++u) {
+            const int pp = tj + (c0 + u) * TJ;
+            const float4 q0 = T[pp].q[0], q1 = T[pp].q[1], q2 = T[pp].q[2], q3 = T[pp].q[3], q4 = T[pp].q[4];
+            const int64_t ja = j0 + 2 * pp;
 #pragma unroll
-            for (int r = 0; r < R; ++r) pair_mixed<MASK>(h, l, w, ip[r], eps2, p[r], MASK && jg == gi[r]);
+            for (int r = 0; r < R; ++r)
+                pair_packed<MASK>(q0, q1, q2, q3, q4, ip[r], e2, p[r], MASK && ja == gi[r], MASK && ja + 1 == gi[r]);
         }
-        if (JPT >= kFoldPairs) {
+        if (PPT >= FP) {
 #pragma unroll
             for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
         }
@@ -379,12 +283,9 @@ __device__ __forceinline__ void sweep_tile(const Smem *sm, int st, int tj, int64
 
 __device__ __forceinline__ void issue_tile(const ForceArgs &A, Smem *sm, int64_t tile, int st)
 {
-    constexpr uint32_t bytes = kJT * sizeof(float4);
-    mbar_arrive_expect_tx(&sm->bar[st], 3 * bytes);
-    const int64_t j0 = tile * kJT;
-    bulk_g2s(sm->hi[st], A.j.hi + j0, bytes, &sm->bar[st]);
-    bulk_g2s(sm->lo[st], A.j.lo + j0, bytes, &sm->bar[st]);
-    bulk_g2s(sm->vel[st], A.j.vel + j0, bytes, &sm->bar[st]);
+    constexpr uint32_t bytes = kPT * sizeof(JPair);
+    mbar_arrive_expect_tx(&sm->bar[st], bytes);
+    bulk_g2s(sm->tile[st], A.j.p + tile * kPT, bytes, &sm->bar[st]);
 }
 
 template <int R, int TJ>
@@ -392,19 +293,20 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 {
     constexpr int TI = kThreads / TJ;
     constexpr int I = TI * R;
-    constexpr int JPT = kJT / TJ;
-    constexpr int kFoldTiles = JPT >= kFoldPairs ? 0 : kFoldPairs / JPT;   // 0: folded inside the sweep
+    constexpr int PPT = kPT / TJ;
+    constexpr int kFoldTiles = PPT >= kFoldPairs / 2 ? 0 : (kFoldPairs / 2) / PPT;   // 0: folded inside the sweep
     static_assert(TJ <= 32 && (32 % TJ) == 0, "TJ must divide a warp");
     const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
 
-    IPart ip[R];
+    IPk ip[R];
     int32_t gi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int64_t ii = bx * I + (int64_t)r * TI + ti;
         gi[r] = A.idx[ii < s ? ii : s - 1];
-        ip[r] = load_ipart(A.j, gi[r]);
+        ip[r] = ipk_of(jrec_load(A.j.p, gi[r]));
     }
+    const float2 e2 = make_float2(A.eps2f, A.eps2f);
     // index range of this i-block (the active list ascends), for self-exclusion
     const int64_t ib0 = bx * I;
     const int64_t ib1 = (ib0 + I < s ? ib0 + I : s) - 1;
@@ -415,7 +317,8 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
 
-    Acc7 p[R], hi[R], lo[R];
+    AccPk p[R];
+    Acc7 hi[R], lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
 
@@ -432,9 +335,9 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
         if (!mbar_wait(&sm->bar[st], (g / kStages) & 1u, A.spin_limit)) sm->abort = 1;
         const int64_t j0 = (t0 + q) * kJT;
         if (j0 <= imax && j0 + kJT - 1 >= imin)
-            sweep_tile<R, TJ, true>(sm, st, tj, j0, ip, gi, A.eps2f, p, hi, lo);
+            sweep_tile<R, TJ, true>(sm, st, tj, j0, ip, gi, e2, p, hi, lo);
         else
-            sweep_tile<R, TJ, false>(sm, st, tj, j0, ip, gi, A.eps2f, p, hi, lo);
+            sweep_tile<R, TJ, false>(sm, st, tj, j0, ip, gi, e2, p, hi, lo);
         if (kFoldTiles > 0 && ++fc == kFoldTiles) {
             fc = 0;
 #pragma unroll
@@ -467,16 +370,16 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 
 // -------------------------------------------------------------- variants
 
-// 0: stream R=1 (I=1)      1: stream R=2 (I=2)      2: tile R=2 TJ=32 (I=16)
-// 3: tile R=2 TJ=8 (I=64)  4: tile R=2 TJ=1 (I=512)
+// 0: stream R=1 (I=1)      1: stream R=2 (I=2)      2: tile R=1 TJ=32 (I=8)
+// 3: tile R=1 TJ=8 (I=32)  4: tile R=1 TJ=1 (I=256)
 __host__ __device__ __forceinline__ int mixed_I(int v)
 {
     switch (v) {
     case 0: return 1;
     case 1: return 2;
-    case 2: return 16;
-    case 3: return 64;
-    default: return 512;
+    case 2: return 8;
+    case 3: return 32;
+    default: return 256;
     }
 }
 
@@ -522,9 +425,9 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         switch (variant) {
         case 0: work_stream<1>(A, s, bx, by, S, sm); break;
         case 1: work_stream<2>(A, s, bx, by, S, sm); break;
-        case 2: work_tile<2, 32>(A, s, bx, by, S, sm, git); break;
-        case 3: work_tile<2, 8>(A, s, bx, by, S, sm, git); break;
-        default: work_tile<2, 1>(A, s, bx, by, S, sm, git); break;
+        case 2: work_tile<1, 32>(A, s, bx, by, S, sm, git); break;
+        case 3: work_tile<1, 8>(A, s, bx, by, S, sm, git); break;
+        default: work_tile<1, 1>(A, s, bx, by, S, sm, git); break;
         }
         if (sm->abort) {
             if (tid == 0) atomicOr(A.status, kStTimeout);
@@ -699,9 +602,9 @@ const char *mixed_variant_name(int v)
     switch (v) {
     case 0: return "stream R=1";
     case 1: return "stream R=2";
-    case 2: return "tile R=2 TJ=32";
-    case 3: return "tile R=2 TJ=8";
-    case 4: return "tile R=2 TJ=1";
+    case 2: return "tile R=1 TJ=32";
+    case 3: return "tile R=1 TJ=8";
+    case 4: return "tile R=1 TJ=1";
     default: return "?";
     }
 }
@@ -763,11 +666,11 @@ void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_p
         v = s <= 64 ? 0 : 1;
     } else if (s <= 1) {
         v = 0;
-    } else if (s <= 8) {
+    } else if (s <= 4) {
         v = 1;
-    } else if (s <= 128) {
+    } else if (s <= 32) {
         v = 2;
-    } else if (s <= 2048) {
+    } else if (s <= 512) {
         v = 3;
     } else {
         v = 4;

@@ -25,12 +25,20 @@ constexpr int kStSteps = 16;         // block-step cap reached inside nb_run
 
 // ------------------------------------------------------------- force kernels
 
-// Mixed-precision j-record, 48 bytes: predicted position split into
-// hi = fl32(x) and lo = fl32(x - hi) (double-single), velocity and mass in FP32.
+// Mixed-precision j-records, two particles per 80-byte record (j = 2p, 2p+1),
+// interleaved so that every float4 holds two (j = 2p, j = 2p+1) pairs of one
+// quantity -- the operand layout of the packed f32x2 instructions:
+//   q[0] = (x_hi, x_hi', y_hi, y_hi')   q[1] = (z_hi, z_hi', m, m')
+//   q[2] = (x_lo, x_lo', y_lo, y_lo')   q[3] = (z_lo, z_lo', vx, vx')
+//   q[4] = (vy, vy', vz, vz')
+// with x_hi = fl32(x), x_lo = fl32(x - x_hi) (double-single position), FP32
+// velocity and mass. Arrays hold n_pad / 2 records.
+struct JPair {
+    float4 q[5];
+};
+
 struct JRecs {
-    float4 *hi;   // (x_hi, y_hi, z_hi, m)
-    float4 *lo;   // (x_lo, y_lo, z_lo, 0)
-    float4 *vel;  // (vx, vy, vz, 0)
+    JPair *p;
 };
 
 struct Tuning {
@@ -88,6 +96,7 @@ struct StepArgs {
     int64_t n, n_pad;
     double *m, *x, *v, *a, *k, *t, *dt;   // state, vectors [3][n_pad]
     double *tn;                           // t + dt per particle (the block-selection key)
+    float2 *x2, *v2, *a2, *k2;            // double-single copies of x, v, a, k [3][n_pad]
     JRecs j;                              // mixed records (written by predict)
     double *xp, *vp;                      // FP64 predicted records [3][n_pad]
     int precision;
@@ -115,6 +124,7 @@ cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_reduce_out(const double *fin, const int64_t *s, int64_t s_host, double *a, double *k,
                               double *phi, int32_t *status, cudaStream_t st);
 cudaError_t launch_tnext(const StepArgs &a, cudaStream_t st);
+cudaError_t launch_state_to_ds(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
 cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_aos, cudaStream_t st);

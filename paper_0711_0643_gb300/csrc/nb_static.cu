@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "nb_internal.cuh"
+#include "nb_pair.cuh"
 
 namespace nb {
 namespace {
@@ -26,10 +27,8 @@ constexpr int64_t kStaticPad = kStaticTiles * kJT;
 constexpr int64_t kStaticPartWords = int64_t(1) << 19;   // split partials: 4 MiB
 
 // byte offsets inside the array (all multiples of 256)
-constexpr size_t kOffHi = 0;
-constexpr size_t kOffLo = kOffHi + kStaticPad * sizeof(float4);
-constexpr size_t kOffVel = kOffLo + kStaticPad * sizeof(float4);
-constexpr size_t kOffPart = kOffVel + kStaticPad * sizeof(float4);
+constexpr size_t kOffRec = 0;
+constexpr size_t kOffPart = kOffRec + (kStaticPad / 2) * sizeof(JPair);
 constexpr size_t kOffFin = kOffPart + kStaticPartWords * 8;
 constexpr size_t kOffTickets = kOffFin + kStaticPad * kPartStride * sizeof(double);
 constexpr size_t kOffS = kOffTickets + ((kStaticPad + 1) * sizeof(int32_t) + 255) / 256 * 256;
@@ -48,9 +47,7 @@ unsigned char *g_addr[256] = {};
 __global__ void static_setup_kernel(const double *m, const double *x, const double *v, int64_t n, int64_t s,
                                     unsigned char *base)
 {
-    float4 *hi = reinterpret_cast<float4 *>(base + kOffHi);
-    float4 *lo = reinterpret_cast<float4 *>(base + kOffLo);
-    float4 *vel = reinterpret_cast<float4 *>(base + kOffVel);
+    JPair *rec = reinterpret_cast<JPair *>(base + kOffRec);
     int32_t *tickets = reinterpret_cast<int32_t *>(base + kOffTickets);
     const int64_t npad = (n + kJT - 1) / kJT * kJT;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -58,13 +55,10 @@ __global__ void static_setup_kernel(const double *m, const double *x, const doub
         if (i < n) {
             const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
             const float hx = (float)px, hy = (float)py, hz = (float)pz;
-            hi[i] = make_float4(hx, hy, hz, (float)m[i]);
-            lo[i] = make_float4((float)(px - (double)hx), (float)(py - (double)hy), (float)(pz - (double)hz), 0.f);
-            vel[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f);
+            jrec_store(rec, i, hx, hy, hz, (float)m[i], (float)(px - (double)hx), (float)(py - (double)hy),
+                       (float)(pz - (double)hz), (float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2]);
         } else {
-            hi[i] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-            lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            jrec_store(rec, i, 1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
         }
         tickets[i] = 0;
     }
@@ -122,9 +116,7 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     ForceArgs F{};
     F.n = n;
     F.n_tiles = n_tiles;
-    F.j.hi = reinterpret_cast<float4 *>(base + kOffHi);
-    F.j.lo = reinterpret_cast<float4 *>(base + kOffLo);
-    F.j.vel = reinterpret_cast<float4 *>(base + kOffVel);
+    F.j.p = reinterpret_cast<JPair *>(base + kOffRec);
     F.eps2f = (float)eps2;
     F.eps2 = eps2;
     F.idx = idx_dev;

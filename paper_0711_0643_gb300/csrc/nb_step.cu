@@ -9,7 +9,10 @@
 // without fused multiply-adds.
 #include <math_constants.h>
 
+#include "nb_ds.cuh"
+#include "nb_hermite.cuh"
 #include "nb_internal.cuh"
+#include "nb_pair.cuh"
 
 namespace nb {
 
@@ -21,79 +24,10 @@ constexpr int kSelThreads = 1024;
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-__device__ __forceinline__ double dot3(double ux, double uy, double uz, double wx, double wy, double wz)
-{
-    return ux * wx + uy * wy + uz * wz;
-}
-
-// largest power of two <= x for finite x > 0
-__device__ __forceinline__ double pow2_floor(double x)
-{
-    int e;
-    (void)frexp(x, &e);
-    return ldexp(1.0, e - 1);
-}
-
-// Power-of-two step rule: drop to the largest power of two below the candidate;
-// double (once) only at times commensurate with twice the old step and within
-// dt_max; otherwise keep. 0 means "below dt_min or no valid candidate".
-__device__ double quantise(double cand, double dt_old, double t_new, double dt_max, double dt_min)
-{
-    if (!(cand > 0.0)) return 0.0;
-    const double q = isinf(cand) ? CUDART_INF : pow2_floor(cand);
-    double dt;
-    const double dt2 = 2.0 * dt_old;
-    if (q < dt_old) {
-        dt = q;
-    } else if (q >= dt2 && dt2 <= dt_max) {
-        const double u = t_new / dt2;
-        dt = (u == floor(u)) ? dt2 : dt_old;
-    } else {
-        dt = dt_old;
-    }
-    if (dt > dt_max) dt = dt_max;
-    if (dt < dt_min) return 0.0;
-    return dt;
-}
-
-// Eq. (timestep): sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| + |a2p|^2)); den = 0 sets no limit.
-__device__ double aarseth(const double *an, const double *kn, const double *a2p, const double *a3, double eta)
-{
-    const double amag = sqrt(dot3(an[0], an[1], an[2], an[0], an[1], an[2]));
-    const double kmag = sqrt(dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]));
-    const double a2mag = sqrt(dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]));
-    const double a3mag = sqrt(dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]));
-    const double num = amag * a2mag + dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]);
-    const double den = kmag * a3mag + dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]);
-    if (den == 0.0) return CUDART_INF;
-    return sqrt(eta * num / den);
-}
-
-__device__ double initial_step(const double *a, const double *k, double eta, double dt_max, double dt_min)
-{
-    const double amag = sqrt(dot3(a[0], a[1], a[2], a[0], a[1], a[2]));
-    const double kmag = sqrt(dot3(k[0], k[1], k[2], k[0], k[1], k[2]));
-    const double cand = (kmag > 0.0) ? eta * amag / kmag : CUDART_INF;
-    if (!(cand > 0.0)) return 0.0;
-    double dt = isinf(cand) ? dt_max : pow2_floor(cand);
-    if (dt > dt_max) dt = dt_max;
-    if (dt < dt_min) return 0.0;
-    return dt;
-}
-
 // Predicted position/velocity of particle i at time tn (Hermite predictor).
 __device__ __forceinline__ void predict_one(const StepArgs &A, int64_t i, double tn, double *xp, double *vp)
 {
-    const int64_t np = A.n_pad;
-    const double d = tn - A.t[i];
-    const double d2 = d * d;
-    const double d3 = d2 * d;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int64_t q = c * np + i;
-        xp[c] = A.x[q] + A.v[q] * d + A.a[q] * d2 / 2.0 + A.k[q] * d3 / 6.0;
-        vp[c] = A.v[q] + A.a[q] * d + A.k[q] * d2 / 2.0;
-    }
+    hermite_predict(A.x, A.v, A.a, A.k, A.t, A.n_pad, i, tn, xp, vp);
 }
 
 // The far-away, massless record used to pad the j arrays to whole tiles.
@@ -104,17 +38,14 @@ __global__ void predict_kernel(StepArgs A, int use_t_next, double t_host)
     const double tn = use_t_next ? *A.t_next : t_host;
     const int64_t np = A.n_pad;
     for (int64_t i = gtid(); i < A.n; i += gstride()) {
-        double xp[3], vp[3];
-        predict_one(A, i, tn, xp, vp);
         if (A.precision == NB_PREC_MIXED) {
-            float hx = (float)xp[0], hy = (float)xp[1], hz = (float)xp[2];
-            float lx = (float)(xp[0] - (double)hx);
-            float ly = (float)(xp[1] - (double)hy);
-            float lz = (float)(xp[2] - (double)hz);
-            A.j.hi[i] = make_float4(hx, hy, hz, (float)A.m[i]);
-            A.j.lo[i] = make_float4(lx, ly, lz, 0.f);
-            A.j.vel[i] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+            // double-single Horner on the FP32 pipe (FP64 is a narrow pipe on this part)
+            float4 h, l, w;
+            ds_predict(A.x2, A.v2, A.a2, A.k2, np, i, tn - A.t[i], h, l, w, (float)A.m[i]);
+            jrec_store(A.j.p, i, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
         } else {
+            double xp[3], vp[3];
+            predict_one(A, i, tn, xp, vp);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 A.xp[c * np + i] = xp[c];
@@ -128,9 +59,7 @@ __global__ void pad_kernel(StepArgs A)
 {
     const int64_t np = A.n_pad;
     for (int64_t i = A.n + gtid(); i < np; i += gstride()) {
-        A.j.hi[i] = make_float4((float)kPadPos, (float)kPadPos, (float)kPadPos, 0.f);
-        A.j.lo[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        A.j.vel[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        jrec_store(A.j.p, i, (float)kPadPos, (float)kPadPos, (float)kPadPos, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
         A.m[i] = 0.0;
         for (int c = 0; c < 3; ++c) {
             A.xp[c * np + i] = kPadPos;
@@ -151,12 +80,28 @@ __global__ void tnext_kernel(StepArgs A)
     for (int64_t i = gtid(); i < A.n; i += gstride()) A.tn[i] = A.t[i] + A.dt[i];
 }
 
+// Double-single copies of the FP64 state (after uploads and state changes).
+__global__ void state_to_ds_kernel(StepArgs A)
+{
+    const int64_t np = A.n_pad;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t q = c * np + i;
+            A.x2[q] = ds_pack(A.x[q]);
+            A.v2[q] = ds_pack(A.v[q]);
+            A.a2[q] = ds_pack(A.a[q]);
+            A.k2[q] = ds_pack(A.k[q]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- selection
-// One CTA: block minimum of tn_i = t_i + dt_i, then an ordered compaction (each
-// thread owns a contiguous chunk; an exclusive scan of the chunk counts gives
-// every thread its output offset, so the list comes out ascending). The keys
-// are non-negative doubles (or +inf for padding), whose bit patterns order
-// like the values, so the comparisons run on the integer pipe.
+// One CTA of 1024 threads. Keys tn_i = t_i + dt_i are non-negative doubles (+inf
+// for padding) whose bit patterns order like the values, so all comparisons run
+// on the integer pipe. Pass 1: coalesced minimum. Pass 2: ordered compaction in
+// rounds of 1024 consecutive keys (warp ballots, then a scan of the 32 warp
+// counts), so the active list comes out ascending.
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
 #pragma unroll
@@ -171,19 +116,29 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
                                                              int set_cond)
 {
     __shared__ long long smin[kSelThreads / 32];
-    __shared__ int scnt[kSelThreads / 32];
+    __shared__ int woff[kSelThreads / 32];
+    __shared__ int wtot;
     __shared__ long long s_kmin;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = A.n;
-    const int64_t chunk = (n + kSelThreads - 1) / kSelThreads;
-    const int64_t b0 = tid * chunk;
-    const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
-    long long m = 0x7ff0000000000000LL;   // +inf
-    for (int64_t i = b0; i < b1; ++i) {
-        const long long k = key[i];
-        m = k < m ? k : m;
+    long long m0 = 0x7ff0000000000000LL, m1 = m0, m2 = m0, m3 = m0;   // +inf
+    int64_t i = tid;
+    for (; i + 3 * kSelThreads < n; i += 4 * kSelThreads) {
+        const long long k0 = key[i], k1 = key[i + kSelThreads], k2 = key[i + 2 * kSelThreads],
+                        k3 = key[i + 3 * kSelThreads];
+        m0 = k0 < m0 ? k0 : m0;
+        m1 = k1 < m1 ? k1 : m1;
+        m2 = k2 < m2 ? k2 : m2;
+        m3 = k3 < m3 ? k3 : m3;
     }
+    for (; i < n; i += kSelThreads) {
+        const long long k0 = key[i];
+        m0 = k0 < m0 ? k0 : m0;
+    }
+    m0 = m1 < m0 ? m1 : m0;
+    m2 = m3 < m2 ? m3 : m2;
+    long long m = m2 < m0 ? m2 : m0;
     m = warp_min_ll(m);
     if (lane == 0) smin[warp] = m;
     __syncthreads();
@@ -194,33 +149,31 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     }
     __syncthreads();
     const long long kmin = s_kmin;
-    int cnt = 0;
-    for (int64_t i = b0; i < b1; ++i) cnt += (key[i] == kmin);
-    // exclusive scan of cnt over the CTA
-    int incl = cnt;
+    int out = 0;   // entries written by earlier rounds (same in every thread)
+    for (int64_t r0 = 0; r0 < n; r0 += kSelThreads) {
+        const int64_t e = r0 + tid;
+        const bool f = e < n && key[e] == kmin;
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        const int pre = __popc(b & ((1u << lane) - 1u));
+        if (lane == 0) woff[warp] = __popc(b);
+        __syncthreads();
+        if (warp == 0) {
+            const int c = woff[lane];
+            int incl = c;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += y;
-    }
-    if (lane == 31) scnt[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int x = lane < kSelThreads / 32 ? scnt[lane] : 0;
-        int xi = x;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, xi, off);
-            if (lane >= off) xi += y;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            woff[lane] = incl - c;
+            if (lane == 31) wtot = incl;
         }
-        if (lane < kSelThreads / 32) scnt[lane] = xi - x;   // exclusive warp offsets
+        __syncthreads();
+        if (f) A.idx[out + woff[warp] + pre] = (int32_t)e;
+        out += wtot;
     }
-    __syncthreads();
-    int pos = scnt[warp] + incl - cnt;
-    for (int64_t i = b0; i < b1; ++i)
-        if (key[i] == kmin) A.idx[pos++] = (int32_t)i;
-    if (tid == kSelThreads - 1) {
-        const int64_t s = (int64_t)pos;   // last thread's end offset = total
+    if (tid == 0) {
+        const int64_t s = (int64_t)out;
         const double tmin = __longlong_as_double(kmin);
         *A.s = s;
         *A.t_next = tmin;
@@ -251,54 +204,14 @@ __global__ void correct_kernel(StepArgs A, int check_due)
     int flags = 0;
     for (int64_t ii = gtid(); ii < s; ii += gstride()) {
         const int64_t i = A.idx[ii];
-        const double dt = A.dt[i];
         if (check_due && A.tn[i] != tn) {
             flags |= kStState;
             continue;
         }
         double an[3], kn[3];
         load_fin(A.fin, ii, an, kn, nullptr);
-        double xp[3], vp[3];
-        predict_one(A, i, tn, xp, vp);
-        // Hermite corrector, da = a_old - a_new. dt is a power of two, so dividing by
-        // dt, dt^2, dt^3 is the same exact scaling as multiplying by their reciprocals.
-        const double dt2 = dt * dt;
-        const double dt3 = dt2 * dt;
-        const double dt4 = dt3 * dt;
-        const double dt5 = dt4 * dt;
-        const double idt = 1.0 / dt;
-        const double idt2 = idt * idt;
-        const double idt3 = idt2 * idt;
-        double x1[3], v1[3], a2[3], a3[3], a2p[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double ao = A.a[c * np + i], ko = A.k[c * np + i];
-            const double da = ao - an[c];
-            a2[c] = -6.0 * da * idt2 - (4.0 * ko + 2.0 * kn[c]) * idt;
-            a3[c] = 12.0 * da * idt3 + 6.0 * (ko + kn[c]) * idt2;
-            x1[c] = xp[c] + a2[c] * dt4 / 24.0 + a3[c] * dt5 / 120.0;
-            v1[c] = vp[c] + a2[c] * dt3 / 6.0 + a3[c] * dt4 / 24.0;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a2p[c] = a2[c] + a3[c] * dt;
-        const double cand = aarseth(an, kn, a2p, a3, A.eta);
-        const double dt_new = quantise(cand, dt, tn, A.dt_max, A.dt_min);
-        bool finite = true;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            finite = finite && isfinite(x1[c]) && isfinite(v1[c]) && isfinite(an[c]) && isfinite(kn[c]);
-        if (!finite) flags |= kStNonfinite;
-        if (dt_new == 0.0) flags |= kStUnderflow;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            A.x[c * np + i] = x1[c];
-            A.v[c * np + i] = v1[c];
-            A.a[c * np + i] = an[c];
-            A.k[c * np + i] = kn[c];
-        }
-        A.t[i] = tn;
-        A.dt[i] = dt_new;
-        A.tn[i] = tn + dt_new;
+        flags |= hermite_correct(A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, np, i, tn, an, kn, A.eta,
+                                 A.dt_max, A.dt_min);
     }
     if (flags) atomicOr(A.status, flags);
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
@@ -321,6 +234,8 @@ __global__ void init_steps_kernel(StepArgs A)
         for (int c = 0; c < 3; ++c) {
             A.a[c * np + i] = an[c];
             A.k[c * np + i] = kn[c];
+            A.a2[c * np + i] = ds_pack(an[c]);
+            A.k2[c * np + i] = ds_pack(kn[c]);
             finite = finite && isfinite(an[c]) && isfinite(kn[c]);
         }
         const double dt = initial_step(an, kn, A.eta, A.dt_max, A.dt_min);
@@ -387,16 +302,16 @@ __global__ void records_to_aos_kernel(StepArgs A, double *xo, double *vo)
     const int64_t np = A.n_pad;
     for (int64_t i = gtid(); i < A.n; i += gstride()) {
         if (A.precision == NB_PREC_MIXED) {
-            const float4 h = A.j.hi[i], l = A.j.lo[i], w = A.j.vel[i];
+            const IPart r = jrec_load(A.j.p, i);
             if (xo) {
-                xo[3 * i + 0] = (double)h.x + (double)l.x;
-                xo[3 * i + 1] = (double)h.y + (double)l.y;
-                xo[3 * i + 2] = (double)h.z + (double)l.z;
+                xo[3 * i + 0] = (double)r.xh + (double)r.xl;
+                xo[3 * i + 1] = (double)r.yh + (double)r.yl;
+                xo[3 * i + 2] = (double)r.zh + (double)r.zl;
             }
             if (vo) {
-                vo[3 * i + 0] = (double)w.x;
-                vo[3 * i + 1] = (double)w.y;
-                vo[3 * i + 2] = (double)w.z;
+                vo[3 * i + 0] = (double)r.vx;
+                vo[3 * i + 1] = (double)r.vy;
+                vo[3 * i + 2] = (double)r.vz;
             }
         } else {
             for (int c = 0; c < 3; ++c) {
@@ -499,6 +414,12 @@ cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cu
 {
     // FP64-heavy: small CTAs so that the work spreads over every SM
     predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, use_t_next ? 1 : 0, t_host);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_to_ds(const StepArgs &a, cudaStream_t st)
+{
+    state_to_ds_kernel<<<grid_for(a.n, kStepThreads), kStepThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

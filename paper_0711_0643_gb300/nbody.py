@@ -85,6 +85,7 @@ _SIGS = [
     ("nb_ensemble_init", C.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
     ("nb_ensemble_run", C.c_int, [_P, _D]),
     ("nb_ensemble_energy", C.c_int, [_P, _P]),
+    ("nb_ensemble_stats", C.c_int, [_P, _P, _P, _P]),
     ("nb_ensemble_get_state", C.c_int, [_P, _P]),
 ]
 EXPORTED = [s[0] for s in _SIGS]
@@ -306,6 +307,13 @@ def nb_ensemble_energy(ctx, nc):
     E = np.zeros(int(nc))
     _check(ctx, load().nb_ensemble_energy(ctx, _ptr(E)))
     return E
+
+
+def nb_ensemble_stats(ctx, nc):
+    """Per-system (block_steps, particle_steps, interactions) arrays."""
+    b = np.zeros(int(nc), dtype=np.int64); p = np.zeros(int(nc), dtype=np.int64); i = np.zeros(int(nc))
+    _check(ctx, load().nb_ensemble_stats(ctx, _ptr(b), _ptr(p), _ptr(i)))
+    return b, p, i
 
 
 def nb_ensemble_get_state(ctx, N):

@@ -1,0 +1,123 @@
+"""Batched ensemble (one persistent cluster launch over many independent systems)
+against the FP64 CPU oracle and against itself.
+
+* initial forces of every member within the mixed-precision tolerance of the
+  parity tests, first steps exactly the oracle's rule on those forces, energies
+  within 1e-12 of the oracle's;
+* every member lands on t_end, conserves energy within 2x the oracle's error
+  plus a round-off floor of 1e-9 (at t = 0.25 both errors sit near the level of
+  summation noise, where a factor of 2 is not resolved);
+* results are bitwise reproducible and do not depend on which other systems
+  share the launch.
+"""
+import numpy as np
+import pytest
+
+import ics
+from tests.nbtools import condition_scales, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody
+    nbody.load()
+    return nbody
+
+
+def _pack(members):
+    off = np.zeros(len(members) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([s.n for s in members])
+    m = np.concatenate([s.m for s in members])
+    x = np.concatenate([s.x for s in members])
+    v = np.concatenate([s.v for s in members])
+    e2 = np.array([s.eps2 for s in members])
+    return off, m, x, v, e2
+
+
+def _members():
+    return ics.ensemble(10, seed=4242, n_lo=40, n_hi=700)
+
+
+def test_ensemble_initial_state(nb, orc):
+    mem = _members()
+    off, m, x, v, e2 = _pack(mem)
+    with nb.Context() as c:
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        st = nb.nb_ensemble_get_state(c.ctx, off[-1])
+        E = nb.nb_ensemble_energy(c.ctx, len(mem))
+    for q, s in enumerate(mem):
+        sl = slice(off[q], off[q + 1])
+        np.testing.assert_array_equal(st["t"][sl], 0.0)
+        ar, kr, _ = orc.force(s.m, s.x, s.v, s.eps2)
+        A, K = condition_scales(s.m, s.x, s.v, s.eps2, np.arange(s.n))
+        assert (np.linalg.norm(st["a"][sl] - ar, axis=1) / A).max() < 1e-6, q
+        assert np.percentile(rel_errors(st["a"][sl], ar, A), 99) < 1e-6, q
+        assert (np.linalg.norm(st["k"][sl] - kr, axis=1) / K).max() < 1e-6, q
+        for i in range(s.n):
+            assert st["dt"][sl][i] == orc.initial_dt(st["a"][sl][i], st["k"][sl][i])
+        Kr, Wr = orc.energy(s.m, s.x, s.v, s.eps2)
+        assert abs(E[q] - (Kr + Wr)) < 1e-12 * abs(Kr + Wr), q
+
+
+def test_ensemble_run_conserves_energy_and_lands(nb, orc):
+    mem = _members()
+    off, m, x, v, e2 = _pack(mem)
+    t_end = 0.25
+    with nb.Context() as c:
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        E0 = nb.nb_ensemble_energy(c.ctx, len(mem))
+        nb.nb_ensemble_run(c.ctx, t_end)
+        E1 = nb.nb_ensemble_energy(c.ctx, len(mem))
+        st = nb.nb_ensemble_get_state(c.ctx, off[-1])
+        bs, ps, inter = nb.nb_ensemble_stats(c.ctx, len(mem))
+    np.testing.assert_array_equal(st["t"], t_end)
+    assert np.all(bs > 0) and np.all(ps >= bs)
+    np.testing.assert_allclose(inter, ps * np.diff(off), rtol=0)
+    for q, s in enumerate(mem):
+        sysr = orc.System(s.m, s.x, s.v, s.eps2, nthreads=orc.default_threads())
+        Er0 = sysr.energy()
+        assert sysr.run(t_end) == 0
+        dEr = abs(sysr.energy() - Er0) / abs(Er0)
+        dE = abs(E1[q] - E0[q]) / abs(E0[q])
+        print(f"member {q} N={s.n}: |dE/E| {dE:.3e} oracle {dEr:.3e}; steps {bs[q]} oracle "
+              f"{sysr.counters['block_steps']}")
+        assert dE <= 2 * dEr + 1e-9, (q, dE, dEr)
+
+
+def test_ensemble_deterministic_and_independent(nb):
+    mem = _members()
+    off, m, x, v, e2 = _pack(mem)
+    states = []
+    for _ in range(2):
+        with nb.Context() as c:
+            nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+            nb.nb_ensemble_run(c.ctx, 0.125)
+            states.append(nb.nb_ensemble_get_state(c.ctx, off[-1]))
+    for key in ("x", "v", "a", "k", "t", "dt"):
+        np.testing.assert_array_equal(states[0][key], states[1][key])
+    # member 3 alone gives the same bits as member 3 inside the batch
+    q = 3
+    s = mem[q]
+    with nb.Context() as c:
+        o1, m1, x1, v1, e1 = _pack([s])
+        nb.nb_ensemble_init(c.ctx, o1, m1, x1, v1, e1)
+        nb.nb_ensemble_run(c.ctx, 0.125)
+        alone = nb.nb_ensemble_get_state(c.ctx, s.n)
+    sl = slice(off[q], off[q + 1])
+    for key in ("x", "v", "t", "dt"):
+        np.testing.assert_array_equal(alone[key], states[0][key][sl])
+
+
+def test_ensemble_argument_errors(nb):
+    with nb.Context() as c:
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_ensemble_run(c.ctx, 1.0)
+        assert e.value.status == nb.NB_ERR_STATE
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_ensemble_init(c.ctx, np.array([0, 5, 5], dtype=np.int64), np.ones(5), np.zeros((5, 3)),
+                                np.zeros((5, 3)), np.array([0.01, 0.01]))
+        assert e.value.status == nb.NB_ERR_ARG

@@ -1,11 +1,12 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Forces: every kernel variant, several split factors, ragged sizes. FP64 path:
-per-particle relative error of a, k and phi within 1e-12. Mixed path: a and phi
-within 1e-6 relative; the jerk within 1e-6 of its condition scale
-K_i = sum_j |jerk term| (the jerk sum of some particles cancels heavily, and any
-FP32 pair arithmetic has error ~ u K_i there); the forward relative jerk error
-is printed beside it.
+per-particle relative error of a, k and phi within 1e-12. Mixed path: phi within
+1e-6 relative; a and the jerk within 1e-6 of their condition scales
+A_i = sum_j |a term|, K_i = sum_j |jerk term| (any FP32 pair arithmetic has an
+error of a few u times that scale; for sums that cancel heavily, the forward
+error grows with the condition number A_i/|a_i|), and the forward relative
+error of a within 1e-6 at the 99th percentile. Forward statistics are printed.
 Predictor, corrector, time steps and block selection: bit-exact against the
 oracle given the same inputs. Integration: the FP64 path reproduces the
 oracle's block schedule for the first 16 steps; both paths keep |dE/E| at
@@ -34,15 +35,30 @@ def nb():
     return nbody
 
 
-def _errors(prec, a, k, phi, ar, kr, pr, A, K):
-    """(e_a, e_k, e_phi, forward e_k): the errors the tolerance applies to."""
-    ea = rel_errors(a, ar, A)
-    ek_fwd = rel_errors(k, kr, K)
-    dk = np.linalg.norm(k - kr, axis=1)
+def _cond_scaled(x, xr, scale):
+    d = np.linalg.norm(x - xr, axis=1)
     with np.errstate(divide="ignore", invalid="ignore"):
-        ek = ek_fwd if prec == 1 else np.where(dk == 0.0, 0.0, dk / K)
+        return np.where(d == 0.0, 0.0, d / scale)
+
+
+def _errors(prec, a, k, phi, ar, kr, pr, A, K):
+    """(e_a, e_k, e_phi, forward e_a, forward e_k): e_* are what the tolerance applies to
+    (forward for FP64, condition-scaled for the mixed path)."""
+    ea_fwd = rel_errors(a, ar, A)
+    ek_fwd = rel_errors(k, kr, K)
+    if prec == 1:
+        ea, ek = ea_fwd, ek_fwd
+    else:
+        ea, ek = _cond_scaled(a, ar, A), _cond_scaled(k, kr, K)
     ep = rel_scalar(phi, pr)
-    return ea, ek, ep, ek_fwd
+    return ea, ek, ep, ea_fwd, ek_fwd
+
+
+def _check(prec, ea, ek, ep, eaf, where):
+    tol = TOL[prec]
+    assert ea.max() < tol and ek.max() < tol and ep.max() < tol, (where, stats(ea), stats(ek), stats(ep))
+    if prec == 0:
+        assert np.percentile(eaf, 99) < tol, (where, stats(eaf))
 
 
 def _forces_vs_oracle(nb, orc, c, snap, idx, prec):
@@ -51,7 +67,7 @@ def _forces_vs_oracle(nb, orc, c, snap, idx, prec):
     a, k, phi = nb.nb_force_jerk(c.ctx, idx)
     ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, idx, nthreads=orc.default_threads())
     A, K = condition_scales(snap.m, xp, vp, snap.eps2, idx)
-    return _errors(prec, a, k, phi, ar, kr, pr, A, K)
+    return _errors(prec, a, k, phi, ar, kr, pr, A, K)[:4]
 
 
 SIZES = [(1, 0.01), (2, 0.0), (7, 0.05), (300, 0.01), (1000, 1.0 / 64), (2049, 1.0 / 256)]
@@ -72,10 +88,8 @@ def test_force_all_variants(nb, orc, prec, n, eps):
                     nb.nb_set_tuning(c.ctx, b, v, split)
                 for sub in subsets:
                     idx = np.unique(sub).astype(np.int32)
-                    ea, ek, ep, ekf = _forces_vs_oracle(nb, orc, c, snap, idx, prec)
-                    tol = TOL[prec]
-                    assert ea.max() < tol and ek.max() < tol and ep.max() < tol, \
-                        (nb.nb_variant_name(c.ctx, v), split, idx.size, stats(ea), stats(ek), stats(ep))
+                    ea, ek, ep, eaf = _forces_vs_oracle(nb, orc, c, snap, idx, prec)
+                    _check(prec, ea, ek, ep, eaf, (nb.nb_variant_name(c.ctx, v), split, idx.size))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -95,14 +109,16 @@ def test_force_plummer_16k_all_blocks(nb, orc, prec):
             pos = np.searchsorted(idx, sample)
             ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, sample, nthreads=orc.default_threads())
             A, K = condition_scales(snap.m, xp, vp, snap.eps2, sample)
-            ea, ek, ep, ekf = _errors(prec, a[pos], k[pos], phi[pos], ar, kr, pr, A, K)
-            print(f"prec {prec} s {s}: a {stats(ea)} k {stats(ek)} k(forward) {stats(ekf)} phi {stats(ep)}")
-            assert ea.max() < TOL[prec] and ek.max() < TOL[prec] and ep.max() < TOL[prec]
+            ea, ek, ep, eaf, ekf = _errors(prec, a[pos], k[pos], phi[pos], ar, kr, pr, A, K)
+            print(f"prec {prec} s {s}: a {stats(ea)} k {stats(ek)} a(forward) {stats(eaf)} "
+                  f"k(forward) {stats(ekf)} phi {stats(ep)}")
+            _check(prec, ea, ek, ep, eaf, s)
 
 
 def test_predictor_bit_exact(nb, orc):
     """FP64 predicted records equal the oracle's predictor bit for bit; the mixed records
-    are the FP64 prediction split into hi + lo (exact to 2^-48 relative)."""
+    (a double-single Horner evaluation, split into hi + lo) agree with it to 2^-45 of each
+    particle's |x| and to FP32 rounding in v."""
     snap = ics.config(1)
     for prec in (1, 0):
         with nb.Context(precision=prec) as c:
@@ -118,8 +134,10 @@ def test_predictor_bit_exact(nb, orc):
                 np.testing.assert_array_equal(xp, xr)
                 np.testing.assert_array_equal(vp, vr)
             else:
-                assert np.max(np.abs(xp - xr) / np.maximum(np.abs(xr), 1e-30)) < 2.0 ** -46
-                assert np.max(np.abs(vp - vr) / np.maximum(np.abs(vr), 1e-30)) < 2.0 ** -24
+                ex = np.linalg.norm(xp - xr, axis=1) / np.linalg.norm(xr, axis=1)
+                ev = np.linalg.norm(vp - vr, axis=1) / np.linalg.norm(vr, axis=1)
+                assert ex.max() < 2.0 ** -45, ex.max()
+                assert ev.max() < 2.0 ** -22, ev.max()
 
 
 def test_corrector_and_steps_bit_exact(nb, orc):
