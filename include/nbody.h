@@ -55,8 +55,8 @@ typedef enum { NB_PREC_MIXED = 0, NB_PREC_FP64 = 1 } nb_precision;
 
 typedef struct {
     double eta;           /* accuracy parameter nu of Eq. (timestep); default 0.01 */
-    double dt_max;        /* largest step, a power of two; default 1/16 */
-    double dt_min;        /* smallest step; default 2^-40 (below: NB_ERR_DT_UNDERFLOW) */
+    double dt_max;        /* largest step, a power of two <= 2^300; default 1/16 */
+    double dt_min;        /* smallest step, >= 2^-300; default 2^-40 (below: NB_ERR_DT_UNDERFLOW) */
     int32_t precision;    /* nb_precision; default NB_PREC_MIXED */
     int32_t autotune;     /* 1: time the kernel variants per active-set size on first use */
     int64_t spin_limit;   /* iteration cap of every device-side wait; default 1<<24 */

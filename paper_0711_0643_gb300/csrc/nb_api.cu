@@ -452,6 +452,8 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
     if (!(c.eta > 0) || !(c.dt_max > 0) || !(c.dt_min > 0) || c.dt_min > c.dt_max) return bad("steps");
     int e2;
     if (std::frexp(c.dt_max, &e2) != 0.5) return bad("dt_max must be a power of two");
+    // steps stay within [2^-300, 2^300], so dt^5 and 1/dt^3 are exact powers of two
+    if (c.dt_min < std::ldexp(1.0, -300) || c.dt_max > std::ldexp(1.0, 300)) return bad("step range");
     if (c.precision != NB_PREC_MIXED && c.precision != NB_PREC_FP64) return bad("precision");
     if (c.spin_limit < 1) return bad("spin_limit");
     int dev = c.device;

@@ -444,26 +444,25 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
                 }
                 __threadfence();
                 cluster.sync();
-                for (int64_t pp = rank + (int64_t)C * tid; pp < s; pp += (int64_t)C * kEnsThreads) {
-                    float h[7], l[7];
-#pragma unroll
-                    for (int c = 0; c < 7; ++c) { h[c] = 0.f; l[c] = 0.f; }
+                // four lanes per particle (correct_group); lane q reduces component min(q, 2)
+                // of a and k over the ranks' partials in rank order
+                const int64_t groups = (int64_t)C * (kEnsThreads / 4);
+                const int64_t gid = (int64_t)rank * (kEnsThreads / 4) + (tid >> 2);
+                const int cq = (tid & 3) < 3 ? (tid & 3) : 2;
+                const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
+                for (int64_t b0 = 0; b0 < s; b0 += groups) {
+                    const int64_t pp = b0 + gid;
+                    const bool live = pp < s;
+                    const int64_t pps = live ? pp : 0;
+                    float ha = 0.f, la = 0.f, hk = 0.f, lk = 0.f;
                     for (int q = 0; q < C; ++q) {
-                        const float2 *src = part + ((int64_t)q * s + pp) * kPartStride;
-#pragma unroll
-                        for (int c = 0; c < 7; ++c) {
-                            const float2 v = __ldcg(src + c);
-                            ds_add(h[c], l[c], v.x, v.y);
-                        }
+                        const float2 *src = part + ((int64_t)q * s + pps) * kPartStride;
+                        const float2 va = __ldcg(src + cq), vk = __ldcg(src + 3 + cq);
+                        ds_add(ha, la, va.x, va.y);
+                        ds_add(hk, lk, vk.x, vk.y);
                     }
-                    double an[3], kn[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        an[c] = (double)h[c] + (double)l[c];
-                        kn[c] = (double)h[3 + c] + (double)l[3 + c];
-                    }
-                    flags |= hermite_correct(E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np,
-                                             base + act[pp], tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                    const double an = (double)ha + (double)la, kn = (double)hk + (double)lk;
+                    flags |= correct_group(H, base + act[pps], live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
                 }
             }
             if (rank == 0 && tid == 0) {

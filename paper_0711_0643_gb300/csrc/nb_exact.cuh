@@ -1,0 +1,94 @@
+// Exact FP64 helpers for the step kernels. On this GPU an FP64 warp instruction
+// occupies the SM sub-partition's FP64 unit for ~70 clocks whatever the number
+// of active lanes, an IEEE FP64 division or square root costs ~10 of them, and
+// so does nothing else in the step kernels. Every helper here returns exactly
+// the bits of the plain IEEE expression it replaces (stated with each one),
+// using fewer FP64 instructions or none.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace nb {
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
+__device__ __forceinline__ int dexpo(double x) { return (int)((dbits(x) >> 52) & 0x7ff); }
+
+// Finite (not inf or NaN), from the exponent field alone.
+__device__ __forceinline__ bool dfinite(double x) { return dexpo(x) != 0x7ff; }
+
+// y / full, correctly rounded, where full = d * scale^-1 with scale a power of two
+// and c = RN(1/d). Markstein's theorem (IBM J. Res. Dev. 34, 1990): if c is within
+// half an ulp of 1/d and q within one ulp of y/d, the residual r = y - q d is exact
+// (one fused multiply-add) and RN(q + r c) = RN(y/d). q = RN(y c) is within one ulp
+// for d = 3 and d = 15 (RN(1/d) is off by at most 2^-54 relative, under half an ulp). Scaling by a
+// power of two is exact while the result stays normal, which the exponent window
+// [63, 2023] of y guarantees; outside it the IEEE division is used.
+__device__ __forceinline__ double div_const(double y, double d, double c, double scale, double full)
+{
+    const int e = dexpo(y);
+    if (e >= 63 && e <= 2023) {
+        const double q = y * c;
+        const double r = fma(-q, d, y);
+        return fma(r, c, q) * scale;
+    }
+    return y / full;
+}
+__device__ __forceinline__ double div6(double y) { return div_const(y, 3.0, 1.0 / 3.0, 0.5, 6.0); }
+__device__ __forceinline__ double div24(double y) { return div_const(y, 3.0, 1.0 / 3.0, 0.125, 24.0); }
+__device__ __forceinline__ double div120(double y) { return div_const(y, 15.0, 1.0 / 15.0, 0.125, 120.0); }
+
+// 1/p for a power of two p whose reciprocal is normal (biased exponent of p in
+// [1, 2045]): the exponent field reflected about the bias, no FP64 instruction.
+__device__ __forceinline__ double recip_pow2(double p) { return dfrom((0x7FEll << 52) - dbits(p)); }
+
+// Bits of the largest power of two <= cand for cand > 0 finite and normal,
+// +inf for +inf, 0 for subnormal cand (frexp/ldexp's answer is then below any
+// normal step bound, which is all the quantisation rule looks at).
+__device__ __forceinline__ long long pow2_floor_bits(double cand) { return dbits(cand) & (long long)0xFFF0000000000000ull; }
+
+// cand > 0 (false for NaN, zeros and negatives), on the integer pipe.
+__device__ __forceinline__ bool dpositive(double cand)
+{
+    const long long b = dbits(cand);
+    return b > 0 && b <= 0x7FF0000000000000ll;
+}
+
+// Is t an integer multiple of the power of two p (p normal)? Equal to
+// u = t / p; u == floor(u) in IEEE arithmetic for finite t.
+__device__ __forceinline__ bool multiple_of_pow2(double t, double p)
+{
+    const long long tb = dbits(t) & 0x7FFFFFFFFFFFFFFFll;
+    if (tb == 0) return true;
+    const int et = (int)(tb >> 52);
+    const long long m = (tb & ((1ll << 52) - 1)) | (et ? (1ll << 52) : 0ll);
+    const int low = (et ? et : 1) - 1075 + (__ffsll(m) - 1);   // exponent of t's lowest set bit
+    return low >= (int)(dbits(p) >> 52) - 1023;
+}
+
+// The power-of-two step rule of the quantiser on bit patterns (all operands are
+// non-negative doubles, whose bit patterns order like their values): drop to q
+// when q < dt_old, double (once) when q >= 2 dt_old, 2 dt_old <= dt_max and
+// t_new is a multiple of 2 dt_old, else keep; clamp to dt_max; 0 below dt_min.
+// qb = pow2_floor_bits(cand); pos = dpositive(cand). dt_old in [2^-300, 2^300].
+__device__ __forceinline__ double quantise_bits(long long qb, bool pos, double dt_old, double t_new, double dt_max,
+                                                double dt_min)
+{
+    if (!pos) return 0.0;
+    const long long dto = dbits(dt_old), dt2 = dto + (1ll << 52), dmax = dbits(dt_max), dmin = dbits(dt_min);
+    long long dt;
+    if (qb < dto) {
+        dt = qb;
+    } else if (qb >= dt2 && dt2 <= dmax) {
+        dt = multiple_of_pow2(t_new, dfrom(dt2)) ? dt2 : dto;
+    } else {
+        dt = dto;
+    }
+    if (dt > dmax) dt = dmax;
+    if (dt < dmin) return 0.0;
+    return dfrom(dt);
+}
+
+}  // namespace nb

@@ -4,11 +4,14 @@
 // Every translation unit that includes this file is compiled with
 // -fmad=false, so each expression rounds operation by operation in the order
 // written -- the same order as the FP64 CPU oracle, giving the same bits.
+// Divisions by the constants 6, 24, 120 and by powers of two are replaced by the
+// exact equivalents of nb_exact.cuh (same bits, a fraction of the FP64 work).
 #pragma once
 
 #include <math_constants.h>
 
 #include "nb_ds.cuh"
+#include "nb_exact.cuh"
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -26,40 +29,44 @@ __device__ __forceinline__ double pow2_floor(double x)
     return ldexp(1.0, e - 1);
 }
 
-// Power-of-two step rule: drop to the largest power of two below the candidate;
-// double (once) only at times commensurate with twice the old step and within
-// dt_max; otherwise keep. 0 means "below dt_min or no valid candidate".
-__device__ __forceinline__ double quantise(double cand, double dt_old, double t_new, double dt_max, double dt_min)
+// The Aarseth step (Eq. timestep) from the squared norms A = |a|^2, K = |k|^2,
+// P = |a2p|^2, Q = |a3|^2 exactly as the oracle evaluates it:
+// sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| + |a2p|^2)); den = 0 sets no limit.
+__device__ __forceinline__ double aarseth_exact(double A, double K, double P, double Q, double eta)
 {
-    if (!(cand > 0.0)) return 0.0;
-    const double q = isinf(cand) ? CUDART_INF : pow2_floor(cand);
-    double dt;
-    const double dt2 = 2.0 * dt_old;
-    if (q < dt_old) {
-        dt = q;
-    } else if (q >= dt2 && dt2 <= dt_max) {
-        const double u = t_new / dt2;
-        dt = (u == floor(u)) ? dt2 : dt_old;
-    } else {
-        dt = dt_old;
-    }
-    if (dt > dt_max) dt = dt_max;
-    if (dt < dt_min) return 0.0;
-    return dt;
-}
-
-// Eq. (timestep): sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| + |a2p|^2)); den = 0 sets no limit.
-__device__ __forceinline__ double aarseth(const double *an, const double *kn, const double *a2p, const double *a3,
-                                          double eta)
-{
-    const double amag = sqrt(dot3(an[0], an[1], an[2], an[0], an[1], an[2]));
-    const double kmag = sqrt(dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]));
-    const double a2mag = sqrt(dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]));
-    const double a3mag = sqrt(dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]));
-    const double num = amag * a2mag + dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]);
-    const double den = kmag * a3mag + dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]);
+    const double num = sqrt(A) * sqrt(P) + K;
+    const double den = sqrt(K) * sqrt(Q) + P;
     if (den == 0.0) return CUDART_INF;
     return sqrt(eta * num / den);
+}
+
+// Squared norm inside [2^-120, 2^120]: its FP32 copy, square root and the
+// products below stay normal.
+__device__ __forceinline__ bool norm2_in_range(double S)
+{
+    const int e = dexpo(S);
+    return e >= 1023 - 120 && e <= 1023 + 120;
+}
+
+// The quantiser needs the Aarseth step only through the largest power of two
+// below it. FP32 estimate from rA = sqrt(A), rK, rP, rQ and fK = K, fP = P (all
+// FP32, from FP64 squared norms in range): relative error under 2^-19 (about a
+// dozen correctly rounded FP32 operations). When the estimate's significand is
+// at least 2^-14 away from 1 and from 2, it has the exact step's exponent: qb is
+// that power of two and the function returns true; otherwise false, and the
+// caller evaluates aarseth_exact.
+__device__ __forceinline__ bool aarseth_estimate(float rA, float rK, float rP, float rQ, float fK, float fP,
+                                                 float eta_f, long long &qb)
+{
+    const float num = rA * rP + fK;
+    const float den = rK * rQ + fP;
+    const float ratio = (eta_f * num) / den;
+    const int re = (__float_as_int(ratio) >> 23) & 0xff;
+    const float c32 = sqrtf(ratio);
+    const int cb = __float_as_int(c32);
+    const int cm = cb & 0x7fffff;
+    qb = (long long)(((cb >> 23) & 0xff) - 127 + 1023) << 52;
+    return re >= 127 - 120 && re <= 127 + 120 && cm >= (1 << 9) && cm <= 0x7fffff - (1 << 10);
 }
 
 __device__ __forceinline__ double initial_step(const double *a, const double *k, double eta, double dt_max,
@@ -86,16 +93,17 @@ __device__ __forceinline__ void hermite_predict(const double *x, const double *v
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int64_t q = c * np + i;
-        xp[c] = x[q] + v[q] * d + a[q] * d2 / 2.0 + k[q] * d3 / 6.0;
-        vp[c] = v[q] + a[q] * d + k[q] * d2 / 2.0;
+        xp[c] = ((x[q] + v[q] * d) + (a[q] * d2) * 0.5) + div6(k[q] * d3);
+        vp[c] = (v[q] + a[q] * d) + (k[q] * d2) * 0.5;
     }
 }
 
 // Hermite corrector and the new quantised step of particle i for the block time
 // tn, given the new force an, kn; updates x, v, a, k, t, dt, tn in place and the
 // double-single copies xd, vd, ad, kd when given (NULL: no copies).
-// Returns status bits (non-finite, underflow). dt is a power of two, so dividing
-// by dt, dt^2, dt^3 is the same exact scaling as multiplying by their reciprocals.
+// Returns status bits (non-finite, underflow). dt is a power of two in
+// [2^-300, 2^300], so dividing by dt, dt^2, dt^3 is the same exact scaling as
+// multiplying by their reciprocals.
 __device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, double *k, double *t, double *dtv,
                                                double *tnv, float2 *xd, float2 *vd, float2 *ad, float2 *kd,
                                                int64_t np, int64_t i, double tn, const double *an,
@@ -108,7 +116,7 @@ __device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, 
     const double dt3 = dt2 * dt;
     const double dt4 = dt3 * dt;
     const double dt5 = dt4 * dt;
-    const double idt = 1.0 / dt;
+    const double idt = recip_pow2(dt);
     const double idt2 = idt * idt;
     const double idt3 = idt2 * idt;
     double x1[3], v1[3], a2[3], a3[3], a2p[3];
@@ -116,19 +124,33 @@ __device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, 
     for (int c = 0; c < 3; ++c) {
         const double ao = a[c * np + i], ko = k[c * np + i];
         const double da = ao - an[c];
-        a2[c] = -6.0 * da * idt2 - (4.0 * ko + 2.0 * kn[c]) * idt;
-        a3[c] = 12.0 * da * idt3 + 6.0 * (ko + kn[c]) * idt2;
-        x1[c] = xp[c] + a2[c] * dt4 / 24.0 + a3[c] * dt5 / 120.0;
-        v1[c] = vp[c] + a2[c] * dt3 / 6.0 + a3[c] * dt4 / 24.0;
+        a2[c] = (-6.0 * da) * idt2 - (4.0 * ko + 2.0 * kn[c]) * idt;
+        a3[c] = (12.0 * da) * idt3 + (6.0 * (ko + kn[c])) * idt2;
+        x1[c] = (xp[c] + div24(a2[c] * dt4)) + div120(a3[c] * dt5);
+        v1[c] = (vp[c] + div6(a2[c] * dt3)) + div24(a3[c] * dt4);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) a2p[c] = a2[c] + a3[c] * dt;
-    const double cand = aarseth(an, kn, a2p, a3, eta);
-    const double dt_new = quantise(cand, dt, tn, dt_max, dt_min);
+    const double A = dot3(an[0], an[1], an[2], an[0], an[1], an[2]);
+    const double K = dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]);
+    const double P = dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]);
+    const double Q = dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]);
+    long long qb = 0;
+    bool pos = true;
+    bool decided = norm2_in_range(A) && norm2_in_range(K) && norm2_in_range(P) && norm2_in_range(Q);
+    if (decided) {
+        const float fK = (float)K, fP = (float)P;
+        decided = aarseth_estimate(sqrtf((float)A), sqrtf(fK), sqrtf(fP), sqrtf((float)Q), fK, fP, (float)eta, qb);
+    }
+    if (!decided) {
+        const double cand = aarseth_exact(A, K, P, Q, eta);
+        qb = pow2_floor_bits(cand);
+        pos = dpositive(cand);
+    }
+    const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
     bool finite = true;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        finite = finite && isfinite(x1[c]) && isfinite(v1[c]) && isfinite(an[c]) && isfinite(kn[c]);
+    for (int c = 0; c < 3; ++c) finite = finite && dfinite(x1[c]) && dfinite(v1[c]) && dfinite(an[c]) && dfinite(kn[c]);
     int flags = 0;
     if (!finite) flags |= kStNonfinite;
     if (dt_new == 0.0) flags |= kStUnderflow;
@@ -151,6 +173,122 @@ __device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, 
     t[i] = tn;
     dtv[i] = dt_new;
     tnv[i] = tn + dt_new;
+    return flags;
+}
+
+// State arrays ([3][np] vectors, [np] scalars) for correct_group.
+struct HState {
+    double *x, *v, *a, *k, *t, *dt, *tn;
+    float2 *x2, *v2, *a2, *k2;   // double-single copies (x2 == nullptr: none kept)
+    int64_t np;
+};
+
+__device__ __forceinline__ double pick4(double v0, double v1, double v2, double v3, int w)
+{
+    return w == 0 ? v0 : (w == 1 ? v1 : (w == 2 ? v2 : v3));
+}
+
+// hermite_correct for one particle per group of four lanes. An FP64 warp
+// instruction costs the same whatever its active lanes, so lanes 0-2 carry the
+// x, y, z components through the predictor and the corrector (a third of the
+// instructions of one thread doing all three) and lane 3 joins for the step.
+// Same results, bit for bit. All 32 lanes of the warp call it together
+// (full-mask shuffles); lane q = lane & 3 passes component min(q, 2) of the new
+// a and k. i must be a valid particle even when live is false: the group then
+// computes without storing. Returns status bits.
+__device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
+                                             double eta, double dt_max, double dt_min)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = lane & 3;
+    const int c = q < 3 ? q : 2;
+    const int g0 = lane & ~3;
+    const unsigned full = 0xffffffffu;
+    const int64_t np = H.np;
+    const double ti = H.t[i], dt = H.dt[i];
+    const int64_t o = c * np + i;
+    const double x = H.x[o], v = H.v[o], ao = H.a[o], ko = H.k[o];
+
+    const double d = tn - ti;
+    const double d2 = d * d;
+    const double d3 = d2 * d;
+    const double xp = ((x + v * d) + (ao * d2) * 0.5) + div6(ko * d3);
+    const double vp = (v + ao * d) + (ko * d2) * 0.5;
+
+    const double dt2 = dt * dt;
+    const double dt3 = dt2 * dt;
+    const double dt4 = dt3 * dt;
+    const double dt5 = dt4 * dt;
+    const double idt = recip_pow2(dt);
+    const double idt2 = idt * idt;
+    const double idt3 = idt2 * idt;
+    const double da = ao - an;
+    const double a2 = (-6.0 * da) * idt2 - (4.0 * ko + 2.0 * kn) * idt;
+    const double a3 = (12.0 * da) * idt3 + (6.0 * (ko + kn)) * idt2;
+    const double x1 = (xp + div24(a2 * dt4)) + div120(a3 * dt5);
+    const double v1 = (vp + div6(a2 * dt3)) + div24(a3 * dt4);
+    const double a2p = a2 + a3 * dt;
+
+    // lane q gathers the three component squares of vector q (a, k, a2p, a3) by
+    // rotating shuffles and sums them in component order, as dot3 does
+    const double s0 = an * an, s1 = kn * kn, s2 = a2p * a2p, s3 = a3 * a3;
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const double mine = pick4(s0, s1, s2, s3, (q - r) & 3);   // lane src supplies vector (src - r) & 3
+        const int src = (q + r) & 3;
+        const double got = __shfl_sync(full, mine, g0 + src);
+        if (src == 0) p0 = got;
+        if (src == 1) p1 = got;
+        if (src == 2) p2 = got;
+    }
+    const double S = (p0 + p1) + p2;
+
+    const float fS = (float)S;
+    const float rS = sqrtf(fS);
+    const float rA = __shfl_sync(full, rS, g0), rK = __shfl_sync(full, rS, g0 + 1);
+    const float rP = __shfl_sync(full, rS, g0 + 2), rQ = __shfl_sync(full, rS, g0 + 3);
+    const float fK = __shfl_sync(full, fS, g0 + 1), fP = __shfl_sync(full, fS, g0 + 2);
+    const unsigned okb = __ballot_sync(full, norm2_in_range(S));
+    long long qb = 0;
+    bool pos = true;
+    bool decided = aarseth_estimate(rA, rK, rP, rQ, fK, fP, (float)eta, qb);
+    decided = decided && ((okb >> g0) & 0xFu) == 0xFu;
+    if (__any_sync(full, live && !decided)) {
+        const double mag = sqrt(S);   // the four magnitudes, one per lane
+        const double mA = __shfl_sync(full, mag, g0), mK = __shfl_sync(full, mag, g0 + 1);
+        const double mP = __shfl_sync(full, mag, g0 + 2), mQ = __shfl_sync(full, mag, g0 + 3);
+        const double K = __shfl_sync(full, S, g0 + 1), P = __shfl_sync(full, S, g0 + 2);
+        if (!decided) {
+            const double num = mA * mP + K;
+            const double den = mK * mQ + P;
+            const double cand = den == 0.0 ? CUDART_INF : sqrt(eta * num / den);
+            qb = pow2_floor_bits(cand);
+            pos = dpositive(cand);
+        }
+    }
+    int flags = 0;
+    if (live) {
+        if (q < 3) {
+            if (!(dfinite(x1) && dfinite(v1) && dfinite(an) && dfinite(kn))) flags |= kStNonfinite;
+            H.x[o] = x1;
+            H.v[o] = v1;
+            H.a[o] = an;
+            H.k[o] = kn;
+            if (H.x2) {
+                H.x2[o] = ds_pack(x1);
+                H.v2[o] = ds_pack(v1);
+                H.a2[o] = ds_pack(an);
+                H.k2[o] = ds_pack(kn);
+            }
+        } else {
+            const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
+            if (dt_new == 0.0) flags |= kStUnderflow;
+            H.t[i] = tn;
+            H.dt[i] = dt_new;
+            H.tn[i] = tn + dt_new;
+        }
+    }
     return flags;
 }
 

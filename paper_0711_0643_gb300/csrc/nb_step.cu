@@ -10,6 +10,7 @@
 #include <math_constants.h>
 
 #include "nb_ds.cuh"
+#include "nb_exact.cuh"
 #include "nb_hermite.cuh"
 #include "nb_internal.cuh"
 #include "nb_pair.cuh"
@@ -99,9 +100,15 @@ __global__ void state_to_ds_kernel(StepArgs A)
 // ---------------------------------------------------------------- selection
 // One CTA of 1024 threads. Keys tn_i = t_i + dt_i are non-negative doubles (+inf
 // for padding) whose bit patterns order like the values, so all comparisons run
-// on the integer pipe. Pass 1: coalesced minimum. Pass 2: ordered compaction in
-// rounds of 1024 consecutive keys (warp ballots, then a scan of the 32 warp
-// counts), so the active list comes out ascending.
+// on the integer pipe. Thread t owns 16 consecutive keys of each chunk of 16384
+// (two 16-byte loads per 4 keys; the padded length is a multiple of 256, so a
+// thread's 16 keys lie wholly inside or outside it). Pass 1: minimum. Pass 2:
+// per-thread counts of keys equal to the minimum, one block-wide exclusive scan,
+// and each thread writes its indices in order, so the list comes out ascending.
+// For up to 16384 particles the keys stay in registers between the passes.
+constexpr int kSelPer = 16;
+constexpr int64_t kSelChunk = (int64_t)kSelThreads * kSelPer;
+
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
 #pragma unroll
@@ -112,6 +119,22 @@ __device__ __forceinline__ long long warp_min_ll(long long v)
     return v;
 }
 
+__device__ __forceinline__ void sel_load(const long long *key, int64_t b, int64_t np, long long *k)
+{
+    if (b < np) {
+        const longlong2 *p = reinterpret_cast<const longlong2 *>(key + b);
+#pragma unroll
+        for (int j = 0; j < kSelPer / 2; ++j) {
+            const longlong2 w = p[j];
+            k[2 * j] = w.x;
+            k[2 * j + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSelPer; ++j) k[j] = 0x7ff0000000000000LL;
+    }
+}
+
 __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGraphConditionalHandle cond,
                                                              int set_cond)
 {
@@ -120,57 +143,63 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     __shared__ int wtot;
     __shared__ long long s_kmin;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t n = A.n;
+    const int64_t n = A.n, np = A.n_pad;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
-    long long m0 = 0x7ff0000000000000LL, m1 = m0, m2 = m0, m3 = m0;   // +inf
-    int64_t i = tid;
-    for (; i + 3 * kSelThreads < n; i += 4 * kSelThreads) {
-        const long long k0 = key[i], k1 = key[i + kSelThreads], k2 = key[i + 2 * kSelThreads],
-                        k3 = key[i + 3 * kSelThreads];
-        m0 = k0 < m0 ? k0 : m0;
-        m1 = k1 < m1 ? k1 : m1;
-        m2 = k2 < m2 ? k2 : m2;
-        m3 = k3 < m3 ? k3 : m3;
+    const int64_t nchunk = (np + kSelChunk - 1) / kSelChunk;
+    long long k[kSelPer];
+    long long m = 0x7ff0000000000000LL;   // +inf
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+        sel_load(key, ch * kSelChunk + (int64_t)tid * kSelPer, np, k);
+#pragma unroll
+        for (int j = 0; j < kSelPer; ++j) m = k[j] < m ? k[j] : m;
     }
-    for (; i < n; i += kSelThreads) {
-        const long long k0 = key[i];
-        m0 = k0 < m0 ? k0 : m0;
-    }
-    m0 = m1 < m0 ? m1 : m0;
-    m2 = m3 < m2 ? m3 : m2;
-    long long m = m2 < m0 ? m2 : m0;
     m = warp_min_ll(m);
     if (lane == 0) smin[warp] = m;
     __syncthreads();
     if (warp == 0) {
-        long long x = lane < kSelThreads / 32 ? smin[lane] : 0x7ff0000000000000LL;
+        long long x = smin[lane];
         x = warp_min_ll(x);
         if (lane == 0) s_kmin = x;
     }
     __syncthreads();
     const long long kmin = s_kmin;
-    int out = 0;   // entries written by earlier rounds (same in every thread)
-    for (int64_t r0 = 0; r0 < n; r0 += kSelThreads) {
-        const int64_t e = r0 + tid;
-        const bool f = e < n && key[e] == kmin;
-        const unsigned b = __ballot_sync(0xffffffffu, f);
-        const int pre = __popc(b & ((1u << lane) - 1u));
-        if (lane == 0) woff[warp] = __popc(b);
+    int out = 0;   // entries written by earlier chunks (same in every thread)
+    for (int64_t ch = 0; ch < nchunk; ++ch) {
+        const int64_t b = ch * kSelChunk + (int64_t)tid * kSelPer;
+        if (nchunk > 1) sel_load(key, b, np, k);
+        unsigned hit = 0;
+#pragma unroll
+        for (int j = 0; j < kSelPer; ++j)
+            if (k[j] == kmin && b + j < n) hit |= 1u << j;
+        const int cnt = __popc(hit);
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) woff[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            const int c = woff[lane];
-            int incl = c;
+            const int cw = woff[lane];
+            int wi = cw;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
+                const int y = __shfl_up_sync(0xffffffffu, wi, off);
+                if (lane >= off) wi += y;
             }
-            woff[lane] = incl - c;
-            if (lane == 31) wtot = incl;
+            woff[lane] = wi - cw;
+            if (lane == 31) wtot = wi;
         }
         __syncthreads();
-        if (f) A.idx[out + woff[warp] + pre] = (int32_t)e;
+        int pos = out + woff[warp] + incl - cnt;
+        while (hit) {
+            const int j = __ffs(hit) - 1;
+            hit &= hit - 1;
+            A.idx[pos++] = (int32_t)(b + j);
+        }
         out += wtot;
+        __syncthreads();   // woff and wtot are rewritten by the next chunk
     }
     if (tid == 0) {
         const int64_t s = (int64_t)out;
@@ -196,22 +225,29 @@ __device__ __forceinline__ void load_fin(const double *fin, int64_t ii, double *
     if (phi) *phi = p[6];
 }
 
-__global__ void correct_kernel(StepArgs A, int check_due)
+// Four lanes per active particle (correct_group): 32 particles per CTA and round.
+constexpr int kCorThreads = 128;
+constexpr int kCorPer = kCorThreads / 4;
+
+__global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int check_due)
 {
     const int64_t s = *A.s;
     const double tn = *A.t_next;
-    const int64_t np = A.n_pad;
+    const HState H{A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, A.n_pad};
+    const int q = threadIdx.x & 3;
+    const int c = q < 3 ? q : 2;
     int flags = 0;
-    for (int64_t ii = gtid(); ii < s; ii += gstride()) {
-        const int64_t i = A.idx[ii];
-        if (check_due && A.tn[i] != tn) {
+    for (int64_t base = (int64_t)blockIdx.x * kCorPer; base < s; base += (int64_t)gridDim.x * kCorPer) {
+        const int64_t ii = base + (threadIdx.x >> 2);
+        bool live = ii < s;
+        const int64_t iis = live ? ii : 0;
+        const int64_t i = A.idx[iis];
+        if (live && check_due && dbits(A.tn[i]) != dbits(tn)) {
+            live = false;
             flags |= kStState;
-            continue;
         }
-        double an[3], kn[3];
-        load_fin(A.fin, ii, an, kn, nullptr);
-        flags |= hermite_correct(A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, np, i, tn, an, kn, A.eta,
-                                 A.dt_max, A.dt_min);
+        const double an = A.fin[iis * kPartStride + c], kn = A.fin[iis * kPartStride + 3 + c];
+        flags |= correct_group(H, i, live, tn, an, kn, A.eta, A.dt_max, A.dt_min);
     }
     if (flags) atomicOr(A.status, flags);
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
@@ -443,8 +479,8 @@ cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_c
 
 cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st)
 {
-    // the grid covers the largest possible block; threads past s exit at once
-    correct_kernel<<<grid_for(a.n, 64, 2048), 64, 0, st>>>(a, check_due ? 1 : 0);
+    // one round covers blocks of up to 608 * 32 particles; CTAs past s exit at once
+    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0);
     return cudaGetLastError();
 }
 

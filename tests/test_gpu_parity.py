@@ -170,6 +170,44 @@ def test_corrector_and_steps_bit_exact(nb, orc):
             np.testing.assert_array_equal(after["x"][others], before["x"][others])
 
 
+def test_corrector_bit_exact_full_blocks(nb, orc):
+    """All 16384 particles of the Plummer workload due at once, for three common
+    steps, two accuracy parameters and both precisions (about 2e5 corrector
+    evaluations): x, v and the new quantised step equal the oracle's bit for bit,
+    given the GPU's own forces. The GPU quantiser decides from an FP32 estimate of
+    the Aarseth step and evaluates the FP64 expression only when the estimate lies
+    within 2^-14 of a power of two; the test counts candidates in that window, so
+    both branches are compared."""
+    snap = ics.config(2)
+    near = 0
+    for prec in (1, 0):
+        for eta in (0.01, 0.02):
+            with nb.Context(precision=prec, eta=eta) as c:
+                c.init(snap)
+                for dt in (2.0 ** -6, 2.0 ** -9, 2.0 ** -12):
+                    st = c.state()
+                    st["dt"][:] = dt          # every t is a multiple of these steps
+                    nb.nb_set_state(c.ctx, st)
+                    tn, s = nb.nb_next_block(c.ctx)
+                    assert s == snap.n and tn == st["t"][0] + dt
+                    idx = nb.nb_get_active(c.ctx, s)
+                    nb.nb_predict(c.ctx, tn)
+                    a_new, k_new, _ = nb.nb_force_jerk(c.ctx, idx)
+                    nb.nb_correct(c.ctx, tn)
+                    after = c.state()
+                    xr, vr = orc.predict(st["x"], st["v"], st["a"], st["k"], st["t"], tn)
+                    for i in range(snap.n):
+                        x1, v1, cand = orc.correct_particle(xr[i], vr[i], st["a"][i], st["k"][i], a_new[i],
+                                                            k_new[i], dt, eta)
+                        assert np.array_equal(after["x"][i], x1) and np.array_equal(after["v"][i], v1), \
+                            (prec, eta, dt, i)
+                        assert after["dt"][i] == orc.quantise(cand, dt, tn), (prec, eta, dt, i, cand)
+                        m = 2.0 * math.frexp(cand)[0]
+                        near += (m - 1.0 < 2.0 ** -14) or (2.0 - m < 2.0 ** -13)
+    print(f"candidates within 2^-14 of a power of two: {near}")
+    assert near > 0
+
+
 def test_initial_steps_and_selection_exact(nb, orc):
     """nb_init's first steps equal the oracle's start rule on the GPU forces; selection
     equals the oracle's definition on the GPU state."""
