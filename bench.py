@@ -310,7 +310,7 @@ def main_gpu(args):
     nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
     torch.cuda.synchronize(dev)
     clk_rf = ClockSampler(local).start()
-    force_ms, nlaunch = nb.nb_run_timed(c.ctx, T_END)
+    force_ms, nlaunch, phase_ms = nb.nb_run_timed(c.ctx, T_END, phases=True)
     clk_rf_s = clk_rf.stop()
     st_rf = nb.nb_stats(c.ctx)
     sm_mhz = clk["sm_mhz"] or clk_rf_s["sm_mhz"] or load_peaks().get("clocks_under_load", {}).get("sm_mhz_median")
@@ -322,7 +322,8 @@ def main_gpu(args):
                 "avg_launch_us": 1e3 * force_ms / max(nlaunch, 1),
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz} MHz (median SM clock "
                               f"sampled during the timed region)",
-                "flop_convention": f"{FLOP_PER_INTERACTION} flop per force+jerk interaction"}
+                "flop_convention": f"{FLOP_PER_INTERACTION} flop per force+jerk interaction",
+                "phases_us_per_block_step": {k: 1e3 * v / max(nlaunch, 1) for k, v in phase_ms.items()}}
 
     # ---- end to end through the C ABI with host buffers
     m_h = np.ascontiguousarray(snap.m); x_h = np.ascontiguousarray(snap.x); v_h = np.ascontiguousarray(snap.v)

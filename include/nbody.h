@@ -167,8 +167,11 @@ nb_status nb_run(nb_ctx *ctx, double t_end);
  * CUDA events around every force launch (a short, time-bounded wait kernel
  * precedes the start event so that it is processed only once the launch is
  * queued). *force_ms = summed force-kernel time, *launches = number of force
- * launches (NULL allowed). For measurement; slower than nb_run. */
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches);
+ * launches. phase_ms: NULL, or 4 doubles receiving the summed times of the
+ * select, predict, force and correct kernels, each bracketed the same way (the
+ * select that ends the loop is not counted). Every pointer may be NULL. For
+ * measurement; slower than nb_run. */
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms);
 
 /* Kinetic, potential (softened, W = sum m_i phi_i / 2) and total energy of the
  * current state, in FP64 on the device. Exact only when all t_i are equal
@@ -190,6 +193,9 @@ nb_status nb_sync(nb_ctx *ctx);
  * for active-set sizes 1, 2, 4, ..., n on the current predicted state and keeps
  * the fastest per size bucket. nb_set_tuning forces (variant, split) for a
  * bucket (bucket b holds s in (2^(b-1), 2^b]); variant -1 restores the default.
+ * split is the j-split factor at the bucket's largest size min(2^b, n); a
+ * smaller block of the bucket keeps the same number of work items (i-blocks x
+ * splits), so its split grows in proportion.
  * nb_get_tuning reads the table (variant[32], split[32]). */
 nb_status nb_autotune(nb_ctx *ctx);
 nb_status nb_set_tuning(nb_ctx *ctx, int32_t bucket, int32_t variant, int32_t split);

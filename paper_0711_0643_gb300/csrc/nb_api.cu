@@ -60,9 +60,6 @@ struct nb_ctx {
     int en_ctas = 0;
     double *en_out = nullptr;
     double *out_a = nullptr, *out_k = nullptr, *out_phi = nullptr;
-    int32_t *sel_cnt = nullptr;
-    double *sel_min = nullptr;
-    int32_t *done_ctr = nullptr;
 
     bool have_state = false;
     bool forces_pending = false;
@@ -145,8 +142,6 @@ StepArgs step_args(nb_ctx *c)
     A.idx = c->idx; A.s = c->s; A.t_next = c->t_next; A.t_end = c->t_end;
     A.fin = c->fin;
     A.status = c->status; A.counters = c->counters; A.interactions = c->interactions;
-    A.chunk_cnt = c->sel_cnt; A.chunk_min = c->sel_min; A.done_ctr = c->done_ctr;
-    A.select_ctas = 1;
     return A;
 }
 
@@ -357,6 +352,11 @@ nb_status check_ctx(nb_ctx *ctx, bool need_state)
     return NB_OK;
 }
 
+// The nb_run graph: select, then a while node whose body is predict -> force ->
+// correct -> select (the body's select sets the condition). The corrector stays
+// a kernel of its own: its FP64 work must spread over many SMs (an FP64 warp
+// instruction holds an SM sub-partition's FP64 unit for ~70 clocks), which the
+// CTAs that finish the force sums of an i-block cannot do.
 nb_status build_run_graph(nb_ctx *ctx)
 {
     if (ctx->run_exec) return NB_OK;
@@ -486,8 +486,7 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
               dalloc(&ctx->counters, 3) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
-              dalloc(&ctx->en_out, 2) == cudaSuccess && dalloc(&ctx->sel_cnt, 1024) == cudaSuccess &&
-              dalloc(&ctx->sel_min, 1024) == cudaSuccess && dalloc(&ctx->done_ctr, 1) == cudaSuccess;
+              dalloc(&ctx->en_out, 2) == cudaSuccess;
     if (!ok) {
         nb_destroy(ctx);
         return NB_ERR_CUDA;
@@ -515,7 +514,7 @@ void nb_destroy(nb_ctx *ctx)
     free_system(ctx);
     nb_ctx_set_ensemble(ctx, nullptr);
     void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
-                    ctx->counters, ctx->interactions, ctx->en_out, ctx->sel_cnt, ctx->sel_min, ctx->done_ctr};
+                    ctx->counters, ctx->interactions, ctx->en_out};
     for (void *p : ptrs) dfree(p);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -714,46 +713,74 @@ nb_status nb_run(nb_ctx *ctx, double t_end)
     return sync_status(ctx);
 }
 
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches)
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms)
 {
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!std::isfinite(t_end)) return fail(ctx, NB_ERR_ARG, "t_end must be finite");
     StepArgs A = step_args(ctx);
+    const bool phases = phase_ms != nullptr;
     int64_t nl = 0;
-    double total = 0.0;
-    if (ctx->ev.size() < 2) {
-        ctx->ev.assign(2, nullptr);
-        CK(cudaEventCreate(&ctx->ev[0]));
-        CK(cudaEventCreate(&ctx->ev[1]));
+    double total[4] = {0.0, 0.0, 0.0, 0.0};   // select, predict, force, correct
+    if (ctx->ev.size() < 8) {
+        for (cudaEvent_t e : ctx->ev)
+            if (e) cudaEventDestroy(e);
+        ctx->ev.assign(8, nullptr);
+        for (int q = 0; q < 8; ++q) CK(cudaEventCreate(&ctx->ev[q]));
     }
+    // A phase is bracketed by events only after a short, time-bounded wait
+    // kernel holds the stream, so that the launch and its end event are queued
+    // before the start event is processed: the events then bracket the kernel
+    // and not the host's launch latency.
+    auto open = [&](int ph) -> cudaError_t {
+        cudaError_t e = launch_delay(20000, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[2 * ph], ctx->stream);
+        return e;
+    };
+    auto close = [&](int ph) { return cudaEventRecord(ctx->ev[2 * ph + 1], ctx->stream); };
+    auto elapsed = [&](int ph) -> cudaError_t {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, ctx->ev[2 * ph], ctx->ev[2 * ph + 1]);
+        total[ph] += ms;
+        return e;
+    };
     for (;;) {
+        if (phases) CK(open(0));
         CK(launch_select(A, 0, false, ctx->stream));
+        if (phases) CK(close(0));
         double tn;
         int64_t ss;
         CK(cudaMemcpyAsync(&tn, ctx->t_next, sizeof tn, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(&ss, ctx->s, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         if (!(tn <= t_end) || ss <= 0) break;
+        if (phases) {
+            CK(elapsed(0));
+            CK(open(1));
+        }
         CK(launch_predict(A, true, 0.0, ctx->stream));
-        // hold the stream until the force launch and its end event are queued, so
-        // the events bracket the kernel and not the host's launch latency
-        CK(launch_delay(20000, ctx->stream));
-        CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+        if (phases) CK(close(1));
+        CK(open(2));
         CK(launch_force_ctx(ctx));
-        CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+        CK(close(2));
+        if (phases) CK(open(3));
         CK(launch_correct(A, false, ctx->stream));
+        if (phases) CK(close(3));
         int32_t stw = 0;
         CK(cudaMemcpyAsync(&stw, ctx->status, sizeof stw, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
-        total += ms;
+        CK(elapsed(2));
+        if (phases) {
+            CK(elapsed(1));
+            CK(elapsed(3));
+        }
         ++nl;
         if (stw) break;
     }
-    if (force_ms) *force_ms = total;
+    if (force_ms) *force_ms = total[2];
     if (launches) *launches = nl;
+    if (phases)
+        for (int q = 0; q < 4; ++q) phase_ms[q] = total[q];
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);
@@ -927,10 +954,16 @@ nb_status nb_autotune(nb_ctx *ctx)
             if (I > 4 * s && v > 0) continue;        // i-blocks mostly empty
             if ((s + I - 1) / I > 4096 && v < nv - 1) continue;   // far too many small work items
             const int64_t nib = (s + I - 1) / I;
-            int64_t S0 = std::max<int64_t>(1, (2 * (int64_t)ctx->num_sms * occ + nib - 1) / nib);
-            S0 = std::min<int64_t>(S0, ctx->n_tiles);
-            int64_t cands[4] = {std::max<int64_t>(1, S0 / 4), std::max<int64_t>(1, S0 / 2), S0,
-                                std::min<int64_t>(ctx->n_tiles, 2 * S0)};
+            const int64_t R = (int64_t)ctx->num_sms * occ;
+            // wave-aligned splits (W = nib * S just below k full waves), the default's
+            // choice, and a few coarse ones; at most 16 waves of items
+            std::vector<int64_t> cands;
+            for (int64_t S : {R / nib, 2 * R / nib, 3 * R / nib, 4 * R / nib, R / (2 * nib),
+                              wave_split(nib, ctx->n_tiles, R), ctx->n_tiles / 4, ctx->n_tiles / 16, (int64_t)1}) {
+                S = std::min<int64_t>(std::max<int64_t>(S, 1), ctx->n_tiles);
+                if (nib * S > 16 * R) continue;
+                if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
+            }
             for (int64_t S : cands) {
                 if (S * s * kPartStride > ctx->part_cap) continue;
                 ForceArgs F = force_args(ctx, v, (int)S);

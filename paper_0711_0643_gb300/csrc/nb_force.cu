@@ -114,6 +114,17 @@ __device__ __forceinline__ int bucket_of(int64_t s)
     return b;
 }
 
+// The table's split is the one for its bucket's largest size s_ref = min(2^b, n);
+// a smaller block of the bucket keeps the same number of work items (i-blocks x
+// splits), so a wave-aligned choice stays wave-aligned.
+__device__ __forceinline__ int table_split(int S_ref, int b, int64_t s, int64_t n, int64_t I)
+{
+    const int64_t s_ref = (int64_t(1) << b) < n ? (int64_t(1) << b) : n;
+    const int64_t nib_ref = (s_ref + I - 1) / I, nib = (s + I - 1) / I;
+    const int64_t S = (int64_t)S_ref * nib_ref / nib;
+    return S < 1 ? 1 : (S > (1 << 30) ? (1 << 30) : (int)S);
+}
+
 // Split factor clamp shared by both precisions.
 __device__ __forceinline__ int clamp_split(int S, int64_t n_tiles, int64_t s, int64_t cap)
 {
@@ -410,7 +421,8 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     } else {
         const int b = bucket_of(s);
         variant = A.tune->variant[b];
-        S = A.tune->split[b];
+        if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
+        S = table_split(A.tune->split[b], b, s, A.n, mixed_I(variant));
     }
     if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
     S = clamp_split(S, A.n_tiles, s, A.part_cap);
@@ -573,7 +585,8 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     } else {
         const int b = bucket_of(s);
         variant = A.tune->variant[b];
-        S = A.tune->split[b];
+        if (variant < 0 || variant >= kF64Variants) variant = kF64Variants - 1;
+        S = table_split(A.tune->split[b], b, s, A.n, f64_I(variant));
     }
     if (variant < 0 || variant >= kF64Variants) variant = kF64Variants - 1;
     S = clamp_split(S, A.n_tiles, s, A.part_cap);
@@ -657,6 +670,31 @@ cudaError_t launch_force_f64(const ForceArgs &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Work items are i-blocks x j-splits over a grid of R = SMs x resident CTAs;
+// a launch takes ceil(W / R) waves of items, so W just above a multiple of R
+// wastes most of a wave. One full wave (S = R / nib) unless items would then be
+// long (64 tiles or more): then the split in [S, 4 S] whose items fill their
+// waves best. At least 4 tiles per item.
+int64_t wave_split(int64_t nib, int64_t n_tiles, int64_t resident)
+{
+    int64_t S = std::max<int64_t>(1, resident / nib);
+    if (n_tiles / S >= 64) {
+        int64_t best = S;
+        double best_eff = 0.0;
+        for (int64_t c = S; c <= 4 * S; ++c) {
+            const int64_t W = nib * c;
+            const double eff = (double)W / (double)(((W + resident - 1) / resident) * resident);
+            if (eff > best_eff + 1e-9) {
+                best_eff = eff;
+                best = c;
+            }
+        }
+        S = best;
+    }
+    S = std::min<int64_t>(S, std::max<int64_t>(1, n_tiles / 4));
+    return std::max<int64_t>(1, std::min<int64_t>(S, n_tiles));
+}
+
 void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_per_sm, int *variant, int *split)
 {
     const int64_t n_tiles = (n + kJT - 1) / kJT;
@@ -664,24 +702,17 @@ void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_p
     int v;
     if (precision == NB_PREC_FP64) {
         v = s <= 64 ? 0 : 1;
-    } else if (s <= 1) {
-        v = 0;
-    } else if (s <= 4) {
-        v = 1;
-    } else if (s <= 32) {
-        v = 2;
-    } else if (s <= 512) {
-        v = 3;
+    } else if (n <= 65536) {
+        // j-records stay in L2 and are cheap to re-read: stream variants (every
+        // thread of a CTA on the same 1 or 2 i-particles) win while blocks are small
+        v = s <= (n <= 32768 ? 64 : 16) ? 0 : s <= 1024 ? 1 : s <= 1536 ? 2 : s <= 12288 ? 3 : 4;
     } else {
-        v = 4;
+        // large N: re-reading all j per i-particle costs more than it hides
+        v = s <= 1 ? 0 : s <= 4 ? 1 : s <= 32 ? 2 : s <= 512 ? 3 : 4;
     }
     const int64_t I = precision == NB_PREC_FP64 ? f64_I(v) : mixed_I(v);
-    const int64_t nib = (s + I - 1) / I;
-    int64_t S = (2 * resident + nib - 1) / nib;
-    if (S < 1) S = 1;
-    if (S > n_tiles) S = n_tiles;
     *variant = v;
-    *split = (int)S;
+    *split = (int)wave_split((s + I - 1) / I, n_tiles, resident);
 }
 
 }  // namespace nb

@@ -176,13 +176,6 @@ __device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, 
     return flags;
 }
 
-// State arrays ([3][np] vectors, [np] scalars) for correct_group.
-struct HState {
-    double *x, *v, *a, *k, *t, *dt, *tn;
-    float2 *x2, *v2, *a2, *k2;   // double-single copies (x2 == nullptr: none kept)
-    int64_t np;
-};
-
 __device__ __forceinline__ double pick4(double v0, double v1, double v2, double v3, int w)
 {
     return w == 0 ? v0 : (w == 1 ? v1 : (w == 2 ? v2 : v3));
@@ -192,10 +185,45 @@ __device__ __forceinline__ double pick4(double v0, double v1, double v2, double 
 // instruction costs the same whatever its active lanes, so lanes 0-2 carry the
 // x, y, z components through the predictor and the corrector (a third of the
 // instructions of one thread doing all three) and lane 3 joins for the step.
-// Same results, bit for bit. All 32 lanes of the warp call it together
-// (full-mask shuffles); lane q = lane & 3 passes component min(q, 2) of the new
-// a and k. i must be a valid particle even when live is false: the group then
-// computes without storing. Returns status bits.
+// Same results, bit for bit. Every FP64 operation is an explicit
+// round-to-nearest intrinsic, so the result does not depend on whether the
+// including file lets the compiler contract multiply-adds. All 32 lanes of the
+// warp call it together (full-mask shuffles); lane q = lane & 3 passes
+// component min(q, 2) of the new a and k. i must be a valid particle even when
+// live is false: the group then computes without storing. Returns status bits.
+__device__ __forceinline__ double rn_div6(double y)
+{
+    const int e = dexpo(y);
+    if (e >= 63 && e <= 2023) {
+        const double q = __dmul_rn(y, 1.0 / 3.0);
+        return __dmul_rn(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), 0.5);
+    }
+    return __ddiv_rn(y, 6.0);
+}
+__device__ __forceinline__ double rn_div24(double y)
+{
+    const int e = dexpo(y);
+    if (e >= 63 && e <= 2023) {
+        const double q = __dmul_rn(y, 1.0 / 3.0);
+        return __dmul_rn(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), 0.125);
+    }
+    return __ddiv_rn(y, 24.0);
+}
+__device__ __forceinline__ double rn_div120(double y)
+{
+    const int e = dexpo(y);
+    if (e >= 63 && e <= 2023) {
+        const double q = __dmul_rn(y, 1.0 / 15.0);
+        return __dmul_rn(__fma_rn(__fma_rn(-q, 15.0, y), 1.0 / 15.0, q), 0.125);
+    }
+    return __ddiv_rn(y, 120.0);
+}
+__device__ __forceinline__ float2 rn_ds_pack(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
+}
+
 __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
                                              double eta, double dt_max, double dt_min)
 {
@@ -209,29 +237,35 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
     const int64_t o = c * np + i;
     const double x = H.x[o], v = H.v[o], ao = H.a[o], ko = H.k[o];
 
-    const double d = tn - ti;
-    const double d2 = d * d;
-    const double d3 = d2 * d;
-    const double xp = ((x + v * d) + (ao * d2) * 0.5) + div6(ko * d3);
-    const double vp = (v + ao * d) + (ko * d2) * 0.5;
+    // predictor: ((x + v d) + (a d^2) / 2) + (k d^3) / 6 and (v + a d) + (k d^2) / 2
+    const double d = __dsub_rn(tn, ti);
+    const double d2 = __dmul_rn(d, d);
+    const double d3 = __dmul_rn(d2, d);
+    const double xp = __dadd_rn(__dadd_rn(__dadd_rn(x, __dmul_rn(v, d)), __dmul_rn(__dmul_rn(ao, d2), 0.5)),
+                                rn_div6(__dmul_rn(ko, d3)));
+    const double vp = __dadd_rn(__dadd_rn(v, __dmul_rn(ao, d)), __dmul_rn(__dmul_rn(ko, d2), 0.5));
 
-    const double dt2 = dt * dt;
-    const double dt3 = dt2 * dt;
-    const double dt4 = dt3 * dt;
-    const double dt5 = dt4 * dt;
+    // corrector (dt is a power of two in [2^-300, 2^300]: 1/dt^k are exact)
+    const double dt2 = __dmul_rn(dt, dt);
+    const double dt3 = __dmul_rn(dt2, dt);
+    const double dt4 = __dmul_rn(dt3, dt);
+    const double dt5 = __dmul_rn(dt4, dt);
     const double idt = recip_pow2(dt);
-    const double idt2 = idt * idt;
-    const double idt3 = idt2 * idt;
-    const double da = ao - an;
-    const double a2 = (-6.0 * da) * idt2 - (4.0 * ko + 2.0 * kn) * idt;
-    const double a3 = (12.0 * da) * idt3 + (6.0 * (ko + kn)) * idt2;
-    const double x1 = (xp + div24(a2 * dt4)) + div120(a3 * dt5);
-    const double v1 = (vp + div6(a2 * dt3)) + div24(a3 * dt4);
-    const double a2p = a2 + a3 * dt;
+    const double idt2 = __dmul_rn(idt, idt);
+    const double idt3 = __dmul_rn(idt2, idt);
+    const double da = __dsub_rn(ao, an);
+    // a2 = -6 da / dt^2 - (4 k_old + 2 k_new) / dt ; a3 = 12 da / dt^3 + 6 (k_old + k_new) / dt^2
+    const double a2 = __dsub_rn(__dmul_rn(__dmul_rn(-6.0, da), idt2),
+                                __dmul_rn(__dadd_rn(__dmul_rn(4.0, ko), __dmul_rn(2.0, kn)), idt));
+    const double a3 = __dadd_rn(__dmul_rn(__dmul_rn(12.0, da), idt3), __dmul_rn(__dmul_rn(6.0, __dadd_rn(ko, kn)), idt2));
+    // x1 = xp + a2 dt^4 / 24 + a3 dt^5 / 120 ; v1 = vp + a2 dt^3 / 6 + a3 dt^4 / 24
+    const double x1 = __dadd_rn(__dadd_rn(xp, rn_div24(__dmul_rn(a2, dt4))), rn_div120(__dmul_rn(a3, dt5)));
+    const double v1 = __dadd_rn(__dadd_rn(vp, rn_div6(__dmul_rn(a2, dt3))), rn_div24(__dmul_rn(a3, dt4)));
+    const double a2p = __dadd_rn(a2, __dmul_rn(a3, dt));
 
     // lane q gathers the three component squares of vector q (a, k, a2p, a3) by
     // rotating shuffles and sums them in component order, as dot3 does
-    const double s0 = an * an, s1 = kn * kn, s2 = a2p * a2p, s3 = a3 * a3;
+    const double s0 = __dmul_rn(an, an), s1 = __dmul_rn(kn, kn), s2 = __dmul_rn(a2p, a2p), s3 = __dmul_rn(a3, a3);
     double p0 = 0.0, p1 = 0.0, p2 = 0.0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -242,27 +276,27 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
         if (src == 1) p1 = got;
         if (src == 2) p2 = got;
     }
-    const double S = (p0 + p1) + p2;
+    const double S = __dadd_rn(__dadd_rn(p0, p1), p2);
 
-    const float fS = (float)S;
-    const float rS = sqrtf(fS);
+    const float fS = __double2float_rn(S);
+    const float rS = __fsqrt_rn(fS);
     const float rA = __shfl_sync(full, rS, g0), rK = __shfl_sync(full, rS, g0 + 1);
     const float rP = __shfl_sync(full, rS, g0 + 2), rQ = __shfl_sync(full, rS, g0 + 3);
     const float fK = __shfl_sync(full, fS, g0 + 1), fP = __shfl_sync(full, fS, g0 + 2);
     const unsigned okb = __ballot_sync(full, norm2_in_range(S));
     long long qb = 0;
     bool pos = true;
-    bool decided = aarseth_estimate(rA, rK, rP, rQ, fK, fP, (float)eta, qb);
+    bool decided = aarseth_estimate(rA, rK, rP, rQ, fK, fP, __double2float_rn(eta), qb);
     decided = decided && ((okb >> g0) & 0xFu) == 0xFu;
     if (__any_sync(full, live && !decided)) {
-        const double mag = sqrt(S);   // the four magnitudes, one per lane
+        const double mag = __dsqrt_rn(S);   // the four magnitudes, one per lane
         const double mA = __shfl_sync(full, mag, g0), mK = __shfl_sync(full, mag, g0 + 1);
         const double mP = __shfl_sync(full, mag, g0 + 2), mQ = __shfl_sync(full, mag, g0 + 3);
         const double K = __shfl_sync(full, S, g0 + 1), P = __shfl_sync(full, S, g0 + 2);
         if (!decided) {
-            const double num = mA * mP + K;
-            const double den = mK * mQ + P;
-            const double cand = den == 0.0 ? CUDART_INF : sqrt(eta * num / den);
+            const double num = __dadd_rn(__dmul_rn(mA, mP), K);
+            const double den = __dadd_rn(__dmul_rn(mK, mQ), P);
+            const double cand = den == 0.0 ? CUDART_INF : __dsqrt_rn(__ddiv_rn(__dmul_rn(eta, num), den));
             qb = pow2_floor_bits(cand);
             pos = dpositive(cand);
         }
@@ -276,17 +310,17 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
             H.a[o] = an;
             H.k[o] = kn;
             if (H.x2) {
-                H.x2[o] = ds_pack(x1);
-                H.v2[o] = ds_pack(v1);
-                H.a2[o] = ds_pack(an);
-                H.k2[o] = ds_pack(kn);
+                H.x2[o] = rn_ds_pack(x1);
+                H.v2[o] = rn_ds_pack(v1);
+                H.a2[o] = rn_ds_pack(an);
+                H.k2[o] = rn_ds_pack(kn);
             }
         } else {
             const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
             if (dt_new == 0.0) flags |= kStUnderflow;
             H.t[i] = tn;
             H.dt[i] = dt_new;
-            H.tn[i] = tn + dt_new;
+            H.tn[i] = __dadd_rn(tn, dt_new);
         }
     }
     return flags;

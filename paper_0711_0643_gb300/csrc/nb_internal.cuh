@@ -47,6 +47,13 @@ struct Tuning {
 };
 
 // Parameters of one force evaluation (both precisions).
+// State arrays ([3][np] vectors, [np] scalars) for correct_group.
+struct HState {
+    double *x, *v, *a, *k, *t, *dt, *tn;
+    float2 *x2, *v2, *a2, *k2;   // double-single copies (x2 == nullptr: none kept)
+    int64_t np;
+};
+
 struct ForceArgs {
     int64_t n;            // particles
     int64_t n_tiles;      // ceil(n / kJT); j arrays are padded to n_tiles * kJT
@@ -86,6 +93,8 @@ int force_mixed_ctas_per_sm();
 int force_f64_ctas_per_sm();
 size_t force_mixed_smem_bytes();
 
+// One-wave (or four-wave, for long items) split factor for nib i-blocks.
+int64_t wave_split(int64_t nib, int64_t n_tiles, int64_t resident);
 // Default tuning (variant, split) for an active count s.
 void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_per_sm, int *variant,
                     int *split);
@@ -110,10 +119,6 @@ struct StepArgs {
     int32_t *status;
     int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps
     double *interactions;                 // sum s*n
-    int32_t *chunk_cnt;                   // scratch for multi-CTA selection
-    double *chunk_min;
-    int32_t *done_ctr;
-    int select_ctas;
 };
 
 cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cudaStream_t st);

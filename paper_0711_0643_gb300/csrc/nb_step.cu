@@ -100,14 +100,16 @@ __global__ void state_to_ds_kernel(StepArgs A)
 // ---------------------------------------------------------------- selection
 // One CTA of 1024 threads. Keys tn_i = t_i + dt_i are non-negative doubles (+inf
 // for padding) whose bit patterns order like the values, so all comparisons run
-// on the integer pipe. Thread t owns 16 consecutive keys of each chunk of 16384
-// (two 16-byte loads per 4 keys; the padded length is a multiple of 256, so a
-// thread's 16 keys lie wholly inside or outside it). Pass 1: minimum. Pass 2:
-// per-thread counts of keys equal to the minimum, one block-wide exclusive scan,
-// and each thread writes its indices in order, so the list comes out ascending.
-// For up to 16384 particles the keys stay in registers between the passes.
-constexpr int kSelPer = 16;
-constexpr int64_t kSelChunk = (int64_t)kSelThreads * kSelPer;
+// on the integer pipe. Chunks of 16384 keys; warp w owns keys [512 w, 512 w + 512)
+// of a chunk, read as 8 coalesced segments of 64 keys (lane l holds keys 2l and
+// 2l + 1 of each segment, one 16-byte load). The padded length is a multiple of
+// 256, so a segment lies wholly inside or outside it. Pass 1: minimum. Pass 2:
+// ballots give each lane the rank of its hits inside its warp's keys (segment
+// by segment, keys in index order), one block-wide scan of the 32 warp counts
+// places the warps, and the active list comes out ascending. Up to 16384
+// particles the keys stay in registers between the passes.
+constexpr int kSelSeg = 8;                                    // segments of 64 keys per warp
+constexpr int64_t kSelChunk = (int64_t)kSelThreads * 2 * kSelSeg;   // 16384
 
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
@@ -119,19 +121,20 @@ __device__ __forceinline__ long long warp_min_ll(long long v)
     return v;
 }
 
-__device__ __forceinline__ void sel_load(const long long *key, int64_t b, int64_t np, long long *k)
+// key index of lane l's pair in segment j of warp w, chunk base c0
+__device__ __forceinline__ int64_t sel_index(int64_t c0, int warp, int j, int lane)
 {
-    if (b < np) {
-        const longlong2 *p = reinterpret_cast<const longlong2 *>(key + b);
+    return c0 + (int64_t)warp * (64 * kSelSeg) + 64 * j + 2 * lane;
+}
+
+__device__ __forceinline__ void sel_load(const long long *key, int64_t c0, int warp, int lane, int64_t np,
+                                         longlong2 *k)
+{
 #pragma unroll
-        for (int j = 0; j < kSelPer / 2; ++j) {
-            const longlong2 w = p[j];
-            k[2 * j] = w.x;
-            k[2 * j + 1] = w.y;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kSelPer; ++j) k[j] = 0x7ff0000000000000LL;
+    for (int j = 0; j < kSelSeg; ++j) {
+        const int64_t e = sel_index(c0, warp, j, lane);
+        k[j] = e < np ? *reinterpret_cast<const longlong2 *>(key + e)
+                      : make_longlong2(0x7ff0000000000000LL, 0x7ff0000000000000LL);
     }
 }
 
@@ -146,12 +149,16 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     const int64_t n = A.n, np = A.n_pad;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
     const int64_t nchunk = (np + kSelChunk - 1) / kSelChunk;
-    long long k[kSelPer];
+    const unsigned below = (1u << lane) - 1u;
+    longlong2 k[kSelSeg];
     long long m = 0x7ff0000000000000LL;   // +inf
     for (int64_t ch = 0; ch < nchunk; ++ch) {
-        sel_load(key, ch * kSelChunk + (int64_t)tid * kSelPer, np, k);
+        sel_load(key, ch * kSelChunk, warp, lane, np, k);
 #pragma unroll
-        for (int j = 0; j < kSelPer; ++j) m = k[j] < m ? k[j] : m;
+        for (int j = 0; j < kSelSeg; ++j) {
+            m = k[j].x < m ? k[j].x : m;
+            m = k[j].y < m ? k[j].y : m;
+        }
     }
     m = warp_min_ll(m);
     if (lane == 0) smin[warp] = m;
@@ -165,20 +172,19 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     const long long kmin = s_kmin;
     int out = 0;   // entries written by earlier chunks (same in every thread)
     for (int64_t ch = 0; ch < nchunk; ++ch) {
-        const int64_t b = ch * kSelChunk + (int64_t)tid * kSelPer;
-        if (nchunk > 1) sel_load(key, b, np, k);
-        unsigned hit = 0;
+        const int64_t c0 = ch * kSelChunk;
+        if (nchunk > 1) sel_load(key, c0, warp, lane, np, k);
+        // per segment: hits of the even and odd key of every lane
+        unsigned be[kSelSeg], bo[kSelSeg];
+        int wcount = 0;
 #pragma unroll
-        for (int j = 0; j < kSelPer; ++j)
-            if (k[j] == kmin && b + j < n) hit |= 1u << j;
-        const int cnt = __popc(hit);
-        int incl = cnt;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
+        for (int j = 0; j < kSelSeg; ++j) {
+            const int64_t e = sel_index(c0, warp, j, lane);
+            be[j] = __ballot_sync(0xffffffffu, k[j].x == kmin && e < n);
+            bo[j] = __ballot_sync(0xffffffffu, k[j].y == kmin && e + 1 < n);
+            wcount += __popc(be[j]) + __popc(bo[j]);
         }
-        if (lane == 31) woff[warp] = incl;
+        if (lane == 0) woff[warp] = wcount;
         __syncthreads();
         if (warp == 0) {
             const int cw = woff[lane];
@@ -192,11 +198,15 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
             if (lane == 31) wtot = wi;
         }
         __syncthreads();
-        int pos = out + woff[warp] + incl - cnt;
-        while (hit) {
-            const int j = __ffs(hit) - 1;
-            hit &= hit - 1;
-            A.idx[pos++] = (int32_t)(b + j);
+        int pos = out + woff[warp];
+#pragma unroll
+        for (int j = 0; j < kSelSeg; ++j) {
+            const int64_t e = sel_index(c0, warp, j, lane);
+            const bool he = (be[j] >> lane) & 1u, ho = (bo[j] >> lane) & 1u;
+            const int r = pos + __popc(be[j] & below) + __popc(bo[j] & below);
+            if (he) A.idx[r] = (int32_t)e;
+            if (ho) A.idx[r + (he ? 1 : 0)] = (int32_t)(e + 1);
+            pos += __popc(be[j]) + __popc(bo[j]);
         }
         out += wtot;
         __syncthreads();   // woff and wtot are rewritten by the next chunk

@@ -70,7 +70,7 @@ _SIGS = [
     ("nb_correct", C.c_int, [_P, _D]),
     ("nb_step", C.c_int, [_P]),
     ("nb_run", C.c_int, [_P, _D]),
-    ("nb_run_timed", C.c_int, [_P, _D, _P, _P]),
+    ("nb_run_timed", C.c_int, [_P, _D, _P, _P, _P]),
     ("nb_energy", C.c_int, [_P, _P, _P, _P]),
     ("nb_get_state", C.c_int, [_P, _P]),
     ("nb_set_state", C.c_int, [_P, _P]),
@@ -215,10 +215,14 @@ def nb_run(ctx, t_end):
     return _check(ctx, load().nb_run(ctx, float(t_end)))
 
 
-def nb_run_timed(ctx, t_end):
-    """Returns (force_ms, launches)."""
+def nb_run_timed(ctx, t_end, phases=False):
+    """Returns (force_ms, launches), plus a dict of summed phase times in ms
+    (select, predict, force, correct) when phases is true."""
     ms = C.c_double(); nl = C.c_int64()
-    _check(ctx, load().nb_run_timed(ctx, float(t_end), C.byref(ms), C.byref(nl)))
+    ph = (C.c_double * 4)() if phases else None
+    _check(ctx, load().nb_run_timed(ctx, float(t_end), C.byref(ms), C.byref(nl), ph))
+    if phases:
+        return ms.value, nl.value, dict(zip(("select", "predict", "force", "correct"), list(ph)))
     return ms.value, nl.value
 
 

@@ -357,10 +357,11 @@ def test_energy_conservation_plummer_1k(nb, orc, prec):
 
 
 def test_run_step_and_timed_paths_agree(nb):
-    """The graph loop (nb_run), host-driven nb_step and nb_run_timed give the same state bitwise."""
+    """The graph loop (nb_run), host-driven nb_step and nb_run_timed (with and without the
+    phase breakdown) give the same state bitwise."""
     snap = ics.plummer(3000, seed=5, eps=1.0 / 128)
     states = []
-    for mode in ("run", "timed", "step"):
+    for mode in ("run", "timed", "phases", "step"):
         with nb.Context(precision=0) as c:
             c.init(snap)
             if mode == "run":
@@ -368,6 +369,9 @@ def test_run_step_and_timed_paths_agree(nb):
             elif mode == "timed":
                 ms, nl = nb.nb_run_timed(c.ctx, 1.0 / 16)
                 assert nl > 0 and ms > 0
+            elif mode == "phases":
+                ms, nl, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
+                assert nl > 0 and ph["force"] == ms and min(ph.values()) > 0
             else:
                 while True:
                     tn, s = nb.nb_next_block(c.ctx)
