@@ -956,12 +956,14 @@ nb_status nb_autotune(nb_ctx *ctx)
             const int64_t nib = (s + I - 1) / I;
             const int64_t R = (int64_t)ctx->num_sms * occ;
             // wave-aligned splits (W = nib * S just below k full waves), the default's
-            // choice, and a few coarse ones; at most 16 waves of items
+            // choice, a few coarse ones and 1..4; more than 16 waves of items only
+            // for splits up to 4
             std::vector<int64_t> cands;
             for (int64_t S : {R / nib, 2 * R / nib, 3 * R / nib, 4 * R / nib, R / (2 * nib),
-                              wave_split(nib, ctx->n_tiles, R), ctx->n_tiles / 4, ctx->n_tiles / 16, (int64_t)1}) {
+                              wave_split(nib, ctx->n_tiles, R), ctx->n_tiles / 4, ctx->n_tiles / 16, (int64_t)1,
+                              (int64_t)2, (int64_t)3, (int64_t)4}) {
                 S = std::min<int64_t>(std::max<int64_t>(S, 1), ctx->n_tiles);
-                if (nib * S > 16 * R) continue;
+                if (nib * S > 16 * R && S > 4) continue;
                 if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
             }
             for (int64_t S : cands) {

@@ -9,15 +9,119 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 namespace nb {
 
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
-__device__ __forceinline__ int dexpo(double x) { return (int)((dbits(x) >> 52) & 0x7ff); }
+__host__ __device__ __forceinline__ long long dbits(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long b;
+    std::memcpy(&b, &x, 8);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double dfrom(long long b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double x;
+    std::memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ float ffrom(unsigned u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ int clz32(unsigned u)
+{
+#ifdef __CUDA_ARCH__
+    return __clz((int)u);
+#else
+    return u ? __builtin_clz(u) : 32;
+#endif
+}
+__host__ __device__ __forceinline__ int dexpo(double x) { return (int)((dbits(x) >> 52) & 0x7ff); }
 
 // Finite (not inf or NaN), from the exponent field alone.
 __device__ __forceinline__ bool dfinite(double x) { return dexpo(x) != 0x7ff; }
+
+// The IEEE product x * p for p = 2^e, on the integer pipe: exact exponent shift
+// when x is normal and the product stays normal, zeros keep their sign; any
+// other case (subnormal, inf, NaN, under/overflow) takes the FP64 multiply out
+// of line (a call, so the compiler cannot predicate it into the common path).
+static __device__ __noinline__ double dmul_slow(double x, double p) { return __dmul_rn(x, p); }
+__host__ __device__ __forceinline__ bool scale2_fast(long long xb, int e)
+{
+    const int ex = (int)((xb >> 52) & 0x7ff);
+    return ex != 0 && ex != 0x7ff && ex + e > 0 && ex + e < 0x7ff;
+}
+__device__ __forceinline__ double scale2(double x, int e, double p)
+{
+    const long long xb = dbits(x);
+    if (scale2_fast(xb, e)) return dfrom(xb + ((long long)e << 52));
+    if ((xb & 0x7FFFFFFFFFFFFFFFll) == 0) return x;
+    return dmul_slow(x, p);
+}
+
+// Double-single split (hi, lo) = (RN32(x), RN32(x - RN32(x))) on the integer
+// pipe, for |x| in [2^-60, 2^100] (both parts then normal floats); returns
+// false otherwise and the caller converts with the FP64 unit. hi rounds the
+// 52-bit significand to 23 bits, ties to even; x - hi is the exact remainder
+// (at most 29 bits, sign flipped when hi rounded up in magnitude), rounded to
+// 24 bits the same way.
+__host__ __device__ __forceinline__ bool ds_split_int(double x, unsigned &hi, unsigned &lo)
+{
+    const long long xb = dbits(x);
+    const int E = (int)((xb >> 52) & 0x7ff);
+    if (E < 1023 - 60 || E > 1023 + 100) return false;
+    const unsigned sign = (unsigned)((unsigned long long)xb >> 63) << 31;
+    const unsigned long long M = (unsigned long long)xb & ((1ull << 52) - 1);
+    unsigned mh = (unsigned)(M >> 29);
+    const unsigned rem = (unsigned)(M & ((1u << 29) - 1));
+    const bool up = rem > (1u << 28) || (rem == (1u << 28) && (mh & 1u));
+    int Eh = E;
+    if (up && ++mh == (1u << 23)) {
+        mh = 0;
+        ++Eh;
+    }
+    hi = sign | ((unsigned)(Eh - 896) << 23) | mh;
+    // remainder x - hi = +-L * 2^(E - 1075), L < 2^29
+    const unsigned L = up ? (1u << 29) - rem : rem;
+    if (L == 0) {
+        lo = 0u;
+        return true;
+    }
+    const unsigned lsign = up ? (sign ^ 0x80000000u) : sign;
+    const int p = 31 - clz32(L);           // top bit of L
+    int el = E - 1075 + p + 127;           // biased float exponent of the leading bit
+    unsigned ml;
+    if (p <= 23) {
+        ml = L << (23 - p);
+    } else {
+        const int sh = p - 23;
+        ml = L >> sh;
+        const unsigned r = L & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        if (r > half || (r == half && (ml & 1u))) {
+            if (++ml == (1u << 24)) {
+                ml = 1u << 23;
+                ++el;
+            }
+        }
+    }
+    lo = lsign | ((unsigned)el << 23) | (ml & 0x7fffffu);
+    return true;
+}
 
 // y / full, correctly rounded, where full = d * scale^-1 with scale a power of two
 // and c = RN(1/d). Markstein's theorem (IBM J. Res. Dev. 34, 1990): if c is within

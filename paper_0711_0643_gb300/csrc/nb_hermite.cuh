@@ -196,7 +196,7 @@ __device__ __forceinline__ double rn_div6(double y)
     const int e = dexpo(y);
     if (e >= 63 && e <= 2023) {
         const double q = __dmul_rn(y, 1.0 / 3.0);
-        return __dmul_rn(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), 0.5);
+        return scale2(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), -1, 0.5);
     }
     return __ddiv_rn(y, 6.0);
 }
@@ -205,7 +205,7 @@ __device__ __forceinline__ double rn_div24(double y)
     const int e = dexpo(y);
     if (e >= 63 && e <= 2023) {
         const double q = __dmul_rn(y, 1.0 / 3.0);
-        return __dmul_rn(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), 0.125);
+        return scale2(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), -3, 0.125);
     }
     return __ddiv_rn(y, 24.0);
 }
@@ -214,15 +214,23 @@ __device__ __forceinline__ double rn_div120(double y)
     const int e = dexpo(y);
     if (e >= 63 && e <= 2023) {
         const double q = __dmul_rn(y, 1.0 / 15.0);
-        return __dmul_rn(__fma_rn(__fma_rn(-q, 15.0, y), 1.0 / 15.0, q), 0.125);
+        return scale2(__fma_rn(__fma_rn(-q, 15.0, y), 1.0 / 15.0, q), -3, 0.125);
     }
     return __ddiv_rn(y, 120.0);
 }
-__device__ __forceinline__ float2 rn_ds_pack(double x)
+static __device__ __noinline__ float2 ds_pack_slow(double x)
 {
     const float h = __double2float_rn(x);
     return make_float2(h, __double2float_rn(__dsub_rn(x, (double)h)));
 }
+// (RN32(x), RN32(x - RN32(x))): on the integer pipe when both parts are normal floats
+__device__ __forceinline__ float2 rn_ds_pack(double x)
+{
+    unsigned h, l;
+    if (ds_split_int(x, h, l)) return make_float2(ffrom(h), ffrom(l));
+    return ds_pack_slow(x);
+}
+__device__ __forceinline__ double pow2_of(int e) { return dfrom((long long)(1023 + e) << 52); }
 
 __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
                                              double eta, double dt_max, double dt_min)
@@ -237,31 +245,50 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
     const int64_t o = c * np + i;
     const double x = H.x[o], v = H.v[o], ao = H.a[o], ko = H.k[o];
 
-    // predictor: ((x + v d) + (a d^2) / 2) + (k d^3) / 6 and (v + a d) + (k d^2) / 2
+    // predictor: ((x + v d) + (a d^2) / 2) + (k d^3) / 6 and (v + a d) + (k d^2) / 2;
+    // corrector: a2 = -6 da / dt^2 - (4 k_old + 2 k_new) / dt,
+    // a3 = 12 da / dt^3 + 6 (k_old + k_new) / dt^2, x1 = xp + a2 dt^4 / 24 + a3 dt^5 / 120,
+    // v1 = vp + a2 dt^3 / 6 + a3 dt^4 / 24, a2p = a2 + a3 dt (dt is a power of two
+    // in [2^-300, 2^300], so 1/dt^k are exact)
     const double d = __dsub_rn(tn, ti);
-    const double d2 = __dmul_rn(d, d);
-    const double d3 = __dmul_rn(d2, d);
-    const double xp = __dadd_rn(__dadd_rn(__dadd_rn(x, __dmul_rn(v, d)), __dmul_rn(__dmul_rn(ao, d2), 0.5)),
-                                rn_div6(__dmul_rn(ko, d3)));
-    const double vp = __dadd_rn(__dadd_rn(v, __dmul_rn(ao, d)), __dmul_rn(__dmul_rn(ko, d2), 0.5));
-
-    // corrector (dt is a power of two in [2^-300, 2^300]: 1/dt^k are exact)
-    const double dt2 = __dmul_rn(dt, dt);
-    const double dt3 = __dmul_rn(dt2, dt);
-    const double dt4 = __dmul_rn(dt3, dt);
-    const double dt5 = __dmul_rn(dt4, dt);
-    const double idt = recip_pow2(dt);
-    const double idt2 = __dmul_rn(idt, idt);
-    const double idt3 = __dmul_rn(idt2, idt);
     const double da = __dsub_rn(ao, an);
-    // a2 = -6 da / dt^2 - (4 k_old + 2 k_new) / dt ; a3 = 12 da / dt^3 + 6 (k_old + k_new) / dt^2
-    const double a2 = __dsub_rn(__dmul_rn(__dmul_rn(-6.0, da), idt2),
-                                __dmul_rn(__dadd_rn(__dmul_rn(4.0, ko), __dmul_rn(2.0, kn)), idt));
-    const double a3 = __dadd_rn(__dmul_rn(__dmul_rn(12.0, da), idt3), __dmul_rn(__dmul_rn(6.0, __dadd_rn(ko, kn)), idt2));
-    // x1 = xp + a2 dt^4 / 24 + a3 dt^5 / 120 ; v1 = vp + a2 dt^3 / 6 + a3 dt^4 / 24
-    const double x1 = __dadd_rn(__dadd_rn(xp, rn_div24(__dmul_rn(a2, dt4))), rn_div120(__dmul_rn(a3, dt5)));
-    const double v1 = __dadd_rn(__dadd_rn(vp, rn_div6(__dmul_rn(a2, dt3))), rn_div24(__dmul_rn(a3, dt4)));
-    const double a2p = __dadd_rn(a2, __dmul_rn(a3, dt));
+    const long long dtb = dbits(dt);
+    const int e = (int)((dtb >> 52) & 0x7ff) - 1023;
+    double x1, v1, a2, a3;
+    if (__all_sync(full, dbits(d) == dtb && e >= -204 && e <= 204)) {
+        // d = dt = 2^e and every dt^k, 1/dt^k is a normal power of two: each product
+        // with one of them (and with 2, 4, 1/2) is an exponent shift (scale2), the
+        // same bits as the FP64 multiply below
+        const double d2 = pow2_of(2 * e), d3 = pow2_of(3 * e), d4 = pow2_of(4 * e), d5 = pow2_of(5 * e);
+        const double i1 = pow2_of(-e), i2 = pow2_of(-2 * e), i3 = pow2_of(-3 * e);
+        const double xp = __dadd_rn(__dadd_rn(__dadd_rn(x, scale2(v, e, dt)), scale2(scale2(ao, 2 * e, d2), -1, 0.5)),
+                                    rn_div6(scale2(ko, 3 * e, d3)));
+        const double vp = __dadd_rn(__dadd_rn(v, scale2(ao, e, dt)), scale2(scale2(ko, 2 * e, d2), -1, 0.5));
+        a2 = __dsub_rn(scale2(__dmul_rn(-6.0, da), -2 * e, i2),
+                       scale2(__dadd_rn(scale2(ko, 2, 4.0), scale2(kn, 1, 2.0)), -e, i1));
+        a3 = __dadd_rn(scale2(__dmul_rn(12.0, da), -3 * e, i3), scale2(__dmul_rn(6.0, __dadd_rn(ko, kn)), -2 * e, i2));
+        x1 = __dadd_rn(__dadd_rn(xp, rn_div24(scale2(a2, 4 * e, d4))), rn_div120(scale2(a3, 5 * e, d5)));
+        v1 = __dadd_rn(__dadd_rn(vp, rn_div6(scale2(a2, 3 * e, d3))), rn_div24(scale2(a3, 4 * e, d4)));
+    } else {
+        const double d2 = __dmul_rn(d, d);
+        const double d3 = __dmul_rn(d2, d);
+        const double xp = __dadd_rn(__dadd_rn(__dadd_rn(x, __dmul_rn(v, d)), __dmul_rn(__dmul_rn(ao, d2), 0.5)),
+                                    rn_div6(__dmul_rn(ko, d3)));
+        const double vp = __dadd_rn(__dadd_rn(v, __dmul_rn(ao, d)), __dmul_rn(__dmul_rn(ko, d2), 0.5));
+        const double dt2 = __dmul_rn(dt, dt);
+        const double dt3 = __dmul_rn(dt2, dt);
+        const double dt4 = __dmul_rn(dt3, dt);
+        const double dt5 = __dmul_rn(dt4, dt);
+        const double idt = recip_pow2(dt);
+        const double idt2 = __dmul_rn(idt, idt);
+        const double idt3 = __dmul_rn(idt2, idt);
+        a2 = __dsub_rn(__dmul_rn(__dmul_rn(-6.0, da), idt2),
+                       __dmul_rn(__dadd_rn(__dmul_rn(4.0, ko), __dmul_rn(2.0, kn)), idt));
+        a3 = __dadd_rn(__dmul_rn(__dmul_rn(12.0, da), idt3), __dmul_rn(__dmul_rn(6.0, __dadd_rn(ko, kn)), idt2));
+        x1 = __dadd_rn(__dadd_rn(xp, rn_div24(__dmul_rn(a2, dt4))), rn_div120(__dmul_rn(a3, dt5)));
+        v1 = __dadd_rn(__dadd_rn(vp, rn_div6(__dmul_rn(a2, dt3))), rn_div24(__dmul_rn(a3, dt4)));
+    }
+    const double a2p = __dadd_rn(a2, scale2(a3, e, dt));
 
     // lane q gathers the three component squares of vector q (a, k, a2p, a3) by
     // rotating shuffles and sums them in component order, as dot3 does
