@@ -364,6 +364,11 @@ def main_gpu(args):
     if args.ensemble and rank == 0:
         ens = ensemble_bench(nb, torch, dev, sptr, stream)
 
+    # ---- Plummer N = 65536 with Salpeter masses to t = 0.5 (opt-in: slow input generation)
+    salp = None
+    if args.salpeter and rank == 0:
+        salp = salpeter_bench(nb, torch, dev, sptr, stream)
+
     # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed, one evaluation per s
     sweep = None
     if args.sweep and rank == 0:
@@ -399,7 +404,7 @@ def main_gpu(args):
             "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / len(e2e_ms)},
             "fp64_gpu": fp64,
-            "ensemble": ens,
+            "ensemble": ens, "salpeter": salp,
             "force_sweep": sweep,
             "cpu_baseline": cpu,
         }
@@ -446,7 +451,42 @@ def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
             "interactions_per_s": total_inter / (run_s + init_s),
             "block_steps_per_s": float(bs.sum()) / run_s, "block_steps": int(bs.sum()),
             "worst_abs_dE_over_E": float(dE.max()), "median_abs_dE_over_E": float(np.median(dE)),
+            "worst_member": {"index": int(np.argmax(dE)), "n": int(np.diff(off)[int(np.argmax(dE))])},
             "n_min": int(np.diff(off).min()), "n_max": int(np.diff(off).max())}
+
+
+def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
+    """Plummer N = 65536 with a Salpeter mass spectrum (slope -2.35 on [0.1, 100],
+    normalised to M = 1), eps = 1/4096, mixed precision, t = 0 -> 0.5, autotuned:
+    one timed run (init + energy + nb_run + energy) after a short warm-up run.
+    Active-set sizes span 1 to N."""
+    import ics
+    snap = ics.config(3)
+    n = snap.n
+    m_d = torch.tensor(snap.m, device=dev)
+    x_d = torch.tensor(snap.x, device=dev)
+    v_d = torch.tensor(snap.v, device=dev)
+    c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+    nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+    nb.nb_autotune(c.ctx)
+    nb.nb_run(c.ctx, 1.0 / 64)   # warm-up: graph instantiation, caches
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+    E0 = nb.nb_energy(c.ctx)[0]
+    nb.nb_run(c.ctx, t_end)
+    E1 = nb.nb_energy(c.ctx)[0]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    st = nb.nb_stats(c.ctx)
+    c.close()
+    sec = e0.elapsed_time(e1) / 1e3
+    inter = st["interactions"] + float(n) * n
+    return {"workload": f"plummer N={n} Salpeter masses [0.1, 100] slope -2.35, eps=1/4096, t=0->{t_end}, mixed",
+            "ms": sec * 1e3, "interactions_per_s": inter / sec, "block_steps": st["block_steps"],
+            "block_steps_per_s": st["block_steps"] / sec, "mean_active": st["particle_steps"] / max(st["block_steps"], 1),
+            "abs_dE_over_E": abs(E1 - E0) / abs(E0)}
 
 
 def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
@@ -514,6 +554,10 @@ def main(argv=None):
                     help="batched ensemble of 256 clusters (default on)")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
                     help="full-N force sweep on King N=2^20 (default on)")
+    ap.add_argument("--salpeter", action=argparse.BooleanOptionalAction, default=True,
+                    help="Plummer N=65536 with Salpeter masses to t=0.5 (default on; ~15 s of input generation)")
+    ap.add_argument("--salpeter-only", action="store_true",
+                    help="run only the Salpeter workload and print it")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="run only the ensemble workload and print it (profiling)")
     ap.add_argument("--ens-nc", type=int, default=256, help="systems of --ensemble-only")
@@ -536,6 +580,8 @@ def main(argv=None):
         return main_sweep(args)
     if args.ensemble_only:
         return main_ensemble(args)
+    if args.salpeter_only:
+        return main_salpeter(args)
     return main_gpu(args)
 
 
@@ -551,6 +597,22 @@ def main_ensemble(args):
     from paper_0711_0643_gb300 import nbody as nb
     nb.load()
     out = ensemble_bench(nb, torch, dev, stream.cuda_stream, stream, nc=args.ens_nc, n_hi=args.ens_nmax)
+    print(json.dumps(out))
+    return 0
+
+
+def main_salpeter(args):
+    """Only the Salpeter N = 65536 workload, printed as one JSON line (not a bench line)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+    out = salpeter_bench(nb, torch, dev, stream.cuda_stream, stream)
     print(json.dumps(out))
     return 0
 

@@ -250,7 +250,7 @@ nb_status alloc_system(nb_ctx *ctx, int64_t n)
     CK(dalloc(&ctx->a2, 3 * np));
     CK(dalloc(&ctx->k2, 3 * np));
     CK(cudaMemsetAsync(ctx->tickets, 0, (np + 1) * sizeof(int32_t), ctx->stream));
-    ctx->en_ctas = (int)((n + 127) / 128);
+    ctx->en_ctas = (int)((n + 127) / 128) * 8;   // i-tiles of 128 x up to 8 j-splits
     CK(dalloc(&ctx->en_scratch, 2 * (size_t)ctx->en_ctas));
     CK(dalloc(&ctx->out_a, 3 * np));
     CK(dalloc(&ctx->out_k, 3 * np));

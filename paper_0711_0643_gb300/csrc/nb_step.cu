@@ -378,49 +378,152 @@ __global__ void iota_kernel(int32_t *idx, int64_t n)
 // Each CTA sums its particles in a fixed order into scratch[cta][2]; a single
 // thread then adds the CTA sums in index order.
 constexpr int kEnThreads = 128;
+constexpr int kEnSplitMax = 8;   // j-splits per i-tile (the scratch holds that many partials per tile)
 
-__global__ void __launch_bounds__(kEnThreads) energy_kernel(StepArgs A, double *scratch)
+// Double-single helpers for the energy sum (this file is compiled without
+// multiply-add contraction, which the two-sum steps rely on).
+__device__ __forceinline__ void en_two_sum(float a, float b, float &s, float &e)
 {
-    __shared__ double sk[kEnThreads], sw[kEnThreads];
-    const int64_t np = A.n_pad;
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void en_fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+// (ah + al) - (bh + bl) as a normalised double-single
+__device__ __forceinline__ void en_diff(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    float s, e;
+    en_two_sum(ah, -bh, s, e);
+    e += al - bl;
+    en_fast_two_sum(s, e, h, l);
+}
+// h + l += bh + bl
+__device__ __forceinline__ void en_acc(float &h, float &l, float bh, float bl)
+{
+    float s, e;
+    en_two_sum(h, bh, s, e);
+    e += l + bl;
+    en_fast_two_sum(s, e, h, l);
+}
+
+// m_j / |r_ij| (softened) as a double-single, from double-single positions and
+// mass: r = x_j - x_i and r^2 + eps^2 to ~2^-46 relative (two-sums and exact
+// squares by FMA), q = (r^2 + eps^2)^(-1/2) from the MUFU estimate, one FP32 and
+// one double-single Newton step (the residual 1 - r^2 y^2 is exact to 2^-46),
+// error ~2^-44 relative.
+__device__ __forceinline__ void en_pair(float4 j0, float4 j1, float2 xi, float2 yi, float2 zi, float2 e2, float &th,
+                                        float &tl)
+{
+    float dh, dl, r2h, r2l, p, e;
+    en_diff(j0.x, j0.y, xi.x, xi.y, dh, dl);
+    r2h = dh * dh;
+    r2l = fmaf(dh, dh, -r2h);
+    r2l = fmaf(2.f * dh, dl, r2l);
+    en_diff(j0.z, j0.w, yi.x, yi.y, dh, dl);
+    p = dh * dh;
+    e = fmaf(dh, dh, -p);
+    e = fmaf(2.f * dh, dl, e);
+    en_acc(r2h, r2l, p, e);
+    en_diff(j1.x, j1.y, zi.x, zi.y, dh, dl);
+    p = dh * dh;
+    e = fmaf(dh, dh, -p);
+    e = fmaf(2.f * dh, dl, e);
+    en_acc(r2h, r2l, p, e);
+    en_acc(r2h, r2l, e2.x, e2.y);
+    float y = rsqrtf(r2h);
+    y = y * fmaf(-0.5f * r2h * y, y, 1.5f);
+    const float a2 = y * y;
+    const float a2e = fmaf(y, y, -a2);
+    const float c = r2h * a2;
+    const float ce = fmaf(r2h, a2, -c);
+    const float res = (1.f - c) - (ce + fmaf(r2h, a2e, r2l * a2));
+    float qh, ql;
+    en_fast_two_sum(y, 0.5f * y * res, qh, ql);
+    th = j1.z * qh;
+    tl = fmaf(j1.z, qh, -th);
+    tl = fmaf(j1.z, ql, tl);
+    tl = fmaf(j1.w, qh, tl);
+}
+
+// K and W of the current state. Grid (i-tiles of 128, j-splits): each thread
+// sums m_j / r_ij over its split's j != i in double-single on the FP32 pipe (an
+// FP64 instruction costs ~64 FP32 lanes' worth here); FP64 takes over per
+// particle (W_i = -m_i phi_i / 2, K_i = m_i v_i^2 / 2) and for the CTA and final
+// sums, all in a fixed order.
+__global__ void __launch_bounds__(kEnThreads) energy_kernel(StepArgs A, double *scratch, int S)
+{
+    __shared__ float4 sj[kEnThreads][2];
+    __shared__ double sk[kEnThreads / 32], sw[kEnThreads / 32];
+    const int64_t n = A.n, np = A.n_pad;
     const int64_t i = (int64_t)blockIdx.x * kEnThreads + threadIdx.x;
-    double ek = 0.0, ew = 0.0;
-    if (i < A.n) {
-        const double xi = A.x[i], yi = A.x[np + i], zi = A.x[2 * np + i];
-        double phi = 0.0;
-        for (int64_t j = 0; j < A.n; ++j) {
-            const double dx = __ldg(A.x + j) - xi;
-            const double dy = __ldg(A.x + np + j) - yi;
-            const double dz = __ldg(A.x + 2 * np + j) - zi;
-            const double r2 = dx * dx + dy * dy + dz * dz + A.eps2;
-            const double q = (j == i) ? 0.0 : rsqrt(r2);
-            phi -= __ldg(A.m + j) * q;
-        }
-        const double vx = A.v[i], vy = A.v[np + i], vz = A.v[2 * np + i];
-        ek = 0.5 * A.m[i] * (vx * vx + vy * vy + vz * vz);
-        ew = 0.5 * A.m[i] * phi;
-    }
-    sk[threadIdx.x] = ek;
-    sw[threadIdx.x] = ew;
-    __syncthreads();
-    for (int h = kEnThreads / 2; h >= 1; h >>= 1) {
-        if (threadIdx.x < h) {
-            sk[threadIdx.x] += sk[threadIdx.x + h];
-            sw[threadIdx.x] += sw[threadIdx.x + h];
+    const int by = blockIdx.y;
+    const bool live = i < n;
+    const int64_t ii = live ? i : 0;
+    const float2 xi = rn_ds_pack(A.x[ii]), yi = rn_ds_pack(A.x[np + ii]), zi = rn_ds_pack(A.x[2 * np + ii]);
+    const float2 e2 = rn_ds_pack(A.eps2);
+    float ph = 0.f, pl = 0.f;
+    const int64_t ntile = (n + kEnThreads - 1) / kEnThreads;
+    const int64_t per = (ntile + S - 1) / S;
+    const int64_t t0 = (int64_t)by * per;
+    const int64_t t1 = t0 + per < ntile ? t0 + per : ntile;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t j = t * kEnThreads + threadIdx.x;
+        __syncthreads();
+        if (j < n) {
+            const float2 x = rn_ds_pack(A.x[j]), y = rn_ds_pack(A.x[np + j]), z = rn_ds_pack(A.x[2 * np + j]);
+            const float2 m = rn_ds_pack(A.m[j]);
+            sj[threadIdx.x][0] = make_float4(x.x, x.y, y.x, y.y);
+            sj[threadIdx.x][1] = make_float4(z.x, z.y, m.x, m.y);
         }
         __syncthreads();
+        const int jn = (int)(n - t * kEnThreads < kEnThreads ? n - t * kEnThreads : kEnThreads);
+        const int self = (int)(i - t * kEnThreads);   // tile slot of i, if it is in this tile
+        for (int q = 0; q < jn; ++q) {
+            float th, tl;
+            en_pair(sj[q][0], sj[q][1], xi, yi, zi, e2, th, tl);
+            if (q != self) en_acc(ph, pl, th, tl);
+        }
     }
+    double ek = 0.0, ew = 0.0;
+    if (live) {
+        const double mi = A.m[i];
+        ew = -0.5 * mi * ((double)ph + (double)pl);
+        if (by == 0) {
+            const double vx = A.v[i], vy = A.v[np + i], vz = A.v[2 * np + i];
+            ek = 0.5 * mi * (vx * vx + vy * vy + vz * vz);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        ek += __shfl_down_sync(0xffffffffu, ek, off);
+        ew += __shfl_down_sync(0xffffffffu, ew, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sk[threadIdx.x >> 5] = ek;
+        sw[threadIdx.x >> 5] = ew;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        scratch[2 * blockIdx.x] = sk[0];
-        scratch[2 * blockIdx.x + 1] = sw[0];
+        double K = 0.0, W = 0.0;
+        for (int w = 0; w < kEnThreads / 32; ++w) {
+            K += sk[w];
+            W += sw[w];
+        }
+        const int64_t slot = (int64_t)blockIdx.x * S + by;
+        scratch[2 * slot] = K;
+        scratch[2 * slot + 1] = W;
     }
 }
 
-__global__ void energy_final_kernel(const double *scratch, int nb, double *out)
+__global__ void energy_final_kernel(const double *scratch, int64_t nslots, double *out)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double K = 0.0, W = 0.0;
-        for (int b = 0; b < nb; ++b) {
+        for (int64_t b = 0; b < nslots; ++b) {
             K += scratch[2 * b];
             W += scratch[2 * b + 1];
         }
@@ -534,10 +637,16 @@ cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st)
 
 cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, double *out, cudaStream_t st)
 {
-    const int nb = (int)((a.n + kEnThreads - 1) / kEnThreads);
-    if (nb > scratch_ctas) return cudaErrorInvalidValue;
-    energy_kernel<<<nb, kEnThreads, 0, st>>>(a, scratch);
-    energy_final_kernel<<<1, 32, 0, st>>>(scratch, nb, out);
+    const int64_t nbx = (a.n + kEnThreads - 1) / kEnThreads;
+    // j-splits so that the grid covers the GPU several times over; the scratch
+    // holds kEnSplitMax partials per i-tile
+    int64_t S = (1216 + nbx - 1) / nbx;
+    if (S > kEnSplitMax) S = kEnSplitMax;
+    if (S > nbx) S = nbx;
+    if (S < 1) S = 1;
+    if (nbx * S > scratch_ctas) return cudaErrorInvalidValue;
+    energy_kernel<<<dim3((unsigned)nbx, (unsigned)S), kEnThreads, 0, st>>>(a, scratch, (int)S);
+    energy_final_kernel<<<1, 32, 0, st>>>(scratch, nbx * S, out);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,30 @@ def test_ensemble_deterministic_and_independent(nb):
         np.testing.assert_array_equal(alone[key], states[0][key][sl])
 
 
+def test_ensemble_largest_energy_error_member_matches_oracle(nb, orc):
+    """Member 46 (N = 4633, eps = 4/N) of the 256-cluster workload (N log-uniform in
+    [256, 8192], seed 20071110) has that workload's largest |dE/E| at t = 1 on the GPU.
+    The oracle integrating the same member gives the same energy error (a close
+    encounter at this softening), so the GPU run must agree within 2x plus a floor."""
+    members = ics.ensemble(256, ics.BASE_SEED + 4, n_lo=256, n_hi=8192)
+    s = members[46]
+    assert s.n == 4633
+    off, m, x, v, e2 = _pack([s])
+    with nb.Context() as c:
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        E0 = nb.nb_ensemble_energy(c.ctx, 1)[0]
+        nb.nb_ensemble_run(c.ctx, 1.0)
+        E1 = nb.nb_ensemble_energy(c.ctx, 1)[0]
+    sysr = orc.System(s.m, s.x, s.v, s.eps2, nthreads=orc.default_threads())
+    Er0 = sysr.energy()
+    assert sysr.run(1.0) == 0
+    dEr = abs(sysr.energy() - Er0) / abs(Er0)
+    dE = abs(E1 - E0) / abs(E0)
+    print(f"member 46: |dE/E| GPU {dE:.6e}, oracle {dEr:.6e}")
+    assert dEr > 1e-6                       # the encounter is there in the oracle too
+    assert dE <= 2 * dEr + 1e-9 and dEr <= 2 * dE + 1e-9
+
+
 def test_ensemble_argument_errors(nb):
     with nb.Context() as c:
         with pytest.raises(nb.NbError) as e:
