@@ -1,9 +1,10 @@
 // Double-single (float hi + float lo) arithmetic for the mixed-precision
 // predictor: the error-free transformations two-sum (Knuth) and two-product
 // (Dekker, with a fused multiply-add) give ~48-bit sums and products on the
-// FP32 pipe. Including translation units are compiled with -fmad=false, so no
-// a*b+c pattern below is contracted behind our back; every fused multiply-add
-// is an explicit fmaf.
+// FP32 pipe. The error-free transformations contain no multiply feeding an add
+// (the products are explicit fmaf), and the one plain FP32 expression uses
+// round-to-nearest intrinsics, so the results do not depend on whether the
+// including file lets the compiler contract multiply-adds.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -76,7 +77,7 @@ __device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, c
         const DS xp = ds_add(DS{X.x, X.y}, t);
         ph[c] = xp.hi;
         pl[c] = xp.lo;
-        pv[c] = (V.x + d.hi * (A.x + d.hi * (0.5f * K.x))) + V.y;
+        pv[c] = __fadd_rn(__fadd_rn(V.x, __fmul_rn(d.hi, __fadd_rn(A.x, __fmul_rn(d.hi, __fmul_rn(0.5f, K.x))))), V.y);
     }
     hi = make_float4(ph[0], ph[1], ph[2], m);
     lo = make_float4(pl[0], pl[1], pl[2], 0.f);
