@@ -102,6 +102,8 @@ struct __align__(128) Smem {
     float2 red[kThreads / 32][kMaxRC];
     uint64_t bar[kStages];
     uint64_t inject_bar;
+    int64_t s;                 // active count of this launch
+    Tuning tune;               // the device tuning table, read once per CTA
     int abort;
     int last;
 };
@@ -210,6 +212,17 @@ template <int R>
 __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t p0 = t0 * kPT, p1 = t1 * kPT;
+    // this thread's first pair record moves into L1 while the i-particle loads
+    // are in flight (a prefetch holds no registers)
+    if (p0 + tid < p1) {
+        const char *a = reinterpret_cast<const char *>(A.j.p + p0 + tid);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a + 64));
+    }
     IPk ip[R];
     int32_t gi[R];
 #pragma unroll
@@ -219,18 +232,17 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
         ip[r] = ipk_of(jrec_load(A.j.p, gi[r]));
     }
     const float2 e2 = make_float2(A.eps2f, A.eps2f);
-    const int64_t tper = (A.n_tiles + S - 1) / S;
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
-    const int64_t p0 = t0 * kPT, p1 = t1 * kPT;
     AccPk p[R];
     Acc7 hi[R], lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
     int cnt = 0;
     for (int64_t pp = p0 + tid; pp < p1; pp += kThreads) {
-        const float4 *q = A.j.p[pp].q;
-        const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3), q4 = __ldg(q + 4);
+        float4 q0, q1, q2, q3, q4;
+        {
+            const float4 *q = A.j.p[pp].q;
+            q0 = __ldg(q); q1 = __ldg(q + 1); q2 = __ldg(q + 2); q3 = __ldg(q + 3); q4 = __ldg(q + 4);
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r)
             pair_packed<true>(q0, q1, q2, q3, q4, ip[r], e2, p[r], 2 * pp == gi[r], 2 * pp + 1 == gi[r]);
@@ -308,6 +320,15 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     constexpr int kFoldTiles = PPT >= kFoldPairs / 2 ? 0 : (kFoldPairs / 2) / PPT;   // 0: folded inside the sweep
     static_assert(TJ <= 32 && (32 % TJ) == 0, "TJ must divide a warp");
     const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t t0 = (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    // the first tiles are in flight before the i-particle loads
+    if (tid == 0) {
+        const int64_t pro = nt < kStages - 1 ? nt : kStages - 1;
+        for (int64_t q = 0; q < pro; ++q) issue_tile(A, sm, t0 + q, (int)((git + q) % kStages));
+    }
 
     IPk ip[R];
     int32_t gi[R];
@@ -323,20 +344,10 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     const int64_t ib1 = (ib0 + I < s ? ib0 + I : s) - 1;
     const int64_t imin = A.idx[ib0], imax = A.idx[ib1];
 
-    const int64_t tper = (A.n_tiles + S - 1) / S;
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
-    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
-
     AccPk p[R];
     Acc7 hi[R], lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
-
-    if (tid == 0) {
-        const int64_t pro = nt < kStages - 1 ? nt : kStages - 1;
-        for (int64_t q = 0; q < pro; ++q) issue_tile(A, sm, t0 + q, (int)((git + q) % kStages));
-    }
     int fc = 0;
     for (int64_t q = 0; q < nt; ++q) {
         const uint32_t g = git + (uint32_t)q;
@@ -404,9 +415,17 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         mbar_init(&sm->inject_bar, 1);
         fence_mbar_init();
         sm->abort = 0;
+        sm->s = *A.s;
+    }
+    // the active count and the whole tuning table in one round trip
+    if (A.force_variant < 0 && tid < 2 * kBuckets) {
+        if (tid < kBuckets)
+            sm->tune.variant[tid] = A.tune->variant[tid];
+        else
+            sm->tune.split[tid - kBuckets] = A.tune->split[tid - kBuckets];
     }
     __syncthreads();
-    const int64_t s = *A.s;
+    const int64_t s = sm->s;
     if (s <= 0) return;
     if (A.inject) {
         // Test hook: wait on a barrier that no one arrives on; the spin limit must
@@ -420,9 +439,9 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         S = A.force_split;
     } else {
         const int b = bucket_of(s);
-        variant = A.tune->variant[b];
+        variant = sm->tune.variant[b];
         if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
-        S = table_split(A.tune->split[b], b, s, A.n, mixed_I(variant));
+        S = table_split(sm->tune.split[b], b, s, A.n, mixed_I(variant));
     }
     if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
     S = clamp_split(S, A.n_tiles, s, A.part_cap);
