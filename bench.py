@@ -316,8 +316,12 @@ def main_gpu(args):
     sm_mhz = clk["sm_mhz"] or clk_rf_s["sm_mhz"] or load_peaks().get("clocks_under_load", {}).get("sm_mhz_median")
     peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None
     achieved = FLOP_PER_INTERACTION * st_rf["interactions"] / (force_ms / 1e3) / 1e12
+    traffic = force_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None,
+                "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                "traffic_basis": "mean DRAM read+write bytes per force launch, cold-cache ncu capture of this "
+                                 "workload to t = 1/64 (profiles/force_traffic_plummer_n16384_t1over64.md)"
+                                 if traffic else None,
                 "kernel": "force_mixed_kernel", "launches": nlaunch,
                 "avg_launch_us": 1e3 * force_ms / max(nlaunch, 1),
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz} MHz (median SM clock "
@@ -410,6 +414,29 @@ def main_gpu(args):
         }
         print(json.dumps(line))
     return 0
+
+
+def force_traffic():
+    """Per-launch DRAM traffic of the force kernel on this workload, from the committed ncu
+    summary, or None when the kernel sources have changed since it was taken."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    prof = os.path.join(root, "profiles", "force_traffic_plummer_n16384_t1over64.md")
+    srcs = ["nb_force.cu", "nb_pair.cuh", "nb_internal.cuh"]
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(os.path.join(root, "paper_0711_0643_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() not in text:
+            return None
+        for line in text.splitlines():
+            if line.startswith("traffic_bytes_per_launch:"):
+                return float(line.split(":")[1])
+    except OSError:
+        return None
+    return None
 
 
 def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
