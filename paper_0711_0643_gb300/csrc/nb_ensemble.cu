@@ -45,6 +45,7 @@ constexpr int kEnsThreads = 256;
 constexpr int kEnsTile = 256;
 constexpr int kEnsSplitMax = 1024;        // j-split (every CTA takes all active i) when s <= this
 constexpr int kEnsPartPerCluster = 16 * kEnsSplitMax;   // C * s_max entries of 8 float2
+constexpr int kEnsSlots = kEnsPartPerCluster / 16;       // entries per CTA in the i-split and start-up rounds
 constexpr int64_t kEnsMaxN = int64_t(1) << 19;          // largest system one cluster takes
 
 struct EnsArgs {
@@ -69,7 +70,7 @@ struct EnsArgs {
 };
 
 struct EnsSmem {
-    float4 hi[kEnsTile], lo[kEnsTile], vel[kEnsTile];
+    JPair tile[kEnsTile / 2];   // a j-tile as pair records (two particles' fields per float4)
     float2 red[kEnsThreads / 32][14];
     double dred[kEnsThreads / 32][2];
     long long kmin;
@@ -82,53 +83,49 @@ struct EnsSmem {
 
 // ------------------------------------------------------------- force (CTA)
 
-// Records of j in [j0, j1) of one member into shared memory, far-away massless
-// padding past j1.
+// Records of j in [j0, j1) of one member into shared memory as pair records
+// (the layout of the packed pair arithmetic), far-away massless padding past j1.
 __device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_t jt, int64_t j1, EnsSmem *sm)
 {
     const int q = threadIdx.x;
     const int64_t j = jt + q;
     if (j < j1) {
-        sm->hi[q] = E.jh[base + j];
-        sm->lo[q] = E.jl[base + j];
-        sm->vel[q] = E.jv[base + j];
+        const float4 h = E.jh[base + j], l = E.jl[base + j], w = E.jv[base + j];
+        jrec_store(sm->tile, q, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
     } else {
-        sm->hi[q] = make_float4(1e18f, 1e18f, 1e18f, 0.f);
-        sm->lo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        sm->vel[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        jrec_store(sm->tile, q, 1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     }
 }
 
-enum { kModeInit = 0, kModeFinal = 1, kModePartial = 2 };
-
 // Forces on the active positions [p0, p1) of list act (member-relative particle
-// indices, ascending) from the member's j in [j0, j1). MODE: kModeInit writes
-// a, k and the first step; kModeFinal runs the corrector; kModePartial stores
-// (hi, lo) partials for rank `rank` in the cluster's partial buffer.
-template <int R, int TJ, int MODE>
-__device__ void cta_force(const EnsArgs &E, int mem, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
-                          int64_t j0, int64_t j1, float eps2f, double tblock, float2 *part, int rank, int64_t s,
-                          EnsSmem *sm, int &flags)
+// indices, ascending) from the member's j in [j0, j1), as (hi, lo) float pairs
+// into part: position pp goes to slot slot0 + pp - p0 (7 values of kPartStride).
+template <int R, int TJ>
+__device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1, int64_t j0,
+                          int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm)
 {
     constexpr int TI = kEnsThreads / TJ;
     constexpr int I = TI * R;
-    constexpr int JPT = kEnsTile / TJ;
-    constexpr int CH = JPT < kFoldPairs ? JPT : kFoldPairs;
-    constexpr int kFoldTiles = JPT >= kFoldPairs ? 0 : kFoldPairs / JPT;
+    constexpr int PPT = (kEnsTile / 2) / TJ;                  // pair records per thread per tile
+    constexpr int FP = kFoldPairs / 2;                       // records per fold
+    constexpr int CH = PPT < FP ? PPT : FP;
+    constexpr int kFoldTiles = PPT >= FP ? 0 : FP / PPT;
     const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+    const float2 e2 = make_float2(eps2f, eps2f);
     for (int64_t pb = p0; pb < p1; pb += I) {
         const int64_t pe = pb + I < p1 ? pb + I : p1;
-        IPart ip[R];
+        IPk ip[R];
         int32_t gi[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int64_t p = pb + (int64_t)r * TI + ti;
             gi[r] = act[p < pe ? p : pe - 1];
-            float4 h = E.jh[base + gi[r]], l = E.jl[base + gi[r]], w = E.jv[base + gi[r]];
-            ip[r] = IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z};
+            const float4 h = E.jh[base + gi[r]], l = E.jl[base + gi[r]], w = E.jv[base + gi[r]];
+            ip[r] = ipk_of(IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z});
         }
         const int64_t imin = act[pb], imax = act[pe - 1];
-        Acc7 p[R], hi[R], lo[R];
+        AccPk p[R];
+        Acc7 hi[R], lo[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
         int fc = 0;
@@ -137,26 +134,32 @@ __device__ void cta_force(const EnsArgs &E, int mem, int64_t base, const int32_t
             load_tile(E, base, jt, j1, sm);
             __syncthreads();
             const bool masked = jt <= imax && jt + kEnsTile - 1 >= imin;
+            // pair records holding real particles in this tile (the rest is padding)
+            const int npairs = (int)((j1 - jt < kEnsTile ? j1 - jt : kEnsTile) + 1) / 2;
 #pragma unroll 1
-            for (int c0 = 0; c0 < JPT; c0 += CH) {
+            for (int c0 = 0; c0 < PPT && c0 * TJ < npairs; c0 += CH) {
                 if (masked) {
 #pragma unroll 4
-                    for (int q = 0; q < CH; ++q) {
-                        const int jj = tj + (c0 + q) * TJ;
-                        const float4 h = sm->hi[jj], l = sm->lo[jj], w = sm->vel[jj];
+                    for (int u = 0; u < CH; ++u) {
+                        const int pp = tj + (c0 + u) * TJ;
+                        const float4 *Q = sm->tile[pp].q;
+                        const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
+                        const int64_t ja = jt + 2 * pp;
 #pragma unroll
-                        for (int r = 0; r < R; ++r) pair_mixed<true>(h, l, w, ip[r], eps2f, p[r], jt + jj == gi[r]);
+                        for (int r = 0; r < R; ++r)
+                            pair_packed<true>(q0, q1, q2, q3, q4, ip[r], e2, p[r], ja == gi[r], ja + 1 == gi[r]);
                     }
                 } else {
 #pragma unroll 4
-                    for (int q = 0; q < CH; ++q) {
-                        const int jj = tj + (c0 + q) * TJ;
-                        const float4 h = sm->hi[jj], l = sm->lo[jj], w = sm->vel[jj];
+                    for (int u = 0; u < CH; ++u) {
+                        const int pp = tj + (c0 + u) * TJ;
+                        const float4 *Q = sm->tile[pp].q;
+                        const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
 #pragma unroll
-                        for (int r = 0; r < R; ++r) pair_mixed<false>(h, l, w, ip[r], eps2f, p[r], false);
+                        for (int r = 0; r < R; ++r) pair_packed<false>(q0, q1, q2, q3, q4, ip[r], e2, p[r], false, false);
                     }
                 }
-                if (JPT >= kFoldPairs) {
+                if (PPT >= FP) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
                 }
@@ -177,63 +180,32 @@ __device__ void cta_force(const EnsArgs &E, int mem, int64_t base, const int32_t
             for (int r = 0; r < R; ++r) {
                 const int64_t pp = pb + (int64_t)r * TI + ti;
                 if (pp >= pe) continue;
-                if (MODE == kModePartial) {
-                    float2 *dst = part + ((int64_t)rank * s + pp) * kPartStride;
+                float2 *dst = part + (slot0 + pp - p0) * kPartStride;
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi[r], c), acc_get(lo[r], c));
-                } else {
-                    double an[3], kn[3];
-                    an[0] = (double)hi[r].ax + (double)lo[r].ax;
-                    an[1] = (double)hi[r].ay + (double)lo[r].ay;
-                    an[2] = (double)hi[r].az + (double)lo[r].az;
-                    kn[0] = (double)hi[r].kx + (double)lo[r].kx;
-                    kn[1] = (double)hi[r].ky + (double)lo[r].ky;
-                    kn[2] = (double)hi[r].kz + (double)lo[r].kz;
-                    const int64_t i = base + gi[r];
-                    if (MODE == kModeInit) {
-                        bool fin = true;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            E.a[c * E.np + i] = an[c];
-                            E.k[c * E.np + i] = kn[c];
-                            E.a2[c * E.np + i] = ds_pack(an[c]);
-                            E.k2[c * E.np + i] = ds_pack(kn[c]);
-                            fin = fin && isfinite(an[c]) && isfinite(kn[c]);
-                        }
-                        const double d0 = initial_step(an, kn, E.eta, E.dt_max, E.dt_min);
-                        if (!fin) flags |= kStNonfinite;
-                        if (d0 == 0.0) flags |= kStUnderflow;
-                        E.t[i] = 0.0;
-                        E.dt[i] = d0;
-                        E.tn[i] = 0.0 + d0;
-                    } else {
-                        flags |= hermite_correct(E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np,
-                                                 i, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
-                    }
-                }
+                for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi[r], c), acc_get(lo[r], c));
             }
         }
     }
 }
 
 // Size-adapted dispatch of cta_force.
-template <int MODE>
-__device__ void cta_force_any(const EnsArgs &E, int mem, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
-                              int64_t j0, int64_t j1, float eps2f, double tblock, float2 *part, int rank, int64_t s,
-                              EnsSmem *sm, int &flags)
+__device__ __noinline__ void cta_force_any(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1, int64_t j0,
+                              int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm)
 {
     const int64_t ni = p1 - p0;
     if (ni <= 0) return;
+    // one i-particle per thread group (R = 1; two would not fit the registers of
+    // the packed form); TJ threads share it
     if (ni <= 8)
-        cta_force<1, 32, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+        cta_force<1, 32>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+    else if (ni <= 32)
+        cta_force<1, 8>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
     else if (ni <= 64)
-        cta_force<2, 8, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+        cta_force<1, 4>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
     else if (ni <= 128)
-        cta_force<2, 4, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
-    else if (ni <= 256)
-        cta_force<2, 2, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+        cta_force<1, 2>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
     else
-        cta_force<2, 1, MODE>(E, mem, base, act, p0, p1, j0, j1, eps2f, tblock, part, rank, s, sm, flags);
+        cta_force<1, 1>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
 }
 
 // ---------------------------------------------------------------- phases
@@ -347,7 +319,38 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
             predict_chunk(E, base, c0, c1, 0.0);
             __threadfence();
             cluster.sync();
-            cta_force_any<kModeInit>(E, mem, base, act, c0, c1, 0, N, eps2f, 0.0, part, rank, N, sm, flags);
+            // own particles in rounds of kEnsSlots: sums into this CTA's slots, then a, k,
+            // their double-single copies and the first step per particle
+            for (int64_t r0 = c0; r0 < c1; r0 += kEnsSlots) {
+                const int64_t r1 = r0 + kEnsSlots < c1 ? r0 + kEnsSlots : c1;
+                const int64_t slot0 = (int64_t)rank * kEnsSlots;
+                cta_force_any(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
+                __syncthreads();
+                for (int64_t pp = r0 + tid; pp < r1; pp += kEnsThreads) {
+                    const float2 *src = part + (slot0 + pp - r0) * kPartStride;
+                    double an[3], kn[3];
+                    bool fin = true;
+                    const int64_t i = base + act[pp];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 va = __ldcg(src + c), vk = __ldcg(src + 3 + c);
+                        an[c] = (double)va.x + (double)va.y;
+                        kn[c] = (double)vk.x + (double)vk.y;
+                        E.a[c * E.np + i] = an[c];
+                        E.k[c * E.np + i] = kn[c];
+                        E.a2[c * E.np + i] = ds_pack(an[c]);
+                        E.k2[c * E.np + i] = ds_pack(kn[c]);
+                        fin = fin && isfinite(an[c]) && isfinite(kn[c]);
+                    }
+                    const double d0 = initial_step(an, kn, E.eta, E.dt_max, E.dt_min);
+                    if (!fin) flags |= kStNonfinite;
+                    if (d0 == 0.0) flags |= kStUnderflow;
+                    E.t[i] = 0.0;
+                    E.dt[i] = d0;
+                    E.tn[i] = 0.0 + d0;
+                }
+                __syncthreads();
+            }
             __threadfence();
             cluster.sync();
             if (rank == 0 && tid == 0) {
@@ -427,17 +430,36 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
             cluster.sync();
             // ---- force and correction
             if (s > kEnsSplitMax) {
+                // i-split: this CTA's share against every j, in rounds of kEnsSlots through
+                // its own slots, each round corrected by four-lane groups
                 const int64_t share = (s + C - 1) / C;
                 const int64_t p0 = (int64_t)rank * share < s ? (int64_t)rank * share : s;
                 const int64_t p1 = p0 + share < s ? p0 + share : s;
-                cta_force_any<kModeFinal>(E, mem, base, act, p0, p1, 0, N, eps2f, tblock, part, rank, s, sm, flags);
+                const int64_t slot0 = (int64_t)rank * kEnsSlots;
+                const int cq = (tid & 3) < 3 ? (tid & 3) : 2;
+                const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
+                for (int64_t r0 = p0; r0 < p1; r0 += kEnsSlots) {
+                    const int64_t r1 = r0 + kEnsSlots < p1 ? r0 + kEnsSlots : p1;
+                    cta_force_any(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
+                    __syncthreads();
+                    for (int64_t b0 = r0; b0 < r1; b0 += kEnsThreads / 4) {
+                        const int64_t pp = b0 + (tid >> 2);
+                        const bool live = pp < r1;
+                        const int64_t pps = live ? pp : r0;
+                        const float2 *src = part + (slot0 + pps - r0) * kPartStride;
+                        const float2 va = __ldcg(src + cq), vk = __ldcg(src + 3 + cq);
+                        const double an = (double)va.x + (double)va.y, kn = (double)vk.x + (double)vk.y;
+                        flags |= correct_group(H, base + act[pps], live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                    }
+                    __syncthreads();
+                }
             } else {
-                const int64_t jc = ((N + C - 1) / C + kEnsTile - 1) / kEnsTile * kEnsTile;
+                // every CTA takes an even-aligned share of j (pair records stay whole)
+                const int64_t jc = ((N + C - 1) / C + 1) / 2 * 2;
                 const int64_t j0 = (int64_t)rank * jc < N ? (int64_t)rank * jc : N;
                 const int64_t j1 = j0 + jc < N ? j0 + jc : N;
                 if (j1 > j0) {
-                    cta_force_any<kModePartial>(E, mem, base, act, 0, s, j0, j1, eps2f, tblock, part, rank, s, sm,
-                                                flags);
+                    cta_force_any(E, base, act, 0, s, j0, j1, eps2f, part, (int64_t)rank * s, sm);
                 } else {
                     for (int64_t q = tid; q < s * 7; q += kEnsThreads)
                         part[((int64_t)rank * s + q / 7) * kPartStride + q % 7] = make_float2(0.f, 0.f);
