@@ -377,6 +377,16 @@ def main_gpu(args):
     sweep = None
     if args.sweep and rank == 0:
         sweep = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz)
+        # mixed vs FP64 kernels on the same model at N = 131072 (an FP64 pass over N = 2^20
+        # would take a minute): interactions/s per s, both autotuned
+        sl = (1, 64, 1024, 16384)
+        mx = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=131072, s_list=sl)
+        f64 = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=131072, s_list=sl,
+                          precision=nb.NB_PREC_FP64)
+        sweep["mixed_vs_fp64_n131072"] = [
+            {"s": a["s"], "mixed_interactions_per_s": a["interactions_per_s"],
+             "fp64_interactions_per_s": b["interactions_per_s"],
+             "speedup": a["interactions_per_s"] / b["interactions_per_s"]} for a, b in zip(mx["points"], f64["points"])]
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -401,7 +411,7 @@ def main_gpu(args):
             "config": dict(WORKLOAD, l2="flushed (256 MB write) before every timed step",
                            parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             "block_steps_per_s": dist_sum(bsteps * args.steps, dev) / (total_ms / 1e3),
-            "block_steps": bsteps, "abs_dE_over_E": dE,
+            "block_steps": bsteps, "abs_dE_over_E": dE, "block_size_hist": size_hist(st),
             "gpu_launches": launches * args.steps,
             "clocks": clk,
             "roofline": roofline,
@@ -414,6 +424,11 @@ def main_gpu(args):
         }
         print(json.dumps(line))
     return 0
+
+
+def size_hist(st):
+    """Block steps per block-size bucket, {upper bound 2^b: count} for the non-empty buckets."""
+    return {str(1 << b): int(c) for b, c in enumerate(st["size_hist"]) if c}
 
 
 def force_traffic():
@@ -513,7 +528,7 @@ def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
     return {"workload": f"plummer N={n} Salpeter masses [0.1, 100] slope -2.35, eps=1/4096, t=0->{t_end}, mixed",
             "ms": sec * 1e3, "interactions_per_s": inter / sec, "block_steps": st["block_steps"],
             "block_steps_per_s": st["block_steps"] / sec, "mean_active": st["particle_steps"] / max(st["block_steps"], 1),
-            "abs_dE_over_E": abs(E1 - E0) / abs(E0)}
+            "abs_dE_over_E": abs(E1 - E0) / abs(E0), "block_size_hist": size_hist(st)}
 
 
 def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
@@ -559,8 +574,17 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
         ips = s * float(n) / sec
         tfl = FLOP_PER_INTERACTION * ips / 1e12
         peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None
-        out["points"].append({"s": s, "ms": sec * 1e3, "interactions_per_s": ips, "tflops": tfl,
-                              "frac_fp32_peak": tfl / peak if peak else None})
+        point = {"s": s, "ms": sec * 1e3, "interactions_per_s": ips, "tflops": tfl,
+                 "frac_fp32_peak": tfl / peak if peak else None}
+        hbm = load_peaks().get("hbm_gbs")
+        if peak and hbm:
+            # the roof of this point: the longer of the FP32 time (60 flop per interaction) and
+            # the HBM time of its algorithmic bytes (N j-records of 40 B, s x (40 B + 56 B))
+            t_fp32 = FLOP_PER_INTERACTION * s * float(n) / (peak * 1e12)
+            t_hbm = (40.0 * n + 96.0 * s) / (hbm * 1e9)
+            point["roof_bound"] = "fp32" if t_fp32 >= t_hbm else "hbm"
+            point["roof_frac"] = max(t_fp32, t_hbm) / sec
+        out["points"].append(point)
     c.close()
     return out
 

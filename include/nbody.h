@@ -65,12 +65,17 @@ typedef struct {
                              nothing completes, so its spin limit must expire */
 } nb_config;
 
+/* Buckets of the block-size histogram: bucket b counts block steps with
+ * 2^(b-1) < s <= 2^b (b = 0: s = 1). */
+#define NB_SIZE_BUCKETS 32
+
 /* Counters since nb_init (block steps, particle steps sum s, interactions sum s*N). */
 typedef struct {
     int64_t block_steps;
     int64_t particle_steps;
     double interactions;
-    double t_now;          /* largest t_i */
+    double t_now;                         /* largest t_i */
+    int64_t size_hist[NB_SIZE_BUCKETS];   /* block steps per block-size bucket */
 } nb_counters;
 
 /* Full particle state; arrays of length n ([n][3] for vectors), caller-owned. */

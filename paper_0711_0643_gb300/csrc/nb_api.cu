@@ -333,6 +333,7 @@ nb_status init_forces(nb_ctx *ctx)
     CK(launch_force_ctx(ctx));
     CK(launch_init_steps(A, ctx->stream));
     CK(cudaMemsetAsync(ctx->counters, 0, 2 * sizeof(int64_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters + 3, 0, NB_SIZE_BUCKETS * sizeof(int64_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->interactions, 0, sizeof(double), ctx->stream));
     ctx->have_state = true;
     ctx->forces_pending = false;
@@ -485,13 +486,13 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
     bool ok = dalloc(&ctx->s, 1) == cudaSuccess && dalloc(&ctx->t_next, 1) == cudaSuccess &&
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
-              dalloc(&ctx->counters, 3) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
+              dalloc(&ctx->counters, 3 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
               dalloc(&ctx->en_out, 2) == cudaSuccess;
     if (!ok) {
         nb_destroy(ctx);
         return NB_ERR_CUDA;
     }
-    int64_t init_counters[3] = {0, 0, int64_t(1) << 40};
+    int64_t init_counters[3 + NB_SIZE_BUCKETS] = {0, 0, int64_t(1) << 40};
     int32_t one = 1;
     bool ok2 = cudaMemset(ctx->status, 0, sizeof(int32_t)) == cudaSuccess &&
                cudaMemcpy(ctx->counters, init_counters, sizeof init_counters, cudaMemcpyHostToDevice) ==
@@ -867,7 +868,7 @@ nb_status nb_stats(nb_ctx *ctx, nb_counters *out)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!out) return fail(ctx, NB_ERR_ARG, "null counters");
-    int64_t c[2];
+    int64_t c[3 + NB_SIZE_BUCKETS];
     double inter;
     CK(cudaMemcpyAsync(c, ctx->counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&inter, ctx->interactions, sizeof inter, cudaMemcpyDeviceToHost, ctx->stream));
@@ -878,6 +879,7 @@ nb_status nb_stats(nb_ctx *ctx, nb_counters *out)
     out->particle_steps = c[1];
     out->interactions = inter;
     out->t_now = *std::max_element(t.begin(), t.end());
+    for (int b = 0; b < NB_SIZE_BUCKETS; ++b) out->size_hist[b] = c[3 + b];
     return NB_OK;
 }
 

@@ -263,6 +263,9 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
         A.counters[0] += 1;
         A.counters[1] += s;
+        int b = 0;
+        while ((int64_t(1) << b) < s && b < NB_SIZE_BUCKETS - 1) ++b;
+        A.counters[3 + b] += 1;   // block-size histogram
         *A.interactions += (double)s * (double)A.n;
     }
 }

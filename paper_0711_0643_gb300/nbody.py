@@ -43,7 +43,7 @@ class nb_config(C.Structure):
 
 class nb_counters(C.Structure):
     _fields_ = [("block_steps", C.c_int64), ("particle_steps", C.c_int64), ("interactions", C.c_double),
-                ("t_now", C.c_double)]
+                ("t_now", C.c_double), ("size_hist", C.c_int64 * 32)]
 
 
 class nb_state_view(C.Structure):
@@ -254,7 +254,7 @@ def nb_stats(ctx) -> dict:
     c = nb_counters()
     _check(ctx, load().nb_stats(ctx, C.byref(c)))
     return {"block_steps": c.block_steps, "particle_steps": c.particle_steps,
-            "interactions": c.interactions, "t_now": c.t_now}
+            "interactions": c.interactions, "t_now": c.t_now, "size_hist": list(c.size_hist)}
 
 
 def nb_sync(ctx):

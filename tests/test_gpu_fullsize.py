@@ -79,3 +79,36 @@ def test_force_salpeter_65536_sampled(nb, orc):
         for s in (1, 256, 4096, n):
             idx = np.unique(rng.next_u64(2 * s) % n)[:s].astype(np.int32) if s < n else np.arange(n, dtype=np.int32)
             _sampled(nb, orc, c, snap, idx, xp, vp, f"salpeter 65536 s={idx.size}")
+
+
+def test_force_errors_along_plummer_16k_run(nb, orc):
+    """Plummer N = 16384 (mixed): the forces of 8 block steps spread over the first 1/16 time
+    unit against the oracle on the GPU's own predicted state of that step (the two
+    trajectories would diverge, so the comparison is always on the same input); up to 64
+    sampled active particles per step, the parity tests' mixed tolerances."""
+    snap = ics.config(2)
+    targets = (1, 50, 200, 400, 700, 1000, 1300, 1600)
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        for k in range(1, targets[-1] + 1):
+            if k not in targets:
+                nb.nb_step(c.ctx)
+                continue
+            tn, s = nb.nb_next_block(c.ctx)
+            idx = nb.nb_get_active(c.ctx, s)
+            nb.nb_predict(c.ctx, tn)
+            xp, vp = nb.nb_get_predicted(c.ctx, snap.n)
+            a, kk, phi = nb.nb_force_jerk(c.ctx, None, s)
+            pos = np.unique(np.linspace(0, s - 1, min(s, 64)).astype(np.int64))
+            sample = idx[pos]
+            ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, sample, nthreads=orc.default_threads())
+            A, K = condition_scales(snap.m, xp, vp, snap.eps2, sample)
+            da = np.linalg.norm(a[pos] - ar, axis=1) / A
+            dk = np.linalg.norm(kk[pos] - kr, axis=1) / K
+            ep = rel_scalar(phi[pos], pr)
+            eaf = rel_errors(a[pos], ar, A)
+            print(f"block step {k} (t = {tn:.6f}, s = {s}): a/A {stats(da)} k/K {stats(dk)} "
+                  f"phi {stats(ep)} a(forward) {stats(eaf)}")
+            assert da.max() < TOL and dk.max() < TOL and ep.max() < TOL, k
+            assert np.percentile(eaf, 99) < TOL, k
+            nb.nb_correct(c.ctx, tn)

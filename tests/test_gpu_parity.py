@@ -397,6 +397,9 @@ def test_run_step_and_timed_paths_agree(nb):
         for key in ("x", "v", "a", "k", "t", "dt"):
             np.testing.assert_array_equal(st[key], states[0][0][key])
         assert cnt["block_steps"] == states[0][1]["block_steps"]
+        assert cnt["size_hist"] == states[0][1]["size_hist"]
+    hist = states[0][1]["size_hist"]
+    assert sum(hist) == states[0][1]["block_steps"] and hist[0] >= 0
 
 
 def test_deterministic_and_resume_bitwise(nb):
