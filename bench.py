@@ -373,6 +373,11 @@ def main_gpu(args):
     if args.salpeter and rank == 0:
         salp = salpeter_bench(nb, torch, dev, sptr, stream)
 
+    # ---- centrally concentrated models: King W0 = 6 and 9, N = 16384, to t = 1/4
+    king = None
+    if args.king and rank == 0:
+        king = king_bench(nb, torch, dev, sptr, stream)
+
     # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed, one evaluation per s
     sweep = None
     if args.sweep and rank == 0:
@@ -418,7 +423,7 @@ def main_gpu(args):
             "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / len(e2e_ms)},
             "fp64_gpu": fp64,
-            "ensemble": ens, "salpeter": salp,
+            "ensemble": ens, "salpeter": salp, "king": king,
             "force_sweep": sweep,
             "cpu_baseline": cpu,
         }
@@ -531,6 +536,41 @@ def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
             "abs_dE_over_E": abs(E1 - E0) / abs(E0), "block_size_hist": size_hist(st)}
 
 
+def king_bench(nb, torch, dev, sptr, stream, n=16384, t_end=0.25):
+    """Centrally concentrated models: King W0 = 6 and W0 = 9, N = 16384, eps = 1/1024, equal
+    masses, mixed precision, autotuned, t = 0 -> 1/4 (seeds 20071106 + 56 and + 59): one timed
+    run (init + energy + nb_run + energy) each after a short warm-up run."""
+    import ics
+    out = []
+    for w0 in (6.0, 9.0):
+        snap = ics.king(n, seed=ics.BASE_SEED + 50 + int(w0), w0=w0, eps=1.0 / 1024)
+        m_d = torch.tensor(snap.m, device=dev)
+        x_d = torch.tensor(snap.x, device=dev)
+        v_d = torch.tensor(snap.v, device=dev)
+        c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+        nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+        nb.nb_autotune(c.ctx)
+        nb.nb_run(c.ctx, 1.0 / 64)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
+        E0 = nb.nb_energy(c.ctx)[0]
+        nb.nb_run(c.ctx, t_end)
+        E1 = nb.nb_energy(c.ctx)[0]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st = nb.nb_stats(c.ctx)
+        c.close()
+        sec = e0.elapsed_time(e1) / 1e3
+        out.append({"workload": f"king W0={w0:g} N={n} eps=1/1024, t=0->{t_end}, mixed", "ms": sec * 1e3,
+                    "interactions_per_s": (st["interactions"] + float(n) * n) / sec,
+                    "block_steps": st["block_steps"], "block_steps_per_s": st["block_steps"] / sec,
+                    "mean_active": st["particle_steps"] / max(st["block_steps"], 1),
+                    "abs_dE_over_E": abs(E1 - E0) / abs(E0), "block_size_hist": size_hist(st)})
+    return out
+
+
 def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
                 precision=None):
     """King W0 = 6, N = 1,048,576, eps = 1e-3: one mixed force evaluation per active-set
@@ -607,6 +647,8 @@ def main(argv=None):
                     help="full-N force sweep on King N=2^20 (default on)")
     ap.add_argument("--salpeter", action=argparse.BooleanOptionalAction, default=True,
                     help="Plummer N=65536 with Salpeter masses to t=0.5 (default on; ~15 s of input generation)")
+    ap.add_argument("--king", action=argparse.BooleanOptionalAction, default=True,
+                    help="King W0 = 6 and 9, N = 16384, to t = 1/4 (default on)")
     ap.add_argument("--salpeter-only", action="store_true",
                     help="run only the Salpeter workload and print it")
     ap.add_argument("--ensemble-only", action="store_true",
