@@ -649,6 +649,8 @@ def main(argv=None):
                     help="Plummer N=65536 with Salpeter masses to t=0.5 (default on; ~15 s of input generation)")
     ap.add_argument("--king", action=argparse.BooleanOptionalAction, default=True,
                     help="King W0 = 6 and 9, N = 16384, to t = 1/4 (default on)")
+    ap.add_argument("--model", action="store_true",
+                    help="fit the per-block-step timing model (select, predict, force, correct) and print it")
     ap.add_argument("--salpeter-only", action="store_true",
                     help="run only the Salpeter workload and print it")
     ap.add_argument("--ensemble-only", action="store_true",
@@ -675,6 +677,8 @@ def main(argv=None):
         return main_ensemble(args)
     if args.salpeter_only:
         return main_salpeter(args)
+    if args.model:
+        return main_model(args)
     return main_gpu(args)
 
 
@@ -690,6 +694,77 @@ def main_ensemble(args):
     from paper_0711_0643_gb300 import nbody as nb
     nb.load()
     out = ensemble_bench(nb, torch, dev, stream.cuda_stream, stream, nc=args.ens_nc, n_hi=args.ens_nmax)
+    print(json.dumps(out))
+    return 0
+
+
+def main_model(args):
+    """The paper's timing model (Sect. 4.1) refitted on this GPU: per block step
+    T = [a_sel + b_sel N] + [a_pr + b_pr N] + [a_f + tau_f s N] + [a_cr + tau_cr s], fitted by
+    least squares to the phase totals of host-driven runs (nb_run_timed, each phase bracketed
+    by events) of Plummer models N = 1024 .. 65536 (eps = 4/N, t = 0 -> 1/16, autotuned); the
+    fitted model then predicts every graph-loop run (nb_run) from its block-step count and
+    sum of s, next to the measured time. Printed as one JSON line (not a bench line)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+    import ics
+    gate_us = None
+    rows = []
+    for n in (1024, 2048, 4096, 8192, 16384, 32768, 65536):
+        snap = ics.plummer(n, seed=ics.BASE_SEED + 70 + n.bit_length(), eps=4.0 / n,
+                           scale="continuum" if n > 16384 else "auto")
+        c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=stream.cuda_stream)
+        c.init(snap)
+        nb.nb_autotune(c.ctx)
+        c.init(snap)
+        _, nl, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
+        st = nb.nb_stats(c.ctx)
+        c.init(snap)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        nb.nb_run(c.ctx, 1.0 / 16)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st2 = nb.nb_stats(c.ctx)
+        c.close()
+        rows.append({"n": n, "steps": st["block_steps"], "sum_s": st["particle_steps"],
+                     "phase_us": {k: 1e3 * v for k, v in ph.items()},
+                     "run_steps": st2["block_steps"], "run_sum_s": st2["particle_steps"],
+                     "run_us": 1e3 * e0.elapsed_time(e1)})
+    # every phase total of run r: steps_r * a + (N_r * steps_r or sum(s N) or sum s) * b
+    A = {"select": [], "predict": [], "force": [], "correct": []}
+    y = {k: [] for k in A}
+    for r in rows:
+        n, k, ss = r["n"], r["steps"], r["sum_s"]
+        A["select"].append((k, k * n)); A["predict"].append((k, k * n))
+        A["force"].append((k, ss * n)); A["correct"].append((k, ss))
+        for key in A:
+            y[key].append(r["phase_us"][key])
+    fit = {}
+    for key in A:
+        coef, *_ = np.linalg.lstsq(np.array(A[key], dtype=float), np.array(y[key]), rcond=None)
+        fit[key] = {"a_us": float(coef[0]), "b_us": float(coef[1])}
+    # the phases above include a gate (delay kernel + events) each; the graph loop has none:
+    # predict the graph loop's time with the fixed terms less the measured gate overhead
+    for r in rows:
+        k, ss, n = r["run_steps"], r["run_sum_s"], r["n"]
+        t = 0.0
+        for key, f in fit.items():
+            lin = {"select": k * n, "predict": k * n, "force": ss * n, "correct": ss}[key]
+            t += f["a_us"] * k + f["b_us"] * lin
+        r["model_phase_sum_us"] = t
+        r["ratio_measured_to_phase_sum"] = r["run_us"] / t
+    out = {"model": "per block step T = sum over phases of (a + b x work), work = N (select, predict), "
+                     "s N (force), s (correct); fitted to nb_run_timed phase totals",
+           "fit": fit, "runs": rows}
     print(json.dumps(out))
     return 0
 

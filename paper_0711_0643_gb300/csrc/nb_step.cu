@@ -7,6 +7,7 @@
 // operation by operation in the order written, so the predictor and the
 // corrector give the same bits as a CPU evaluation of the same formulas
 // without fused multiply-adds.
+#include <cooperative_groups.h>
 #include <math_constants.h>
 
 #include "nb_ds.cuh"
@@ -19,8 +20,9 @@ namespace nb {
 
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kStepThreads = 256;
-constexpr int kSelThreads = 1024;
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
@@ -98,18 +100,21 @@ __global__ void state_to_ds_kernel(StepArgs A)
 }
 
 // ---------------------------------------------------------------- selection
-// One CTA of 1024 threads. Keys tn_i = t_i + dt_i are non-negative doubles (+inf
-// for padding) whose bit patterns order like the values, so all comparisons run
-// on the integer pipe. Chunks of 16384 keys; warp w owns keys [512 w, 512 w + 512)
+// Keys tn_i = t_i + dt_i are non-negative doubles (+inf for padding) whose bit
+// patterns order like the values, so all comparisons run on the integer pipe.
+// Chunks of 16 x (threads) keys; warp w owns keys [512 w, 512 w + 512)
 // of a chunk, read as 8 coalesced segments of 64 keys (lane l holds keys 2l and
 // 2l + 1 of each segment, one 16-byte load). The padded length is a multiple of
 // 256, so a segment lies wholly inside or outside it. Pass 1: minimum. Pass 2:
 // ballots give each lane the rank of its hits inside its warp's keys (segment
-// by segment, keys in index order), one block-wide scan of the 32 warp counts
-// places the warps, and the active list comes out ascending. Up to 16384
-// particles the keys stay in registers between the passes.
-constexpr int kSelSeg = 8;                                    // segments of 64 keys per warp
-constexpr int64_t kSelChunk = (int64_t)kSelThreads * 2 * kSelSeg;   // 16384
+// by segment, keys in index order), one block-wide scan of the warp counts
+// places the warps, and the active list comes out ascending. While a CTA has a
+// single chunk its keys stay in registers between the passes.
+constexpr int kSelSeg = 8;   // segments of 64 keys per warp
+// one CTA of 1024 threads (chunks of 16384 keys) up to 16384 particles; above,
+// a cluster of 512-thread CTAs (chunks of 8192 keys: 102 registers, no spills)
+constexpr int kSelSmallThreads = 1024, kSelClusterThreads = 512;
+constexpr int64_t kSelSmallMax = 16384;
 
 __device__ __forceinline__ long long warp_min_ll(long long v)
 {
@@ -138,21 +143,39 @@ __device__ __forceinline__ void sel_load(const long long *key, int64_t c0, int w
     }
 }
 
-__global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGraphConditionalHandle cond,
-                                                             int set_cond)
+// CLUSTER: a thread-block cluster of C CTAs (up to one CTA per chunk, a power
+// of two, at most 16); CTA r takes a contiguous run of chunks.
+// The CTA minima meet through distributed shared memory across one cluster
+// barrier; with C > 1 each CTA then counts its hits, the counts meet across a
+// second barrier (a CTA's list starts after the hits of the lower ranks), and a
+// last barrier keeps every CTA's shared memory alive until all have read it.
+template <int T, bool CLUSTER>
+__global__ void __launch_bounds__(T) select_kernel(StepArgs A, cudaGraphConditionalHandle cond, int set_cond)
 {
+    constexpr int kSelThreads = T;
+    constexpr int64_t kSelChunk = (int64_t)T * 2 * kSelSeg;
     __shared__ long long smin[kSelThreads / 32];
     __shared__ int woff[kSelThreads / 32];
     __shared__ int wtot;
-    __shared__ long long s_kmin;
+    __shared__ long long s_kmin;   // this CTA's minimum
+    __shared__ int s_cnt;          // this CTA's hits
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = CLUSTER ? (int)cluster.num_blocks() : 1;
+    const int rank = CLUSTER ? (int)cluster.block_rank() : 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = A.n, np = A.n_pad;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
     const int64_t nchunk = (np + kSelChunk - 1) / kSelChunk;
+    const int64_t cpc = (nchunk + C - 1) / C;
+    const int64_t ch0 = (int64_t)rank * cpc < nchunk ? (int64_t)rank * cpc : nchunk;
+    const int64_t ch1 = ch0 + cpc < nchunk ? ch0 + cpc : nchunk;
+    const bool resident = ch1 - ch0 <= 1;   // the keys stay in registers between the passes
     const unsigned below = (1u << lane) - 1u;
     longlong2 k[kSelSeg];
+#pragma unroll
+    for (int j = 0; j < kSelSeg; ++j) k[j] = make_longlong2(0x7ff0000000000000LL, 0x7ff0000000000000LL);
     long long m = 0x7ff0000000000000LL;   // +inf
-    for (int64_t ch = 0; ch < nchunk; ++ch) {
+    for (int64_t ch = ch0; ch < ch1; ++ch) {
         sel_load(key, ch * kSelChunk, warp, lane, np, k);
 #pragma unroll
         for (int j = 0; j < kSelSeg; ++j) {
@@ -164,16 +187,56 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
     if (lane == 0) smin[warp] = m;
     __syncthreads();
     if (warp == 0) {
-        long long x = smin[lane];
+        long long x = lane < kSelThreads / 32 ? smin[lane] : 0x7ff0000000000000LL;
         x = warp_min_ll(x);
         if (lane == 0) s_kmin = x;
     }
-    __syncthreads();
-    const long long kmin = s_kmin;
-    int out = 0;   // entries written by earlier chunks (same in every thread)
-    for (int64_t ch = 0; ch < nchunk; ++ch) {
+    long long kmin;
+    if (CLUSTER) {
+        cluster.sync();
+        kmin = s_kmin;
+        for (int r = 0; r < C; ++r) {
+            const long long o = *cluster.map_shared_rank(&s_kmin, r);
+            kmin = o < kmin ? o : kmin;
+        }
+    } else {
+        __syncthreads();
+        kmin = s_kmin;
+    }
+    int out = 0;   // entries written before this chunk (same in every thread)
+    int total = 0;
+    if (CLUSTER && C > 1) {
+        // count this CTA's hits, then place the CTA after the lower ranks' hits
+        int cnt = 0;
+        for (int64_t ch = ch0; ch < ch1; ++ch) {
+            const int64_t c0 = ch * kSelChunk;
+            if (!resident) sel_load(key, c0, warp, lane, np, k);
+#pragma unroll
+            for (int j = 0; j < kSelSeg; ++j) {
+                const int64_t e = sel_index(c0, warp, j, lane);
+                cnt += (k[j].x == kmin && e < n) + (k[j].y == kmin && e + 1 < n);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (lane == 0) woff[warp] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int w = 0; w < kSelThreads / 32; ++w) t += woff[w];
+            s_cnt = t;
+        }
+        cluster.sync();
+        for (int r = 0; r < C; ++r) {
+            const int cr = *cluster.map_shared_rank(&s_cnt, r);
+            if (r < rank) out += cr;
+            total += cr;
+        }
+        cluster.sync();   // no CTA leaves (or rewrites woff) while others read its shared memory
+    }
+    for (int64_t ch = ch0; ch < ch1; ++ch) {
         const int64_t c0 = ch * kSelChunk;
-        if (nchunk > 1) sel_load(key, c0, warp, lane, np, k);
+        if (!resident) sel_load(key, c0, warp, lane, np, k);
         // per segment: hits of the even and odd key of every lane
         unsigned be[kSelSeg], bo[kSelSeg];
         int wcount = 0;
@@ -187,14 +250,14 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
         if (lane == 0) woff[warp] = wcount;
         __syncthreads();
         if (warp == 0) {
-            const int cw = woff[lane];
+            const int cw = lane < kSelThreads / 32 ? woff[lane] : 0;
             int wi = cw;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, wi, off);
                 if (lane >= off) wi += y;
             }
-            woff[lane] = wi - cw;
+            if (lane < kSelThreads / 32) woff[lane] = wi - cw;
             if (lane == 31) wtot = wi;
         }
         __syncthreads();
@@ -211,8 +274,9 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(StepArgs A, cudaGra
         out += wtot;
         __syncthreads();   // woff and wtot are rewritten by the next chunk
     }
-    if (tid == 0) {
-        const int64_t s = (int64_t)out;
+    if (C == 1) total = out;
+    if (rank == 0 && tid == 0) {
+        const int64_t s = (int64_t)total;
         const double tmin = __longlong_as_double(kmin);
         *A.s = s;
         *A.t_next = tmin;
@@ -587,10 +651,63 @@ cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Cluster size of the selection for n_pad > kSelSmallMax keys: one CTA per
+// 8192-key chunk, a power of two, at most 16 and at most what the device can
+// co-schedule (queried once).
+int select_cluster(int64_t np)
+{
+    static int cmax = -1;
+    if (cmax < 0) {
+        cmax = 1;
+        cudaFuncSetAttribute(select_kernel<kSelClusterThreads, true>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                             1);
+        for (int c = 16; c >= 2; c >>= 1) {
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3((unsigned)c);
+            cfg.blockDim = dim3(kSelClusterThreads);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclu = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclu, select_kernel<kSelClusterThreads, true>, &cfg) == cudaSuccess &&
+                nclu > 0) {
+                cmax = c;
+                break;
+            }
+        }
+        (void)cudaGetLastError();
+    }
+    const int64_t nchunk = (np + 2 * kSelSeg * kSelClusterThreads - 1) / (2 * kSelSeg * kSelClusterThreads);
+    int c = 1;
+    while (c * 2 <= cmax && c * 2 <= nchunk) c *= 2;
+    return c;
+}
+
 cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st)
 {
-    select_kernel<<<1, kSelThreads, 0, st>>>(a, (cudaGraphConditionalHandle)cond, set_cond ? 1 : 0);
-    return cudaGetLastError();
+    if (a.n_pad <= kSelSmallMax) {
+        select_kernel<kSelSmallThreads, false>
+            <<<1, kSelSmallThreads, 0, st>>>(a, (cudaGraphConditionalHandle)cond, set_cond ? 1 : 0);
+        return cudaGetLastError();
+    }
+    const int C = select_cluster(a.n_pad);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kSelClusterThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, select_kernel<kSelClusterThreads, true>, a, (cudaGraphConditionalHandle)cond,
+                              set_cond ? 1 : 0);
 }
 
 cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st)
