@@ -44,6 +44,7 @@ struct nb_ctx {
     int32_t *idx = nullptr;
     int64_t *s = nullptr;
     double *t_next = nullptr, *t_end = nullptr;
+    double *t_cand = nullptr, *t_min2 = nullptr;   // next block time being formed (nb_run loop)
     double *part = nullptr;
     int64_t part_cap = 0;
     double *fin = nullptr;          // final force sums [n_pad][8]
@@ -95,6 +96,7 @@ nb_status nb_ctx_fail(nb_ctx *ctx, nb_status st, const char *msg)
 namespace {
 
 constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
+constexpr int kRunUnroll = 4;                          // block steps per pass of the nb_run while node
 
 nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
 {
@@ -140,6 +142,7 @@ StepArgs step_args(nb_ctx *c)
     A.eps2 = c->eps2;
     A.eta = c->cfg.eta; A.dt_max = c->cfg.dt_max; A.dt_min = c->cfg.dt_min;
     A.idx = c->idx; A.s = c->s; A.t_next = c->t_next; A.t_end = c->t_end;
+    A.t_cand = c->t_cand; A.t_min2 = c->t_min2;
     A.fin = c->fin;
     A.status = c->status; A.counters = c->counters; A.interactions = c->interactions;
     return A;
@@ -324,7 +327,7 @@ nb_status init_forces(nb_ctx *ctx)
     StepArgs A = step_args(ctx);
     CK(launch_pad_records(A, ctx->stream));
     CK(launch_state_to_ds(A, ctx->stream));
-    CK(launch_predict(A, false, 0.0, ctx->stream));    // t = 0, a = k = 0: records = positions
+    CK(launch_predict(A, nullptr, 0.0, false, ctx->stream));    // t = 0, a = k = 0: records = positions
     CK(launch_fill_iota(ctx->idx, ctx->n, ctx->stream));
     CK(cudaMemcpyAsync(ctx->s, &ctx->n, sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
     if (!ctx->tuned) fill_default_tuning(ctx);
@@ -353,11 +356,19 @@ nb_status check_ctx(nb_ctx *ctx, bool need_state)
     return NB_OK;
 }
 
-// The nb_run graph: select, then a while node whose body is predict -> force ->
-// correct -> select (the body's select sets the condition). The corrector stays
-// a kernel of its own: its FP64 work must spread over many SMs (an FP64 warp
-// instruction holds an SM sub-partition's FP64 unit for ~70 clocks), which the
-// CTAs that finish the force sums of an i-block cannot do.
+// The nb_run graph: a full selection (block time = smallest key; sets the
+// condition and the candidate slot), then a while node whose body is kRunUnroll
+// block steps of
+//     [selection of the known block time || predictor to it] -> force -> corrector.
+// The next block time is formed during the block (StepArgs::t_cand), so the
+// selection and the predictor of a block depend only on the previous corrector
+// and run side by side. Each selection sets the condition to "this block is
+// done"; a step that finds no block due runs as no-ops (s = 0), and so do the
+// steps after it in the body. Going round the while node costs ~5 us on this
+// GPU against ~1 us between two kernels of the body, hence the unrolling.
+// The corrector stays a kernel of its own: its FP64 work must spread over many
+// SMs (an FP64 warp instruction holds an SM sub-partition's FP64 unit for ~70
+// clocks), which the CTAs that finish the force sums of an i-block cannot do.
 nb_status build_run_graph(nb_ctx *ctx)
 {
     if (ctx->run_exec) return NB_OK;
@@ -368,7 +379,7 @@ nb_status build_run_graph(nb_ctx *ctx)
     StepArgs A = step_args(ctx);
     // 1) first selection (sets the condition)
     CK(cudaStreamBeginCaptureToGraph(ctx->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    cudaError_t e1 = launch_select(A, (unsigned long long)h, true, ctx->stream);
+    cudaError_t e1 = launch_select(A, SEL_FULL, (unsigned long long)h, true, ctx->stream);
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGraphDestroy(g);
@@ -388,14 +399,38 @@ nb_status build_run_graph(nb_ctx *ctx)
     cudaGraphNode_t wn;
     CK(cudaGraphAddNode(&wn, g, nodes.data(), nullptr, nn, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    // 3) body: predict -> force -> correct -> select
-    CK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    cudaError_t eb = launch_predict(A, true, 0.0, ctx->stream);
-    if (eb == cudaSuccess) eb = launch_force(ctx, force_args(ctx));
-    if (eb == cudaSuccess) eb = launch_correct(A, false, ctx->stream);
-    if (eb == cudaSuccess) eb = launch_select(A, (unsigned long long)h, true, ctx->stream);
-    cudaGraph_t body_out = body;
-    cudaError_t ee = cudaStreamEndCapture(ctx->stream, &body_out);
+    // 3) body: the predictor forks onto a side stream and joins before the force kernel
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t eb = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (eb == cudaSuccess) eb = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (eb == cudaSuccess) eb = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+    cudaError_t ee = cudaSuccess;
+    if (eb == cudaSuccess) {
+        eb = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (eb == cudaSuccess) {
+            for (int u = 0; u < kRunUnroll && eb == cudaSuccess; ++u) {
+                eb = cudaEventRecord(fork, ctx->stream);
+                if (eb == cudaSuccess) eb = cudaStreamWaitEvent(side, fork, 0);
+                if (eb == cudaSuccess) eb = launch_predict(A, A.t_cand, 0.0, true, side);
+                if (eb == cudaSuccess) eb = cudaEventRecord(join, side);
+                if (eb == cudaSuccess) eb = launch_select(A, SEL_KNOWN, (unsigned long long)h, true, ctx->stream);
+                if (eb == cudaSuccess) eb = cudaStreamWaitEvent(ctx->stream, join, 0);
+                if (eb == cudaSuccess) {
+                    ForceArgs F = force_args(ctx);
+                    F.t_src = ctx->t_min2;
+                    F.t_dst = ctx->t_cand;
+                    eb = launch_force(ctx, F);
+                }
+                if (eb == cudaSuccess) eb = launch_correct(A, false, true, ctx->stream);
+            }
+            cudaGraph_t body_out = body;
+            ee = cudaStreamEndCapture(ctx->stream, &body_out);
+        }
+    }
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (side) cudaStreamDestroy(side);
     if (eb != cudaSuccess || ee != cudaSuccess) {
         cudaGraphDestroy(g);
         return fail(ctx, NB_ERR_CUDA, "graph capture (body): %s / %s", cudaGetErrorString(eb),
@@ -484,6 +519,7 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
     (void)force_mixed_ctas_per_sm();   // sets kernel attributes before any graph capture
     (void)force_f64_ctas_per_sm();
     bool ok = dalloc(&ctx->s, 1) == cudaSuccess && dalloc(&ctx->t_next, 1) == cudaSuccess &&
+              dalloc(&ctx->t_cand, 1) == cudaSuccess && dalloc(&ctx->t_min2, 1) == cudaSuccess &&
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
               dalloc(&ctx->counters, 3 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
@@ -514,7 +550,7 @@ void nb_destroy(nb_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_system(ctx);
     nb_ctx_set_ensemble(ctx, nullptr);
-    void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
+    void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_cand, ctx->t_min2, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
                     ctx->counters, ctx->interactions, ctx->en_out};
     for (void *p : ptrs) dfree(p);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -564,7 +600,7 @@ nb_status nb_next_block(nb_ctx *ctx, double *t_next, int64_t *s)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     StepArgs A = step_args(ctx);
-    CK(launch_select(A, 0, false, ctx->stream));
+    CK(launch_select(A, SEL_FULL, 0, false, ctx->stream));
     double tn;
     int64_t ss;
     CK(cudaMemcpyAsync(&tn, ctx->t_next, sizeof tn, cudaMemcpyDeviceToHost, ctx->stream));
@@ -594,7 +630,7 @@ nb_status nb_predict(nb_ctx *ctx, double t)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!std::isfinite(t)) return fail(ctx, NB_ERR_ARG, "t must be finite");
-    CK(launch_predict(step_args(ctx), false, t, ctx->stream));
+    CK(launch_predict(step_args(ctx), nullptr, t, false, ctx->stream));
     return NB_OK;
 }
 
@@ -667,7 +703,7 @@ nb_status nb_correct(nb_ctx *ctx, double t_block)
     CK(launch_check_due(A, t_block, ctx->stream));
     st = sync_status(ctx);
     if (st != NB_OK) return st;
-    CK(launch_correct(A, true, ctx->stream));
+    CK(launch_correct(A, true, false, ctx->stream));
     ctx->forces_pending = false;
     return sync_status(ctx);
 }
@@ -677,10 +713,10 @@ nb_status nb_step(nb_ctx *ctx)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     StepArgs A = step_args(ctx);
-    CK(launch_select(A, 0, false, ctx->stream));
-    CK(launch_predict(A, true, 0.0, ctx->stream));
+    CK(launch_select(A, SEL_FULL, 0, false, ctx->stream));
+    CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream));
     CK(launch_force_ctx(ctx));
-    CK(launch_correct(A, false, ctx->stream));
+    CK(launch_correct(A, false, false, ctx->stream));
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);
@@ -747,7 +783,7 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
     };
     for (;;) {
         if (phases) CK(open(0));
-        CK(launch_select(A, 0, false, ctx->stream));
+        CK(launch_select(A, SEL_FULL, 0, false, ctx->stream));
         if (phases) CK(close(0));
         double tn;
         int64_t ss;
@@ -759,13 +795,13 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
             CK(elapsed(0));
             CK(open(1));
         }
-        CK(launch_predict(A, true, 0.0, ctx->stream));
+        CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream));
         if (phases) CK(close(1));
         CK(open(2));
         CK(launch_force_ctx(ctx));
         CK(close(2));
         if (phases) CK(open(3));
-        CK(launch_correct(A, false, ctx->stream));
+        CK(launch_correct(A, false, false, ctx->stream));
         if (phases) CK(close(3));
         int32_t stw = 0;
         CK(cudaMemcpyAsync(&stw, ctx->status, sizeof stw, cudaMemcpyDeviceToHost, ctx->stream));

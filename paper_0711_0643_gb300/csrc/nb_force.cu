@@ -416,6 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         fence_mbar_init();
         sm->abort = 0;
         sm->s = *A.s;
+        if (A.t_dst && blockIdx.x == 0) *A.t_dst = *A.t_src;
     }
     // the active count and the whole tuning table in one round trip
     if (A.force_variant < 0 && tid < 2 * kBuckets) {
@@ -586,6 +587,7 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     __shared__ double red[kThreads / 32][7];
     __shared__ uint64_t inject_bar;
     __shared__ int last;
+    if (A.t_dst && blockIdx.x == 0 && threadIdx.x == 0) *A.t_dst = *A.t_src;
     const int64_t s = *A.s;
     if (s <= 0) return;
     if (A.inject) {

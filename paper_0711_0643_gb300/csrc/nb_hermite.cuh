@@ -190,7 +190,8 @@ __device__ __forceinline__ double pick4(double v0, double v1, double v2, double 
 // including file lets the compiler contract multiply-adds. All 32 lanes of the
 // warp call it together (full-mask shuffles); lane q = lane & 3 passes
 // component min(q, 2) of the new a and k. i must be a valid particle even when
-// live is false: the group then computes without storing. Returns status bits.
+// live is false: the group then computes without storing. Returns status bits;
+// lane 3 of a live group also writes the new key t + dt to *key_out if given.
 __device__ __forceinline__ double rn_div6(double y)
 {
     const int e = dexpo(y);
@@ -233,7 +234,7 @@ __device__ __forceinline__ float2 rn_ds_pack(double x)
 __device__ __forceinline__ double pow2_of(int e) { return dfrom((long long)(1023 + e) << 52); }
 
 __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
-                                             double eta, double dt_max, double dt_min)
+                                             double eta, double dt_max, double dt_min, long long *key_out = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int q = lane & 3;
@@ -345,9 +346,11 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
         } else {
             const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
             if (dt_new == 0.0) flags |= kStUnderflow;
+            const double key = __dadd_rn(tn, dt_new);
             H.t[i] = tn;
             H.dt[i] = dt_new;
-            H.tn[i] = __dadd_rn(tn, dt_new);
+            H.tn[i] = key;
+            if (key_out) *key_out = dbits(key);
         }
     }
     return flags;

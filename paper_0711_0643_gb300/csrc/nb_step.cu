@@ -36,9 +36,11 @@ __device__ __forceinline__ void predict_one(const StepArgs &A, int64_t i, double
 // The far-away, massless record used to pad the j arrays to whole tiles.
 constexpr double kPadPos = 1e18;
 
-__global__ void predict_kernel(StepArgs A, int use_t_next, double t_host)
+__global__ void predict_kernel(StepArgs A, const double *t_dev, double t_host, int skip_past)
 {
-    const double tn = use_t_next ? *A.t_next : t_host;
+    const double tn = t_dev ? *t_dev : t_host;
+    // nb_run loop: no block is due at a time past t_end (the loop's last pass)
+    if (skip_past && !(tn <= *A.t_end)) return;
     const int64_t np = A.n_pad;
     for (int64_t i = gtid(); i < A.n; i += gstride()) {
         if (A.precision == NB_PREC_MIXED) {
@@ -284,8 +286,161 @@ __global__ void __launch_bounds__(T) select_kernel(StepArgs A, cudaGraphConditio
             const bool ok = (tmin <= *A.t_end) && s > 0 && (*A.status == 0);
             bool more = ok && (A.counters[0] < A.counters[2]);
             if (ok && !more) atomicOr(A.status, kStSteps);
+            *A.t_cand = tmin;   // the nb_run loop body's first block time
             cudaGraphSetConditional(cond, more ? 1u : 0u);
         }
+    }
+}
+
+// The nb_run loop body's selection, at a known block time (*t_cand, formed by
+// the previous corrector): no minimum pass. A cluster of C CTAs (C <= 16) splits
+// the keys in chunks of 16 T keys; one pass gives every warp its hits (ballots)
+// and its smallest key other than the block time. The CTA totals and minima go
+// into every rank's shared memory across one cluster barrier, then each CTA
+// writes its hits after those of the lower ranks, ascending. With one chunk per
+// CTA the ballots stay in registers between the count and the write.
+// Writes s (0 when the block is not to be done: past *t_end, an error, the step
+// cap; force and corrector are then no-ops), t_next and t_min2, and sets the
+// while-node condition to "this block is done".
+template <int T>
+__global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphConditionalHandle cond)
+{
+    constexpr int kW = T / 32;
+    constexpr int64_t kChunk = (int64_t)T * 2 * kSelSeg;
+    constexpr long long kInf = 0x7ff0000000000000LL;
+    __shared__ int woff[kW];
+    __shared__ long long wmin[kW];
+    __shared__ int wtot;
+    __shared__ int r_cnt[16];         // hits of each rank, written by that rank
+    __shared__ long long r_min[16];   // smallest key other than the block time, per rank
+    // Once this barrier phase completes every CTA of the cluster is running:
+    // no CTA writes into another's shared memory before that.
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t np = A.n_pad;
+    const long long *key = reinterpret_cast<const long long *>(A.tn);
+    const int64_t nchunk = (np + kChunk - 1) / kChunk;
+    const int64_t cpc = (nchunk + C - 1) / C;
+    const int64_t ch0 = (int64_t)rank * cpc < nchunk ? (int64_t)rank * cpc : nchunk;
+    const int64_t ch1 = ch0 + cpc < nchunk ? ch0 + cpc : nchunk;
+    const bool resident = ch1 - ch0 <= 1;
+    // what the last step reads (the previous corrector wrote it), loaded up front
+    const bool lead = rank == 0 && tid == 0;
+    const double t_end = lead ? *A.t_end : 0.0;
+    const int32_t status0 = lead ? *A.status : 0;
+    const bool cap_ok = lead ? A.counters[0] < A.counters[2] : false;
+    const long long kmin = *reinterpret_cast<const long long *>(A.t_cand);
+    // padding keys and keys past n_pad are +inf: with a finite block time every
+    // hit is a particle; an infinite one selects nothing
+    const bool live = kmin < kInf;
+    const unsigned below = (1u << lane) - 1u;
+    longlong2 k[kSelSeg];
+    unsigned be[kSelSeg], bo[kSelSeg];
+    long long m2 = kInf;   // smallest key other than kmin (one below kmin is a state error)
+    int wcnt = 0;          // this warp's hits
+    for (int64_t ch = ch0; ch < ch1; ++ch) {
+        sel_load(key, ch * kChunk, warp, lane, np, k);
+#pragma unroll
+        for (int j = 0; j < kSelSeg; ++j) {
+            const long long x = k[j].x == kmin ? kInf : k[j].x;
+            const long long y = k[j].y == kmin ? kInf : k[j].y;
+            m2 = x < m2 ? x : m2;
+            m2 = y < m2 ? y : m2;
+            be[j] = __ballot_sync(0xffffffffu, live && k[j].x == kmin);
+            bo[j] = __ballot_sync(0xffffffffu, live && k[j].y == kmin);
+            wcnt += __popc(be[j]) + __popc(bo[j]);
+        }
+    }
+    m2 = warp_min_ll(m2);
+    if (lane == 0) {
+        woff[warp] = wcnt;
+        wmin[warp] = m2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int cw = lane < kW ? woff[lane] : 0;
+        int wi = cw;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        if (lane < kW) woff[lane] = wi - cw;   // the warps' offsets inside this CTA (one chunk)
+        const int tot = __shfl_sync(0xffffffffu, wi, 31);
+        const long long mm = warp_min_ll(lane < kW ? wmin[lane] : kInf);
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+        if (lane < C) {
+            *cluster.map_shared_rank(&r_cnt[rank], lane) = tot;
+            *cluster.map_shared_rank(&r_min[rank], lane) = mm;
+        }
+    } else {
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    }
+    cluster.sync();   // every rank's total and minimum are in this CTA's shared memory
+    int out = 0, total = 0;
+    long long m2all = kInf;
+    for (int r = 0; r < C; ++r) {
+        const int cr = r_cnt[r];
+        if (r < rank) out += cr;
+        total += cr;
+        m2all = r_min[r] < m2all ? r_min[r] : m2all;
+    }
+    for (int64_t ch = ch0; ch < ch1; ++ch) {
+        const int64_t c0 = ch * kChunk;
+        if (!resident) {
+            // several chunks: ballots and warp offsets again, chunk by chunk
+            sel_load(key, c0, warp, lane, np, k);
+            int wc = 0;
+#pragma unroll
+            for (int j = 0; j < kSelSeg; ++j) {
+                be[j] = __ballot_sync(0xffffffffu, live && k[j].x == kmin);
+                bo[j] = __ballot_sync(0xffffffffu, live && k[j].y == kmin);
+                wc += __popc(be[j]) + __popc(bo[j]);
+            }
+            __syncthreads();   // the previous chunk's offsets have been read
+            if (lane == 0) woff[warp] = wc;
+            __syncthreads();
+            if (warp == 0) {
+                const int cw = lane < kW ? woff[lane] : 0;
+                int wi = cw;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, wi, off);
+                    if (lane >= off) wi += y;
+                }
+                if (lane < kW) woff[lane] = wi - cw;
+                if (lane == 31) wtot = wi;
+            }
+            __syncthreads();
+        }
+        int pos = out + woff[warp];
+#pragma unroll
+        for (int j = 0; j < kSelSeg; ++j) {
+            const int64_t e = sel_index(c0, warp, j, lane);
+            const bool he = (be[j] >> lane) & 1u, ho = (bo[j] >> lane) & 1u;
+            const int r = pos + __popc(be[j] & below) + __popc(bo[j] & below);
+            if (he) A.idx[r] = (int32_t)e;
+            if (ho) A.idx[r + (he ? 1 : 0)] = (int32_t)(e + 1);
+            pos += __popc(be[j]) + __popc(bo[j]);
+        }
+        if (!resident) out += wtot;
+    }
+    if (lead) {
+        const int64_t s = (int64_t)total;
+        const double tmin = __longlong_as_double(kmin);
+        const bool due = tmin <= t_end;
+        const bool sound = m2all >= kmin && (s > 0 || !due);
+        if (!sound) atomicOr(A.status, kStState);
+        const bool ok = due && sound && status0 == 0;
+        const bool more = ok && cap_ok;
+        if (ok && !more) atomicOr(A.status, kStSteps);
+        *A.s = more ? s : 0;
+        *A.t_next = tmin;
+        *A.t_min2 = more ? __longlong_as_double(m2all) : tmin;
+        cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
 }
 
@@ -303,7 +458,7 @@ __device__ __forceinline__ void load_fin(const double *fin, int64_t ii, double *
 constexpr int kCorThreads = 128;
 constexpr int kCorPer = kCorThreads / 4;
 
-__global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int check_due)
+__global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int check_due, int lower_cand)
 {
     const int64_t s = *A.s;
     const double tn = *A.t_next;
@@ -311,6 +466,7 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
     const int q = threadIdx.x & 3;
     const int c = q < 3 ? q : 2;
     int flags = 0;
+    long long kmin = 0x7ff0000000000000LL;   // smallest new key of this thread's particles
     for (int64_t base = (int64_t)blockIdx.x * kCorPer; base < s; base += (int64_t)gridDim.x * kCorPer) {
         const int64_t ii = base + (threadIdx.x >> 2);
         bool live = ii < s;
@@ -321,7 +477,16 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
             flags |= kStState;
         }
         const double an = A.fin[iis * kPartStride + c], kn = A.fin[iis * kPartStride + 3 + c];
-        flags |= correct_group(H, i, live, tn, an, kn, A.eta, A.dt_max, A.dt_min);
+        long long key = 0x7ff0000000000000LL;
+        flags |= correct_group(H, i, live, tn, an, kn, A.eta, A.dt_max, A.dt_min, &key);
+        kmin = key < kmin ? key : kmin;
+    }
+    if (lower_cand) {
+        // the next block time: the smallest of the unchanged keys (*t_cand, from
+        // the selection) and the new ones; non-negative doubles order like their bits
+        kmin = warp_min_ll(kmin);
+        if ((threadIdx.x & 31) == 0 && kmin != 0x7ff0000000000000LL)
+            atomicMin(reinterpret_cast<long long *>(A.t_cand), kmin);
     }
     if (flags) atomicOr(A.status, flags);
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
@@ -626,10 +791,10 @@ int grid_for(int64_t n, int threads, int max_grid = 4096)
 
 // -------------------------------------------------------------------- launchers
 
-cudaError_t launch_predict(const StepArgs &a, bool use_t_next, double t_host, cudaStream_t st)
+cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st)
 {
     // FP64-heavy: small CTAs so that the work spreads over every SM
-    predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, use_t_next ? 1 : 0, t_host);
+    predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, t_dev, t_host, skip_past ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -651,69 +816,98 @@ cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Cluster size of the selection for n_pad > kSelSmallMax keys: one CTA per
-// 8192-key chunk, a power of two, at most 16 and at most what the device can
-// co-schedule (queried once).
-int select_cluster(int64_t np)
+// Largest cluster (16, 8, 4, 2) the device co-schedules for kernel K with the
+// given CTA size (queried once per kernel).
+template <class K>
+int max_cluster(K kernel, int threads)
 {
-    static int cmax = -1;
-    if (cmax < 0) {
-        cmax = 1;
-        cudaFuncSetAttribute(select_kernel<kSelClusterThreads, true>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                             1);
-        for (int c = 16; c >= 2; c >>= 1) {
-            cudaLaunchConfig_t cfg{};
-            cfg.gridDim = dim3((unsigned)c);
-            cfg.blockDim = dim3(kSelClusterThreads);
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)c;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int nclu = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclu, select_kernel<kSelClusterThreads, true>, &cfg) == cudaSuccess &&
-                nclu > 0) {
-                cmax = c;
-                break;
-            }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c = 16; c >= 2; c >>= 1) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3((unsigned)threads);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclu = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclu, kernel, &cfg) == cudaSuccess && nclu > 0) {
+            (void)cudaGetLastError();
+            return c;
         }
-        (void)cudaGetLastError();
     }
-    const int64_t nchunk = (np + 2 * kSelSeg * kSelClusterThreads - 1) / (2 * kSelSeg * kSelClusterThreads);
-    int c = 1;
-    while (c * 2 <= cmax && c * 2 <= nchunk) c *= 2;
-    return c;
+    (void)cudaGetLastError();
+    return 1;
 }
 
-cudaError_t launch_select(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st)
+// Launch configuration of a one-cluster grid of C CTAs.
+void cluster_config(int C, int threads, cudaStream_t st, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at)
 {
-    if (a.n_pad <= kSelSmallMax) {
-        select_kernel<kSelSmallThreads, false>
-            <<<1, kSelSmallThreads, 0, st>>>(a, (cudaGraphConditionalHandle)cond, set_cond ? 1 : 0);
-        return cudaGetLastError();
-    }
-    const int C = select_cluster(a.n_pad);
-    cudaLaunchConfig_t cfg{};
+    cfg = cudaLaunchConfig_t{};
     cfg.gridDim = dim3((unsigned)C);
-    cfg.blockDim = dim3(kSelClusterThreads);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)C;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+}
+
+// Full selection: one CTA of 1024 threads (chunks of 16384 keys) up to
+// kSelSmallMax keys, above that a cluster of 512-thread CTAs, one per chunk of
+// 8192 keys, a power of two, at most 16 and at most what the device co-schedules.
+cudaError_t launch_select_full(const StepArgs &a, unsigned long long cond, bool set_cond, cudaStream_t st)
+{
+    if (a.n_pad <= kSelSmallMax) {
+        select_kernel<kSelSmallThreads, false>
+            <<<1, kSelSmallThreads, 0, st>>>(a, (cudaGraphConditionalHandle)cond, set_cond ? 1 : 0);
+        return cudaGetLastError();
+    }
+    static const int cmax = max_cluster(select_kernel<kSelClusterThreads, true>, kSelClusterThreads);
+    const int64_t nchunk = (a.n_pad + 2 * kSelSeg * kSelClusterThreads - 1) / (2 * kSelSeg * kSelClusterThreads);
+    int C = 1;
+    while (C * 2 <= cmax && C * 2 <= nchunk) C *= 2;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cluster_config(C, kSelClusterThreads, st, cfg, at);
     return cudaLaunchKernelEx(&cfg, select_kernel<kSelClusterThreads, true>, a, (cudaGraphConditionalHandle)cond,
                               set_cond ? 1 : 0);
 }
 
-cudaError_t launch_correct(const StepArgs &a, bool check_due, cudaStream_t st)
+// Selection at a known block time: CTAs of T threads (chunks of 16 T keys) with
+// T the smallest of 64, 128, 256, 512 that covers the keys in 16 chunks; as many
+// CTAs as chunks, a power of two, at most 16 and at most what the device co-schedules.
+template <int T>
+cudaError_t launch_select_known_T(const StepArgs &a, unsigned long long cond, cudaStream_t st)
+{
+    static const int cmax = max_cluster(select_known_kernel<T>, T);
+    const int64_t nchunk = (a.n_pad + 2 * kSelSeg * T - 1) / (2 * kSelSeg * T);
+    int C = 1;
+    while (C * 2 <= cmax && C * 2 <= nchunk) C *= 2;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cluster_config(C, T, st, cfg, at);
+    return cudaLaunchKernelEx(&cfg, select_known_kernel<T>, a, (cudaGraphConditionalHandle)cond);
+}
+
+cudaError_t launch_select(const StepArgs &a, SelMode mode, unsigned long long cond, bool set_cond, cudaStream_t st)
+{
+    if (mode == SEL_FULL) return launch_select_full(a, cond, set_cond, st);
+    if (a.n_pad <= 16 * 2 * kSelSeg * 64) return launch_select_known_T<64>(a, cond, st);
+    if (a.n_pad <= 16 * 2 * kSelSeg * 128) return launch_select_known_T<128>(a, cond, st);
+    if (a.n_pad <= 16 * 2 * kSelSeg * 256) return launch_select_known_T<256>(a, cond, st);
+    return launch_select_known_T<512>(a, cond, st);
+}
+
+cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_cand, cudaStream_t st)
 {
     // one round covers blocks of up to 608 * 32 particles; CTAs past s exit at once
-    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0);
+    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0, lower_cand ? 1 : 0);
     return cudaGetLastError();
 }
 
