@@ -44,7 +44,7 @@ struct nb_ctx {
     int32_t *idx = nullptr;
     int64_t *s = nullptr;
     double *t_next = nullptr, *t_end = nullptr;
-    double *t_cand = nullptr, *t_min2 = nullptr;   // next block time being formed (nb_run loop)
+    double *t_slot = nullptr;     // [2] block times of the nb_run loop (StepArgs::t_known, t_form)
     double *part = nullptr;
     int64_t part_cap = 0;
     double *fin = nullptr;          // final force sums [n_pad][8]
@@ -97,6 +97,7 @@ namespace {
 
 constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
 constexpr int kRunUnroll = 4;                          // block steps per pass of the nb_run while node
+static_assert(kRunUnroll % 2 == 0, "the loop's steps alternate two block-time slots");
 
 nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
 {
@@ -142,7 +143,7 @@ StepArgs step_args(nb_ctx *c)
     A.eps2 = c->eps2;
     A.eta = c->cfg.eta; A.dt_max = c->cfg.dt_max; A.dt_min = c->cfg.dt_min;
     A.idx = c->idx; A.s = c->s; A.t_next = c->t_next; A.t_end = c->t_end;
-    A.t_cand = c->t_cand; A.t_min2 = c->t_min2;
+    A.t_known = c->t_slot; A.t_form = c->t_slot + 1;
     A.fin = c->fin;
     A.status = c->status; A.counters = c->counters; A.interactions = c->interactions;
     return A;
@@ -158,6 +159,7 @@ ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
     F.eps2f = (float)c->eps2;
     F.eps2 = c->eps2;
     F.idx = c->idx;
+    F.idx_cap = c->n_pad;
     F.s = c->s;
     F.part = c->part;
     F.part_cap = c->part_cap;
@@ -360,7 +362,7 @@ nb_status check_ctx(nb_ctx *ctx, bool need_state)
 // condition and the candidate slot), then a while node whose body is kRunUnroll
 // block steps of
 //     [selection of the known block time || predictor to it] -> force -> corrector.
-// The next block time is formed during the block (StepArgs::t_cand), so the
+// The next block time is formed during the block (StepArgs::t_form), so the
 // selection and the predictor of a block depend only on the previous corrector
 // and run side by side. Each selection sets the condition to "this block is
 // done"; a step that finds no block due runs as no-ops (s = 0), and so do the
@@ -410,19 +412,17 @@ nb_status build_run_graph(nb_ctx *ctx)
         eb = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (eb == cudaSuccess) {
             for (int u = 0; u < kRunUnroll && eb == cudaSuccess; ++u) {
+                StepArgs Au = A;   // step u reads slot u % 2 and forms slot (u + 1) % 2
+                Au.t_known = ctx->t_slot + (u & 1);
+                Au.t_form = ctx->t_slot + ((u + 1) & 1);
                 eb = cudaEventRecord(fork, ctx->stream);
                 if (eb == cudaSuccess) eb = cudaStreamWaitEvent(side, fork, 0);
-                if (eb == cudaSuccess) eb = launch_predict(A, A.t_cand, 0.0, true, side);
+                if (eb == cudaSuccess) eb = launch_predict(Au, Au.t_known, 0.0, true, side);
                 if (eb == cudaSuccess) eb = cudaEventRecord(join, side);
-                if (eb == cudaSuccess) eb = launch_select(A, SEL_KNOWN, (unsigned long long)h, true, ctx->stream);
+                if (eb == cudaSuccess) eb = launch_select(Au, SEL_KNOWN, (unsigned long long)h, true, ctx->stream);
                 if (eb == cudaSuccess) eb = cudaStreamWaitEvent(ctx->stream, join, 0);
-                if (eb == cudaSuccess) {
-                    ForceArgs F = force_args(ctx);
-                    F.t_src = ctx->t_min2;
-                    F.t_dst = ctx->t_cand;
-                    eb = launch_force(ctx, F);
-                }
-                if (eb == cudaSuccess) eb = launch_correct(A, false, true, ctx->stream);
+                if (eb == cudaSuccess) eb = launch_force(ctx, force_args(ctx));
+                if (eb == cudaSuccess) eb = launch_correct(Au, false, true, ctx->stream);
             }
             cudaGraph_t body_out = body;
             ee = cudaStreamEndCapture(ctx->stream, &body_out);
@@ -519,7 +519,7 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
     (void)force_mixed_ctas_per_sm();   // sets kernel attributes before any graph capture
     (void)force_f64_ctas_per_sm();
     bool ok = dalloc(&ctx->s, 1) == cudaSuccess && dalloc(&ctx->t_next, 1) == cudaSuccess &&
-              dalloc(&ctx->t_cand, 1) == cudaSuccess && dalloc(&ctx->t_min2, 1) == cudaSuccess &&
+              dalloc(&ctx->t_slot, 2) == cudaSuccess &&
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
               dalloc(&ctx->counters, 3 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
@@ -550,7 +550,7 @@ void nb_destroy(nb_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_system(ctx);
     nb_ctx_set_ensemble(ctx, nullptr);
-    void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_cand, ctx->t_min2, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
+    void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_slot, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
                     ctx->counters, ctx->interactions, ctx->en_out};
     for (void *p : ptrs) dfree(p);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);

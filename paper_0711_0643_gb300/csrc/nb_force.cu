@@ -104,6 +104,7 @@ struct __align__(128) Smem {
     uint64_t inject_bar;
     int64_t s;                 // active count of this launch
     Tuning tune;               // the device tuning table, read once per CTA
+    int32_t idx_pre[kThreads]; // the first kThreads entries of the active list, read with s
     int abort;
     int last;
 };
@@ -116,15 +117,30 @@ __device__ __forceinline__ int bucket_of(int64_t s)
     return b;
 }
 
+// a / b for a >= 0, b > 0. A 64-bit division is a long dependent instruction
+// chain on this GPU (several of them sat on the critical path of every launch);
+// the 32-bit one is short, and the sizes of a launch fit in 32 bits.
+__device__ __forceinline__ int64_t qdiv(int64_t a, int64_t b)
+{
+    if ((((uint64_t)a | (uint64_t)b) >> 32) == 0) return (int64_t)((uint32_t)a / (uint32_t)b);
+    return a / b;
+}
+
 // The table's split is the one for its bucket's largest size s_ref = min(2^b, n);
 // a smaller block of the bucket keeps the same number of work items (i-blocks x
 // splits), so a wave-aligned choice stays wave-aligned.
 __device__ __forceinline__ int table_split(int S_ref, int b, int64_t s, int64_t n, int64_t I)
 {
     const int64_t s_ref = (int64_t(1) << b) < n ? (int64_t(1) << b) : n;
-    const int64_t nib_ref = (s_ref + I - 1) / I, nib = (s + I - 1) / I;
-    const int64_t S = (int64_t)S_ref * nib_ref / nib;
+    const int64_t nib_ref = qdiv(s_ref + I - 1, I), nib = qdiv(s + I - 1, I);
+    const int64_t S = qdiv((int64_t)S_ref * nib_ref, nib);
     return S < 1 ? 1 : (S > (1 << 30) ? (1 << 30) : (int)S);
+}
+
+// Entry jj < s of the active list (the first kThreads from shared memory).
+__device__ __forceinline__ int32_t idx_at(const ForceArgs &A, const Smem *sm, int64_t jj)
+{
+    return jj < kThreads ? sm->idx_pre[jj] : A.idx[jj];
 }
 
 // Split factor clamp shared by both precisions.
@@ -132,7 +148,7 @@ __device__ __forceinline__ int clamp_split(int S, int64_t n_tiles, int64_t s, in
 {
     if (S < 1) S = 1;
     if (S > n_tiles) S = (int)n_tiles;
-    int64_t lim = cap / (s * kPartStride);
+    int64_t lim = qdiv(cap, s * kPartStride);
     if (lim < 1) lim = 1;
     if (S > lim) S = (int)lim;
     return S;
@@ -168,12 +184,12 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
         __threadfence();
         const int64_t ib0 = bx * I;
         const int64_t ib1 = ib0 + I < s ? ib0 + I : s;
-        const int64_t cnt = (ib1 - ib0) * 7;
+        const int cnt = (int)(ib1 - ib0) * 7;
         if (S <= 4) {
             // few splits: one thread per (particle, component)
-            for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
+            for (int q = threadIdx.x; q < cnt; q += kThreads) {
                 const int64_t ii = ib0 + q / 7;
-                const int c = (int)(q % 7);
+                const int c = q % 7;
                 const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
                 float h = 0.f, l = 0.f;
                 for (int sp = 0; sp < S; ++sp) {
@@ -186,9 +202,9 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
             // many splits: one warp per (particle, component); lanes stride over the
             // splits and a fixed butterfly of two-sums combines them
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            for (int64_t q = warp; q < cnt; q += kThreads / 32) {
+            for (int q = warp; q < cnt; q += kThreads / 32) {
                 const int64_t ii = ib0 + q / 7;
-                const int c = (int)(q % 7);
+                const int c = q % 7;
                 const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
                 float h = 0.f, l = 0.f;
                 for (int sp = lane; sp < S; sp += 32) {
@@ -212,7 +228,7 @@ template <int R>
 __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
     const int64_t t0 = (int64_t)by * tper;
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
     const int64_t p0 = t0 * kPT, p1 = t1 * kPT;
@@ -228,7 +244,7 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int64_t ii = bx * R + r;
-        gi[r] = A.idx[ii < s ? ii : s - 1];
+        gi[r] = idx_at(A, sm, ii < s ? ii : s - 1);
         ip[r] = ipk_of(jrec_load(A.j.p, gi[r]));
     }
     const float2 e2 = make_float2(A.eps2f, A.eps2f);
@@ -320,7 +336,7 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     constexpr int kFoldTiles = PPT >= kFoldPairs / 2 ? 0 : (kFoldPairs / 2) / PPT;   // 0: folded inside the sweep
     static_assert(TJ <= 32 && (32 % TJ) == 0, "TJ must divide a warp");
     const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
-    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
     const int64_t t0 = (int64_t)by * tper;
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
@@ -335,14 +351,14 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int64_t ii = bx * I + (int64_t)r * TI + ti;
-        gi[r] = A.idx[ii < s ? ii : s - 1];
+        gi[r] = idx_at(A, sm, ii < s ? ii : s - 1);
         ip[r] = ipk_of(jrec_load(A.j.p, gi[r]));
     }
     const float2 e2 = make_float2(A.eps2f, A.eps2f);
     // index range of this i-block (the active list ascends), for self-exclusion
     const int64_t ib0 = bx * I;
     const int64_t ib1 = (ib0 + I < s ? ib0 + I : s) - 1;
-    const int64_t imin = A.idx[ib0], imax = A.idx[ib1];
+    const int64_t imin = idx_at(A, sm, ib0), imax = idx_at(A, sm, ib1);
 
     AccPk p[R];
     Acc7 hi[R], lo[R];
@@ -410,13 +426,14 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem *sm = reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
+    // read ahead of s: entries past s are stale and never used (idx_cap >= s)
+    const int32_t ipre = tid < A.idx_cap ? A.idx[tid] : 0;
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) mbar_init(&sm->bar[st], 1);
         mbar_init(&sm->inject_bar, 1);
         fence_mbar_init();
         sm->abort = 0;
         sm->s = *A.s;
-        if (A.t_dst && blockIdx.x == 0) *A.t_dst = *A.t_src;
     }
     // the active count and the whole tuning table in one round trip
     if (A.force_variant < 0 && tid < 2 * kBuckets) {
@@ -425,6 +442,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         else
             sm->tune.split[tid - kBuckets] = A.tune->split[tid - kBuckets];
     }
+    sm->idx_pre[tid] = ipre;
     __syncthreads();
     const int64_t s = sm->s;
     if (s <= 0) return;
@@ -448,12 +466,12 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     S = clamp_split(S, A.n_tiles, s, A.part_cap);
     if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
     const int64_t I = mixed_I(variant);
-    const int64_t nib = (s + I - 1) / I;
+    const int64_t nib = qdiv(s + I - 1, I);
     const int64_t W = nib * S;
     uint32_t git = 0;
     for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
-        const int64_t bx = w / S;
-        const int by = (int)(w % S);
+        const int64_t bx = qdiv(w, S);
+        const int by = (int)(w - bx * S);
         switch (variant) {
         case 0: work_stream<1>(A, s, bx, by, S, sm); break;
         case 1: work_stream<2>(A, s, bx, by, S, sm); break;
@@ -509,7 +527,7 @@ __device__ void work_f64_stream(const ForceArgs &A, int64_t s, int64_t bx, int b
     double xi[6];
     load_i64(A, gi, xi);
     const int64_t np = A.n_tiles * kJT;
-    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
     const int64_t t0 = (int64_t)by * tper;
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -540,7 +558,7 @@ __device__ void work_f64_iloop(const ForceArgs &A, int64_t s, int64_t bx, int by
     double xi[6];
     load_i64(A, gi, xi);
     const int64_t np = A.n_tiles * kJT;
-    const int64_t tper = (A.n_tiles + S - 1) / S;
+    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
     const int64_t t0 = (int64_t)by * tper;
     const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -587,7 +605,6 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     __shared__ double red[kThreads / 32][7];
     __shared__ uint64_t inject_bar;
     __shared__ int last;
-    if (A.t_dst && blockIdx.x == 0 && threadIdx.x == 0) *A.t_dst = *A.t_src;
     const int64_t s = *A.s;
     if (s <= 0) return;
     if (A.inject) {
@@ -613,10 +630,10 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     S = clamp_split(S, A.n_tiles, s, A.part_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) *A.split_used = S;
     const int64_t I = f64_I(variant);
-    const int64_t W = ((s + I - 1) / I) * S;
+    const int64_t W = qdiv(s + I - 1, I) * S;
     for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
-        const int64_t bx = w / S;
-        const int by = (int)(w % S);
+        const int64_t bx = qdiv(w, S);
+        const int by = (int)(w - bx * S);
         if (variant == 0)
             work_f64_stream(A, s, bx, by, S, red);
         else

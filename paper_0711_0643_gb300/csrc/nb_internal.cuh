@@ -64,6 +64,7 @@ struct ForceArgs {
     float eps2f;
     double eps2;
     const int32_t *idx;   // active list (ascending), length *s
+    int64_t idx_cap;      // readable entries of idx (>= *s): the kernel reads ahead before *s arrives
     const int64_t *s;     // active count (device)
     double *part;         // split partials [s][split][8] (mixed: float2 (hi, lo) pairs)
     int64_t part_cap;     // capacity of part in 8-byte words
@@ -76,11 +77,6 @@ struct ForceArgs {
     int32_t *status;
     int64_t spin_limit;
     int32_t inject;       // test hook (see nb_config.inject)
-    // nb_run loop only (else null): one thread copies *t_src to *t_dst, the
-    // selection's smallest key above the block time into the slot that the
-    // corrector then lowers to the next block time (see StepArgs::t_cand)
-    const double *t_src;
-    double *t_dst;
 };
 
 // Variant catalogue. Mixed: 0..kMixedVariants-1; FP64: 0..kF64Variants-1.
@@ -121,12 +117,13 @@ struct StepArgs {
     double *t_next;                       // block time
     double *t_end;                        // nb_run target
     // nb_run loop: the next block time is formed while a block is processed.
-    // The selection writes the smallest key above the block time to *t_min2;
-    // the force kernel copies it to *t_cand; the corrector lowers *t_cand by
-    // every new key (atomic minimum on the bit patterns). Keys of inactive
-    // particles do not change, so *t_cand is then the smallest key of all.
-    double *t_cand;
-    double *t_min2;
+    // The selection reads this block's time from *t_known and writes the
+    // smallest key above it to *t_form; the corrector lowers *t_form by every
+    // new key (atomic minimum on the bit patterns). Keys of inactive particles
+    // do not change, so *t_form ends as the smallest key of all: the next
+    // block's *t_known. Consecutive steps swap the two slots.
+    double *t_known;
+    double *t_form;
     const double *fin;                    // final force sums [s][8]
     int32_t *status;
     int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps
@@ -136,14 +133,14 @@ struct StepArgs {
 // predictor to *t_dev (non-null; with skip_past also *t_dev <= *t_end, else no-op) or t_host
 cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st);
 // Selection. SEL_FULL: the smallest key is the block time. SEL_KNOWN (nb_run
-// loop body): the block time is *t_cand; also writes *t_min2 and, when the block
-// is not to be done (past *t_end, an error, the step cap), s = 0.
+// loop body): the block time is *t_known; also writes *t_form and, when the
+// block is not to be done (past *t_end, an error, the step cap), s = 0.
 // set_cond: SEL_FULL sets the while-node condition to "the first block is due"
-// and copies the block time to *t_cand; SEL_KNOWN sets it to "this block is done".
+// and writes the block time to *t_known; SEL_KNOWN sets it to "this block is done".
 enum SelMode { SEL_FULL = 0, SEL_KNOWN = 1 };
 cudaError_t launch_select(const StepArgs &a, SelMode mode, unsigned long long cond, bool set_cond, cudaStream_t st);
-// corrector; lower_cand: atomic minimum of the new keys into *t_cand
-cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_cand, cudaStream_t st);
+// corrector; lower_form: atomic minimum of the new keys into *t_form
+cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, cudaStream_t st);
 cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_reduce_out(const double *fin, const int64_t *s, int64_t s_host, double *a, double *k,
                               double *phi, int32_t *status, cudaStream_t st);

@@ -120,6 +120,7 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     F.eps2f = (float)eps2;
     F.eps2 = eps2;
     F.idx = idx_dev;
+    F.idx_cap = s;
     F.s = reinterpret_cast<const int64_t *>(base + kOffS);
     F.part = reinterpret_cast<double *>(base + kOffPart);
     F.part_cap = kStaticPartWords;

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(T) select_kernel(StepArgs A, cudaGraphConditio
     const int64_t n = A.n, np = A.n_pad;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
     const int64_t nchunk = (np + kSelChunk - 1) / kSelChunk;
-    const int64_t cpc = (nchunk + C - 1) / C;
+    const int64_t cpc = (int64_t)(((uint32_t)nchunk + (uint32_t)C - 1u) / (uint32_t)C);   // nchunk < 2^32
     const int64_t ch0 = (int64_t)rank * cpc < nchunk ? (int64_t)rank * cpc : nchunk;
     const int64_t ch1 = ch0 + cpc < nchunk ? ch0 + cpc : nchunk;
     const bool resident = ch1 - ch0 <= 1;   // the keys stay in registers between the passes
@@ -286,13 +286,13 @@ __global__ void __launch_bounds__(T) select_kernel(StepArgs A, cudaGraphConditio
             const bool ok = (tmin <= *A.t_end) && s > 0 && (*A.status == 0);
             bool more = ok && (A.counters[0] < A.counters[2]);
             if (ok && !more) atomicOr(A.status, kStSteps);
-            *A.t_cand = tmin;   // the nb_run loop body's first block time
+            *A.t_known = tmin;   // the nb_run loop body's first block time
             cudaGraphSetConditional(cond, more ? 1u : 0u);
         }
     }
 }
 
-// The nb_run loop body's selection, at a known block time (*t_cand, formed by
+// The nb_run loop body's selection, at a known block time (*t_known, formed by
 // the previous corrector): no minimum pass. A cluster of C CTAs (C <= 16) splits
 // the keys in chunks of 16 T keys; one pass gives every warp its hits (ballots)
 // and its smallest key other than the block time. The CTA totals and minima go
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(T) select_kernel(StepArgs A, cudaGraphConditio
 // writes its hits after those of the lower ranks, ascending. With one chunk per
 // CTA the ballots stay in registers between the count and the write.
 // Writes s (0 when the block is not to be done: past *t_end, an error, the step
-// cap; force and corrector are then no-ops), t_next and t_min2, and sets the
+// cap; force and corrector are then no-ops), t_next and *t_form, and sets the
 // while-node condition to "this block is done".
 template <int T>
 __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphConditionalHandle cond)
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphCo
     const int64_t np = A.n_pad;
     const long long *key = reinterpret_cast<const long long *>(A.tn);
     const int64_t nchunk = (np + kChunk - 1) / kChunk;
-    const int64_t cpc = (nchunk + C - 1) / C;
+    const int64_t cpc = (int64_t)(((uint32_t)nchunk + (uint32_t)C - 1u) / (uint32_t)C);   // nchunk < 2^32
     const int64_t ch0 = (int64_t)rank * cpc < nchunk ? (int64_t)rank * cpc : nchunk;
     const int64_t ch1 = ch0 + cpc < nchunk ? ch0 + cpc : nchunk;
     const bool resident = ch1 - ch0 <= 1;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphCo
     const double t_end = lead ? *A.t_end : 0.0;
     const int32_t status0 = lead ? *A.status : 0;
     const bool cap_ok = lead ? A.counters[0] < A.counters[2] : false;
-    const long long kmin = *reinterpret_cast<const long long *>(A.t_cand);
+    const long long kmin = *reinterpret_cast<const long long *>(A.t_known);
     // padding keys and keys past n_pad are +inf: with a finite block time every
     // hit is a particle; an infinite one selects nothing
     const bool live = kmin < kInf;
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphCo
         if (ok && !more) atomicOr(A.status, kStSteps);
         *A.s = more ? s : 0;
         *A.t_next = tmin;
-        *A.t_min2 = more ? __longlong_as_double(m2all) : tmin;
+        *A.t_form = more ? __longlong_as_double(m2all) : tmin;
         cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
 }
@@ -458,7 +458,7 @@ __device__ __forceinline__ void load_fin(const double *fin, int64_t ii, double *
 constexpr int kCorThreads = 128;
 constexpr int kCorPer = kCorThreads / 4;
 
-__global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int check_due, int lower_cand)
+__global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int check_due, int lower_form)
 {
     const int64_t s = *A.s;
     const double tn = *A.t_next;
@@ -481,12 +481,12 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
         flags |= correct_group(H, i, live, tn, an, kn, A.eta, A.dt_max, A.dt_min, &key);
         kmin = key < kmin ? key : kmin;
     }
-    if (lower_cand) {
-        // the next block time: the smallest of the unchanged keys (*t_cand, from
+    if (lower_form) {
+        // the next block time: the smallest of the unchanged keys (*t_form, from
         // the selection) and the new ones; non-negative doubles order like their bits
         kmin = warp_min_ll(kmin);
         if ((threadIdx.x & 31) == 0 && kmin != 0x7ff0000000000000LL)
-            atomicMin(reinterpret_cast<long long *>(A.t_cand), kmin);
+            atomicMin(reinterpret_cast<long long *>(A.t_form), kmin);
     }
     if (flags) atomicOr(A.status, flags);
     if (blockIdx.x == 0 && threadIdx.x == 0 && s > 0) {
@@ -904,10 +904,10 @@ cudaError_t launch_select(const StepArgs &a, SelMode mode, unsigned long long co
     return launch_select_known_T<512>(a, cond, st);
 }
 
-cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_cand, cudaStream_t st)
+cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, cudaStream_t st)
 {
     // one round covers blocks of up to 608 * 32 particles; CTAs past s exit at once
-    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0, lower_cand ? 1 : 0);
+    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0, lower_form ? 1 : 0);
     return cudaGetLastError();
 }
 
