@@ -96,7 +96,7 @@ nb_status nb_ctx_fail(nb_ctx *ctx, nb_status st, const char *msg)
 namespace {
 
 constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
-constexpr int kRunUnroll = 4;                          // block steps per pass of the nb_run while node
+constexpr int kRunUnroll = 16;                         // block steps per pass of the nb_run while node
 static_assert(kRunUnroll % 2 == 0, "the loop's steps alternate two block-time slots");
 
 nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
@@ -422,7 +422,7 @@ nb_status build_run_graph(nb_ctx *ctx)
                 if (eb == cudaSuccess) eb = launch_select(Au, SEL_KNOWN, (unsigned long long)h, true, ctx->stream);
                 if (eb == cudaSuccess) eb = cudaStreamWaitEvent(ctx->stream, join, 0);
                 if (eb == cudaSuccess) eb = launch_force(ctx, force_args(ctx));
-                if (eb == cudaSuccess) eb = launch_correct(Au, false, true, ctx->stream);
+                if (eb == cudaSuccess) eb = launch_correct(Au, false, true, true, ctx->stream);
             }
             cudaGraph_t body_out = body;
             ee = cudaStreamEndCapture(ctx->stream, &body_out);
@@ -703,7 +703,7 @@ nb_status nb_correct(nb_ctx *ctx, double t_block)
     CK(launch_check_due(A, t_block, ctx->stream));
     st = sync_status(ctx);
     if (st != NB_OK) return st;
-    CK(launch_correct(A, true, false, ctx->stream));
+    CK(launch_correct(A, true, false, false, ctx->stream));
     ctx->forces_pending = false;
     return sync_status(ctx);
 }
@@ -716,7 +716,7 @@ nb_status nb_step(nb_ctx *ctx)
     CK(launch_select(A, SEL_FULL, 0, false, ctx->stream));
     CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream));
     CK(launch_force_ctx(ctx));
-    CK(launch_correct(A, false, false, ctx->stream));
+    CK(launch_correct(A, false, false, false, ctx->stream));
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);
@@ -801,7 +801,7 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
         CK(launch_force_ctx(ctx));
         CK(close(2));
         if (phases) CK(open(3));
-        CK(launch_correct(A, false, false, ctx->stream));
+        CK(launch_correct(A, false, false, false, ctx->stream));
         if (phases) CK(close(3));
         int32_t stw = 0;
         CK(cudaMemcpyAsync(&stw, ctx->status, sizeof stw, cudaMemcpyDeviceToHost, ctx->stream));

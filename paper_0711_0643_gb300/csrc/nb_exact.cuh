@@ -144,6 +144,79 @@ __device__ __forceinline__ double div6(double y) { return div_const(y, 3.0, 1.0 
 __device__ __forceinline__ double div24(double y) { return div_const(y, 3.0, 1.0 / 3.0, 0.125, 24.0); }
 __device__ __forceinline__ double div120(double y) { return div_const(y, 15.0, 1.0 / 15.0, 0.125, 120.0); }
 
+// High 64 bits of the 128-bit product a b.
+__host__ __device__ __forceinline__ unsigned long long umulhi64(unsigned long long a, unsigned long long b)
+{
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Correctly rounded y / 3 * 2^-s (s = 1: y / 6, s = 3: y / 24) and y / 15 * 2^-s
+// (s = 3: y / 120) on the integer pipe; false when the biased exponent E of y is
+// outside [64, 2046] (zero, subnormal, inf, NaN and huge values: the caller
+// divides in FP64). With y = +-M 2^(E - 1075), M in [2^52, 2^53), N = M 2^k puts
+// N / d in [2^52, 2^53); Q = floor(N / d) is a multiply-high by m = ceil(2^(64+l)
+// / d) and a shift by l (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994: m d - 2^(64+l) <= 2^l holds, 1 for d = 3,
+// l = 1 and 7 for d = 15, l = 3). The exact quotient is Q + R / d with R = N - d Q;
+// rounding to nearest takes Q + 1 when R / d > 1/2 (R / d = 1/2 is impossible for
+// odd d), and Q + 1 < 2^53 always.
+__host__ __device__ __forceinline__ bool div3_int(double y, int s, double &out)
+{
+    const long long yb = dbits(y);
+    const int E = (int)((yb >> 52) & 0x7ff);
+    if (E < 64 || E > 2046) return false;
+    const unsigned long long M = ((unsigned long long)yb & ((1ull << 52) - 1)) | (1ull << 52);
+    const int k = M >= (3ull << 51) ? 1 : 2;
+    const unsigned long long N = M << k;
+    const unsigned long long Q = umulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
+    const unsigned long long Qr = Q + ((N - 3 * Q) == 2 ? 1 : 0);
+    out = dfrom((long long)((unsigned long long)yb & 0x8000000000000000ull) | ((long long)(E - k - s) << 52) |
+                (long long)(Qr - (1ull << 52)));
+    return true;
+}
+__host__ __device__ __forceinline__ bool div15_int(double y, int s, double &out)
+{
+    const long long yb = dbits(y);
+    const int E = (int)((yb >> 52) & 0x7ff);
+    if (E < 64 || E > 2046) return false;
+    const unsigned long long M = ((unsigned long long)yb & ((1ull << 52) - 1)) | (1ull << 52);
+    const int k = M >= (15ull << 49) ? 3 : 4;
+    const unsigned long long N = M << k;
+    const unsigned long long Q = umulhi64(N, 0x8888888888888889ull) >> 3;
+    const unsigned long long Qr = Q + ((N - 15 * Q) >= 8 ? 1 : 0);
+    out = dfrom((long long)((unsigned long long)yb & 0x8000000000000000ull) | ((long long)(E - k - s) << 52) |
+                (long long)(Qr - (1ull << 52)));
+    return true;
+}
+
+// Correctly rounded 3 y 2^s (0 <= s <= 3) on the integer pipe, ties to even;
+// false outside biased exponents [1, 2040] of y. P = 3 M has 54 or 55 bits; the
+// low sh = 1 or 2 bits are rounded off and a carry to 2^53 renormalises.
+__host__ __device__ __forceinline__ bool mul3_int(double y, int s, double &out)
+{
+    const long long yb = dbits(y);
+    const int E = (int)((yb >> 52) & 0x7ff);
+    if (E < 1 || E > 2040) return false;
+    const unsigned long long M = ((unsigned long long)yb & ((1ull << 52) - 1)) | (1ull << 52);
+    const unsigned long long P = 3 * M;
+    const int sh = P >= (1ull << 54) ? 2 : 1;
+    unsigned long long q = P >> sh;
+    const unsigned long long r = P & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    q += (r > half || (r == half && (q & 1))) ? 1 : 0;
+    int Eo = E + sh + s;
+    if (q == (1ull << 53)) {
+        q >>= 1;
+        ++Eo;
+    }
+    out = dfrom((long long)((unsigned long long)yb & 0x8000000000000000ull) | ((long long)Eo << 52) |
+                (long long)(q - (1ull << 52)));
+    return true;
+}
+
 // 1/p for a power of two p whose reciprocal is normal (biased exponent of p in
 // [1, 2045]): the exponent field reflected about the bias, no FP64 instruction.
 __device__ __forceinline__ double recip_pow2(double p) { return dfrom((0x7FEll << 52) - dbits(p)); }

@@ -426,6 +426,10 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem *sm = reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
+    // a launch that depends on this one programmatically (the nb_run loop's
+    // corrector) may start now: it reads only what was written before this kernel
+    // until it waits for this grid's completion
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // read ahead of s: entries past s are stale and never used (idx_cap >= s)
     const int32_t ipre = tid < A.idx_cap ? A.idx[tid] : 0;
     if (tid == 0) {
@@ -605,6 +609,7 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     __shared__ double red[kThreads / 32][7];
     __shared__ uint64_t inject_bar;
     __shared__ int last;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t s = *A.s;
     if (s <= 0) return;
     if (A.inject) {

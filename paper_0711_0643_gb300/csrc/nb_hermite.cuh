@@ -192,33 +192,30 @@ __device__ __forceinline__ double pick4(double v0, double v1, double v2, double 
 // component min(q, 2) of the new a and k. i must be a valid particle even when
 // live is false: the group then computes without storing. Returns status bits;
 // lane 3 of a live group also writes the new key t + dt to *key_out if given.
+// y / 6, y / 24, y / 120 and 3 y 2^s, correctly rounded, on the integer pipe
+// (nb_exact.cuh); the FP64 unit only out of line, outside the exponent window.
+static __device__ __noinline__ double ddiv_slow(double y, double d) { return __ddiv_rn(y, d); }
 __device__ __forceinline__ double rn_div6(double y)
 {
-    const int e = dexpo(y);
-    if (e >= 63 && e <= 2023) {
-        const double q = __dmul_rn(y, 1.0 / 3.0);
-        return scale2(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), -1, 0.5);
-    }
-    return __ddiv_rn(y, 6.0);
+    double q;
+    return div3_int(y, 1, q) ? q : ddiv_slow(y, 6.0);
 }
 __device__ __forceinline__ double rn_div24(double y)
 {
-    const int e = dexpo(y);
-    if (e >= 63 && e <= 2023) {
-        const double q = __dmul_rn(y, 1.0 / 3.0);
-        return scale2(__fma_rn(__fma_rn(-q, 3.0, y), 1.0 / 3.0, q), -3, 0.125);
-    }
-    return __ddiv_rn(y, 24.0);
+    double q;
+    return div3_int(y, 3, q) ? q : ddiv_slow(y, 24.0);
 }
 __device__ __forceinline__ double rn_div120(double y)
 {
-    const int e = dexpo(y);
-    if (e >= 63 && e <= 2023) {
-        const double q = __dmul_rn(y, 1.0 / 15.0);
-        return scale2(__fma_rn(__fma_rn(-q, 15.0, y), 1.0 / 15.0, q), -3, 0.125);
-    }
-    return __ddiv_rn(y, 120.0);
+    double q;
+    return div15_int(y, 3, q) ? q : ddiv_slow(y, 120.0);
 }
+__device__ __forceinline__ double rn_mul3(double y, int s, double p)   // p = 3 * 2^s
+{
+    double q;
+    return mul3_int(y, s, q) ? q : dmul_slow(y, p);
+}
+__device__ __forceinline__ double dneg(double x) { return dfrom(dbits(x) ^ (long long)0x8000000000000000ull); }
 static __device__ __noinline__ float2 ds_pack_slow(double x)
 {
     const float h = __double2float_rn(x);
@@ -265,9 +262,10 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
         const double xp = __dadd_rn(__dadd_rn(__dadd_rn(x, scale2(v, e, dt)), scale2(scale2(ao, 2 * e, d2), -1, 0.5)),
                                     rn_div6(scale2(ko, 3 * e, d3)));
         const double vp = __dadd_rn(__dadd_rn(v, scale2(ao, e, dt)), scale2(scale2(ko, 2 * e, d2), -1, 0.5));
-        a2 = __dsub_rn(scale2(__dmul_rn(-6.0, da), -2 * e, i2),
+        // -6 da, 12 da and 6 (k_old + k_new) as exact integer products (same bits)
+        a2 = __dsub_rn(scale2(dneg(rn_mul3(da, 1, 6.0)), -2 * e, i2),
                        scale2(__dadd_rn(scale2(ko, 2, 4.0), scale2(kn, 1, 2.0)), -e, i1));
-        a3 = __dadd_rn(scale2(__dmul_rn(12.0, da), -3 * e, i3), scale2(__dmul_rn(6.0, __dadd_rn(ko, kn)), -2 * e, i2));
+        a3 = __dadd_rn(scale2(rn_mul3(da, 2, 12.0), -3 * e, i3), scale2(rn_mul3(__dadd_rn(ko, kn), 1, 6.0), -2 * e, i2));
         x1 = __dadd_rn(__dadd_rn(xp, rn_div24(scale2(a2, 4 * e, d4))), rn_div120(scale2(a3, 5 * e, d5)));
         v1 = __dadd_rn(__dadd_rn(vp, rn_div6(scale2(a2, 3 * e, d3))), rn_div24(scale2(a3, 4 * e, d4)));
     } else {

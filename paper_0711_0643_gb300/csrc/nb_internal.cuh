@@ -139,8 +139,10 @@ cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host
 // and writes the block time to *t_known; SEL_KNOWN sets it to "this block is done".
 enum SelMode { SEL_FULL = 0, SEL_KNOWN = 1 };
 cudaError_t launch_select(const StepArgs &a, SelMode mode, unsigned long long cond, bool set_cond, cudaStream_t st);
-// corrector; lower_form: atomic minimum of the new keys into *t_form
-cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, cudaStream_t st);
+// corrector; lower_form: atomic minimum of the new keys into *t_form;
+// after_force: launched with a programmatic dependency on the force kernel
+// launched just before it on the stream (its first loads overlap that kernel)
+cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, bool after_force, cudaStream_t st);
 cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st);
 cudaError_t launch_reduce_out(const double *fin, const int64_t *s, int64_t s_host, double *a, double *k,
                               double *phi, int32_t *status, cudaStream_t st);

@@ -465,6 +465,26 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
     const HState H{A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, A.n_pad};
     const int q = threadIdx.x & 3;
     const int c = q < 3 ? q : 2;
+    {
+        // Launched programmatically after the force kernel (nb_run loop), this
+        // part overlaps its end: the active list, the block time and the state
+        // were written before it, only the new forces (fin) after. The first
+        // particle's state moves into L1; then wait for the force grid.
+        const int64_t ii = (int64_t)blockIdx.x * kCorPer + (threadIdx.x >> 2);
+        if (ii < s) {
+            const int64_t i = A.idx[ii];
+            const int64_t o = c * A.n_pad + i;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.x + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.v + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.a + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.k + o));
+            if (q == 3) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(H.t + i));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(H.dt + i));
+            }
+        }
+        asm volatile("griddepcontrol.wait;" ::: "memory");   // returns at once without such a dependency
+    }
     int flags = 0;
     long long kmin = 0x7ff0000000000000LL;   // smallest new key of this thread's particles
     for (int64_t base = (int64_t)blockIdx.x * kCorPer; base < s; base += (int64_t)gridDim.x * kCorPer) {
@@ -904,11 +924,22 @@ cudaError_t launch_select(const StepArgs &a, SelMode mode, unsigned long long co
     return launch_select_known_T<512>(a, cond, st);
 }
 
-cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, cudaStream_t st)
+cudaError_t launch_correct(const StepArgs &a, bool check_due, bool lower_form, bool after_force, cudaStream_t st)
 {
     // one round covers blocks of up to 608 * 32 particles; CTAs past s exit at once
-    correct_kernel<<<grid_for(a.n, kCorPer, 608), kCorThreads, 0, st>>>(a, check_due ? 1 : 0, lower_form ? 1 : 0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid_for(a.n, kCorPer, 608));
+    cfg.blockDim = dim3(kCorThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    if (after_force) {
+        // programmatic dependency on the force kernel just before it in the stream
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, correct_kernel, a, check_due ? 1 : 0, lower_form ? 1 : 0);
 }
 
 cudaError_t launch_init_steps(const StepArgs &a, cudaStream_t st)

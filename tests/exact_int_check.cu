@@ -1,0 +1,70 @@
+// Host check of the integer-pipe exact helpers of nb_exact.cuh against the host's
+// IEEE double arithmetic (correctly rounded by IEEE 754): div3_int, div15_int and
+// mul3_int must return the bits of y / 6, y / 24, y / 120 and 3 y 2^s wherever they
+// accept y. Random and edge significands over the whole accepted exponent window.
+// Usage: exact_int_check [cases]; exits non-zero on the first mismatch.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "nb_exact.cuh"
+
+using namespace nb;
+
+static unsigned long long sm_state = 0x2007110812345678ull;
+static unsigned long long splitmix()
+{
+    unsigned long long z = (sm_state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int fails = 0;
+static void check(const char *what, double y, bool ok, double got, double ref)
+{
+    if (!ok) return;
+    if (dbits(got) != dbits(ref)) {
+        if (fails < 10)
+            std::printf("MISMATCH %s y=%a got=%a ref=%a\n", what, y, got, ref);
+        ++fails;
+    }
+}
+
+int main(int argc, char **argv)
+{
+    const long long cases = argc > 1 ? std::atoll(argv[1]) : 4000000;
+    const unsigned long long edges[] = {0ull, 1ull, 2ull, (1ull << 52) - 1, (1ull << 52) - 2, (1ull << 51),
+                                        (1ull << 51) - 1, (1ull << 51) + 1, (1ull << 50), (1ull << 49),
+                                        (3ull << 49) - 1, (3ull << 49), (7ull << 49) - 1, (7ull << 49),
+                                        (5ull << 48), 0x5555555555555ull, 0xAAAAAAAAAAAAAull,
+                                        0x1111111111111ull, 0x8888888888888ull, 0x2AAAAAAAAAAAAull};
+    long long accepted = 0, declined = 0;
+    for (long long n = 0; n < cases; ++n) {
+        const unsigned long long r = splitmix();
+        unsigned long long mant = r & ((1ull << 52) - 1);
+        if ((n & 7) == 0) mant = edges[(r >> 52) % (sizeof edges / sizeof edges[0])] ^ ((r >> 60) & 1);
+        const int E = (int)(splitmix() % 2047);   // every biased exponent but inf/NaN
+        const unsigned long long sign = (splitmix() & 1) << 63;
+        const double y = dfrom((long long)(sign | ((unsigned long long)E << 52) | mant));
+        double out;
+        bool ok;
+        ok = div3_int(y, 1, out);
+        check("y/6", y, ok, out, y / 6.0);
+        accepted += ok; declined += !ok;
+        ok = div3_int(y, 3, out);
+        check("y/24", y, ok, out, y / 24.0);
+        ok = div3_int(y, 0, out);
+        check("y/3", y, ok, out, y / 3.0);
+        ok = div15_int(y, 3, out);
+        check("y/120", y, ok, out, y / 120.0);
+        ok = div15_int(y, 0, out);
+        check("y/15", y, ok, out, y / 15.0);
+        for (int s = 0; s <= 3; ++s) {
+            ok = mul3_int(y, s, out);
+            check("3y*2^s", y, ok, out, (3.0 * y) * std::ldexp(1.0, s));
+        }
+    }
+    std::printf("cases %lld (div3 accepted %lld, declined %lld), mismatches %d\n", cases, accepted, declined, fails);
+    return fails ? 1 : 0;
+}
