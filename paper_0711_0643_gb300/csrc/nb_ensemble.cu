@@ -551,8 +551,13 @@ void ensemble_free(nb_ensemble *e)
     delete e;
 }
 
-// Chooses the cluster size (16 when allowed, else 8) and the number of clusters
-// that are resident at once.
+// Chooses the cluster size and the number of clusters that are resident at
+// once: the largest of 16, 8, 4 CTAs per cluster whose resident clusters keep
+// at least 90 % of the kernel's resident CTAs busy. Clusters must fit inside a
+// GPC, so on this GPU 16-CTA clusters leave a quarter of the CTA slots empty
+// (14 clusters, 224 of 304 CTAs) where 8-CTA clusters fill 288: measured on the
+// 256-cluster workload, 4.37 s with 16 against 2.46 s with 8 (3.4 s with 4,
+// 6.2 s with 2: smaller clusters lengthen every system's block step).
 static cudaError_t ensemble_shape(int *cluster, int *nclusters)
 {
     static int c_cached = 0, n_cached = 0;
@@ -562,7 +567,15 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
         return cudaSuccess;
     }
     cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    for (int C : {16, 8}) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel, kEnsThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return cudaErrorInvalidConfiguration;
+    const int slots = sms * per_sm;
+    int best_c = 0, best_n = 0;
+    for (int C : {16, 8, 4}) {
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -575,17 +588,27 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclu = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclu, ensemble_kernel, &cfg) == cudaSuccess && nclu > 0) {
-            c_cached = C;
-            n_cached = nclu;
-            *cluster = C;
-            *nclusters = nclu;
+        if (cudaOccupancyMaxActiveClusters(&nclu, ensemble_kernel, &cfg) != cudaSuccess || nclu < 1) {
             cudaGetLastError();
-            return cudaSuccess;
+            continue;
         }
-        cudaGetLastError();
+        if (!best_c) {   // fallback: the largest size that runs at all
+            best_c = C;
+            best_n = nclu;
+        }
+        if (10 * C * nclu >= 9 * slots) {
+            best_c = C;
+            best_n = nclu;
+            break;
+        }
     }
-    return cudaErrorInvalidConfiguration;
+    cudaGetLastError();
+    if (!best_c) return cudaErrorInvalidConfiguration;
+    c_cached = best_c;
+    n_cached = best_n;
+    *cluster = best_c;
+    *nclusters = best_n;
+    return cudaSuccess;
 }
 
 cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_max, double dt_min, cudaStream_t st)
