@@ -383,11 +383,14 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
             if (flags) atomicOr(&sm->err, flags);
             flags = 0;
             cluster.sync();
-            long long kmin = 0x7ff0000000000000LL;
-            int err = 0;
-            for (int q = 0; q < C; ++q) {
-                kmin = min_ll(kmin, *cluster.map_shared_rank(&sm->kmin, q));
-                err |= *cluster.map_shared_rank(&sm->err, q);
+            // lane q reads rank q's minimum and flags (C <= 32): one round of
+            // distributed shared-memory loads, then warp reductions
+            long long kmin = lane < C ? *cluster.map_shared_rank(&sm->kmin, lane) : 0x7ff0000000000000LL;
+            int err = lane < C ? *cluster.map_shared_rank(&sm->err, lane) : 0;
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                kmin = min_ll(kmin, __shfl_xor_sync(0xffffffffu, kmin, off));
+                err |= __shfl_xor_sync(0xffffffffu, err, off);
             }
             const double tblock = __longlong_as_double(kmin);
             int cnt = 0;
@@ -408,10 +411,16 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
             if (tid == 0) sm->cnt = total;
             cluster.sync();
             int64_t offset = 0, s = 0;
-            for (int q = 0; q < C; ++q) {
-                const int cq = *cluster.map_shared_rank(&sm->cnt, q);
-                if (q < rank) offset += cq;
-                s += cq;
+            {
+                const int cq = lane < C ? *cluster.map_shared_rank(&sm->cnt, lane) : 0;
+                int lo = lane < rank ? cq : 0, all = cq;
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    lo += __shfl_xor_sync(0xffffffffu, lo, off);
+                    all += __shfl_xor_sync(0xffffffffu, all, off);
+                }
+                offset = lo;
+                s = all;
             }
             const bool go = (tblock <= E.t_end) && s > 0 && err == 0 && nsteps < E.max_steps;
             if (!go) {
@@ -454,10 +463,11 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
                     __syncthreads();
                 }
             } else {
-                // every CTA takes an even-aligned share of j (pair records stay whole)
-                const int64_t jc = ((N + C - 1) / C + 1) / 2 * 2;
-                const int64_t j0 = (int64_t)rank * jc < N ? (int64_t)rank * jc : N;
-                const int64_t j1 = j0 + jc < N ? j0 + jc : N;
+                // every CTA takes an even-aligned share of j (pair records stay whole);
+                // 32-bit division (N < 2^19)
+                const int64_t jcs = (int64_t)((((uint32_t)N + (uint32_t)C - 1u) / (uint32_t)C + 1u) / 2u * 2u);
+                const int64_t j0 = (int64_t)rank * jcs < N ? (int64_t)rank * jcs : N;
+                const int64_t j1 = j0 + jcs < N ? j0 + jcs : N;
                 if (j1 > j0) {
                     cta_force_any(E, base, act, 0, s, j0, j1, eps2f, part, (int64_t)rank * s, sm);
                 } else {

@@ -380,14 +380,17 @@ __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphCo
         asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     }
     cluster.sync();   // every rank's total and minimum are in this CTA's shared memory
-    int out = 0, total = 0;
-    long long m2all = kInf;
-    for (int r = 0; r < C; ++r) {
-        const int cr = r_cnt[r];
-        if (r < rank) out += cr;
-        total += cr;
-        m2all = r_min[r] < m2all ? r_min[r] : m2all;
+    // lane r holds rank r's entries; warp reductions give this CTA's offset (the
+    // lower ranks' hits), the total and the smallest other key
+    const int cr = lane < C ? r_cnt[lane] : 0;
+    int out = lane < rank ? cr : 0, total = cr;
+    long long m2all = lane < C ? r_min[lane] : kInf;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        out += __shfl_xor_sync(0xffffffffu, out, off);
+        total += __shfl_xor_sync(0xffffffffu, total, off);
     }
+    m2all = warp_min_ll(m2all);
     for (int64_t ch = ch0; ch < ch1; ++ch) {
         const int64_t c0 = ch * kChunk;
         if (!resident) {
