@@ -369,7 +369,13 @@ __global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
             const int64_t sub = (c1 - c0 + kEnsThreads - 1) / kEnsThreads;
             const int64_t s0 = c0 + tid * sub < c1 ? c0 + tid * sub : c1;
             const int64_t s1 = s0 + sub < c1 ? s0 + sub : c1;
-            for (int64_t q = s0; q < s1; ++q) mloc = min_ll(mloc, key[q]);
+            for (int64_t q = s0; q < s1; q += 4) {   // four loads in flight
+                long long kv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) kv[u] = q + u < s1 ? key[q + u] : 0x7ff0000000000000LL;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) mloc = min_ll(mloc, kv[u]);
+            }
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) mloc = min_ll(mloc, __shfl_xor_sync(0xffffffffu, mloc, off));
             if (lane == 0) sm->wmin[warp] = mloc;
