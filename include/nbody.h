@@ -163,8 +163,11 @@ nb_status nb_correct(nb_ctx *ctx, double t_block);
 nb_status nb_step(nb_ctx *ctx);
 
 /* Block steps until the next block time exceeds t_end (t_end must be a multiple
- * of dt_max for every particle to land on it). One CUDA-graph launch whose
- * while-node repeats predict -> force -> correct -> select on the device.
+ * of dt_max for every particle to land on it). One CUDA-graph launch: a full
+ * selection, then a while node whose body runs 16 block steps of
+ * [selection at the known block time || predictor] -> force -> corrector on
+ * the device (the corrector forms the next block time; steps past t_end are
+ * no-ops). Same trajectory, bit for bit, as repeated nb_step.
  * One call runs at most 2^22 block steps (then NB_ERR_STATE, "block-step cap"). */
 nb_status nb_run(nb_ctx *ctx, double t_end);
 
@@ -179,8 +182,10 @@ nb_status nb_run(nb_ctx *ctx, double t_end);
 nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms);
 
 /* Kinetic, potential (softened, W = sum m_i phi_i / 2) and total energy of the
- * current state, in FP64 on the device. Exact only when all t_i are equal
- * (e.g. after nb_run). Any pointer may be NULL. */
+ * current state, on the device: K in FP64; the pair terms of W in double-single
+ * arithmetic on the FP32 pipe (agrees with FP64 sums to ~1e-15 relative) with
+ * FP64 per-particle and fixed-order final sums. Exact only when all t_i are
+ * equal (e.g. after nb_run). Any pointer may be NULL. */
 nb_status nb_energy(nb_ctx *ctx, double *E, double *K, double *W);
 
 /* Copies the full FP64 state to / from host arrays (view->n must equal the
