@@ -575,7 +575,9 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
                 precision=None):
     """King W0 = 6, N = 1,048,576, eps = 1e-3: one mixed force evaluation per active-set
     size s in {1, 64, 1024, 16384, N} (active = first s of a seeded permutation, ascending),
-    split factor autotuned; interactions/s and FP32 roofline fraction per s."""
+    split factor autotuned; interactions/s and FP32 roofline fraction per s. Each point is
+    the median of single nb_force_jerk_dev calls (active list in, a/k/phi out, all on the
+    device), each timed with L2 flushed before it."""
     import ics
     snap = ics.config(5, n=n_override)
     n = snap.n
@@ -590,9 +592,11 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
         nb.nb_autotune(c.ctx)
     perm = np.argsort(ics.SplitMix64(ics.BASE_SEED + 5).uniform(n))
     out = {"workload": f"king W0=6 N={n} eps=1e-3, single evaluation", "points": [],
-           "precision": "fp64" if prec == nb.NB_PREC_FP64 else "mixed"}
+           "precision": "fp64" if prec == nb.NB_PREC_FP64 else "mixed",
+           "l2": "flushed (256 MB write) before every timed call; median of single calls"}
     stream = torch.cuda.current_stream(dev)
     assert stream.cuda_stream == sptr
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     for s in (s_list or (1, 64, 1024, 16384, n)):
         s = min(int(s), n)
         idx = np.sort(perm[:s]).astype(np.int32)
@@ -602,15 +606,20 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
         p_d = torch.empty(s, dtype=torch.float64, device=dev)
         for _ in range(3):
             nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
-        reps = 3 if s < n else 2
+        # each timed call starts with L2 flushed (the j-records, 40 MB at N = 2^20, would
+        # otherwise stay in the 129 MB L2 between calls): median of single calls
+        reps = 9 if s < n else 2
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
+        times = []
         for _ in range(reps):
+            l2_flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
             nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        sec = e0.elapsed_time(e1) / 1e3 / reps
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1) / 1e3)
+        sec = float(np.median(times))
         ips = s * float(n) / sec
         tfl = FLOP_PER_INTERACTION * ips / 1e12
         peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None

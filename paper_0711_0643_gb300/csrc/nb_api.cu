@@ -688,8 +688,7 @@ nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, doub
     if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
     if (s == 0) return NB_OK;
     if (!idx_dev) return fail(ctx, NB_ERR_ARG, "null idx_dev");
-    CK(cudaMemcpyAsync(ctx->idx, idx_dev, s * sizeof(int32_t), cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->s, &s, sizeof s, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_set_active(idx_dev, ctx->idx, s, ctx->s, ctx->stream));
     return force_common(ctx, s, a, k, phi);
 }
 

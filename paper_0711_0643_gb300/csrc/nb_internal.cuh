@@ -152,6 +152,8 @@ cudaError_t launch_aos_to_soa(const double *src, double *dst, int64_t n, int64_t
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int64_t n, int64_t n_pad, cudaStream_t st);
 cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_aos, cudaStream_t st);
 cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st);
+// copies the device list src[s] to dst and writes s to *s_dev (one launch)
+cudaError_t launch_set_active(const int32_t *src, int32_t *dst, int64_t s, int64_t *s_dev, cudaStream_t st);
 cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st);
 // energy: writes K, W to out[0], out[1] (fixed-order sums)
 cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, double *out,

@@ -628,6 +628,14 @@ __global__ void iota_kernel(int32_t *idx, int64_t n)
     for (int64_t i = gtid(); i < n; i += gstride()) idx[i] = (int32_t)i;
 }
 
+// A caller's device active list and its length into the context (one launch
+// instead of a device copy and a host-to-device copy of the count).
+__global__ void set_active_kernel(const int32_t *src, int32_t *dst, int64_t s, int64_t *s_dev)
+{
+    for (int64_t i = gtid(); i < s; i += gstride()) dst[i] = src[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *s_dev = s;
+}
+
 // ------------------------------------------------------------------- energy
 // K = sum m v^2 / 2, W = sum m_i phi_i / 2 with the softened FP64 potential.
 // Each CTA sums its particles in a fixed order into scratch[cta][2]; a single
@@ -980,6 +988,12 @@ cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_
 cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st)
 {
     iota_kernel<<<grid_for(n, kStepThreads), kStepThreads, 0, st>>>(idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_active(const int32_t *src, int32_t *dst, int64_t s, int64_t *s_dev, cudaStream_t st)
+{
+    set_active_kernel<<<grid_for(s > 0 ? s : 1, kStepThreads, 1216), kStepThreads, 0, st>>>(src, dst, s, s_dev);
     return cudaGetLastError();
 }
 
