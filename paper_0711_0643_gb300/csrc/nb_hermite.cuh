@@ -192,6 +192,7 @@ __device__ __forceinline__ double pick4(double v0, double v1, double v2, double 
 // component min(q, 2) of the new a and k. i must be a valid particle even when
 // live is false: the group then computes without storing. Returns status bits;
 // lane 3 of a live group also writes the new key t + dt to *key_out if given.
+// g is load_group(H, i), read by the caller (the overload below reads it).
 // y / 6, y / 24, y / 120 and 3 y 2^s, correctly rounded, on the integer pipe
 // (nb_exact.cuh); the FP64 unit only out of line, outside the exponent window.
 static __device__ __noinline__ double ddiv_slow(double y, double d) { return __ddiv_rn(y, d); }
@@ -230,8 +231,20 @@ __device__ __forceinline__ float2 rn_ds_pack(double x)
 }
 __device__ __forceinline__ double pow2_of(int e) { return dfrom((long long)(1023 + e) << 52); }
 
-__device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
-                                             double eta, double dt_max, double dt_min, long long *key_out = nullptr)
+// The state correct_group reads for particle i (lane q: component min(q, 2)).
+struct GroupState {
+    double ti, dt, x, v, ao, ko;
+};
+__device__ __forceinline__ GroupState load_group(const HState &H, int64_t i)
+{
+    const int q = threadIdx.x & 3;
+    const int64_t o = (q < 3 ? q : 2) * H.np + i;
+    return GroupState{H.t[i], H.dt[i], H.x[o], H.v[o], H.a[o], H.k[o]};
+}
+
+__device__ __forceinline__ int correct_group(const HState &H, int64_t i, const GroupState &g, bool live, double tn,
+                                             double an, double kn, double eta, double dt_max, double dt_min,
+                                             long long *key_out = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int q = lane & 3;
@@ -239,9 +252,8 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
     const int g0 = lane & ~3;
     const unsigned full = 0xffffffffu;
     const int64_t np = H.np;
-    const double ti = H.t[i], dt = H.dt[i];
     const int64_t o = c * np + i;
-    const double x = H.x[o], v = H.v[o], ao = H.a[o], ko = H.k[o];
+    const double ti = g.ti, dt = g.dt, x = g.x, v = g.v, ao = g.ao, ko = g.ko;
 
     // predictor: ((x + v d) + (a d^2) / 2) + (k d^3) / 6 and (v + a d) + (k d^2) / 2;
     // corrector: a2 = -6 da / dt^2 - (4 k_old + 2 k_new) / dt,
@@ -352,6 +364,11 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool li
         }
     }
     return flags;
+}
+__device__ __forceinline__ int correct_group(const HState &H, int64_t i, bool live, double tn, double an, double kn,
+                                             double eta, double dt_max, double dt_min, long long *key_out = nullptr)
+{
+    return correct_group(H, i, load_group(H, i), live, tn, an, kn, eta, dt_max, dt_min, key_out);
 }
 
 }  // namespace nb

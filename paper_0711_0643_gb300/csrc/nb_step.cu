@@ -468,40 +468,34 @@ __global__ void __launch_bounds__(kCorThreads) correct_kernel(StepArgs A, int ch
     const HState H{A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, A.n_pad};
     const int q = threadIdx.x & 3;
     const int c = q < 3 ? q : 2;
-    {
-        // Launched programmatically after the force kernel (nb_run loop), this
-        // part overlaps its end: the active list, the block time and the state
-        // were written before it, only the new forces (fin) after. The first
-        // particle's state moves into L1; then wait for the force grid.
-        const int64_t ii = (int64_t)blockIdx.x * kCorPer + (threadIdx.x >> 2);
-        if (ii < s) {
-            const int64_t i = A.idx[ii];
-            const int64_t o = c * A.n_pad + i;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.x + o));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.v + o));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.a + o));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(H.k + o));
-            if (q == 3) {
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(H.t + i));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(H.dt + i));
-            }
-        }
-        asm volatile("griddepcontrol.wait;" ::: "memory");   // returns at once without such a dependency
+    // Launched programmatically after the force kernel (nb_run loop), this part
+    // overlaps its end: the active list, the block time and the state were
+    // written before it, only the new forces (fin) after. The first round's
+    // particle and its state are read here; then wait for the force grid.
+    const int64_t base0 = (int64_t)blockIdx.x * kCorPer;
+    int64_t i0 = 0;
+    GroupState g0{};
+    if (base0 < s) {
+        const int64_t ii = base0 + (threadIdx.x >> 2);
+        i0 = A.idx[ii < s ? ii : 0];
+        g0 = load_group(H, i0);
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // returns at once without such a dependency
     int flags = 0;
     long long kmin = 0x7ff0000000000000LL;   // smallest new key of this thread's particles
-    for (int64_t base = (int64_t)blockIdx.x * kCorPer; base < s; base += (int64_t)gridDim.x * kCorPer) {
+    for (int64_t base = base0; base < s; base += (int64_t)gridDim.x * kCorPer) {
         const int64_t ii = base + (threadIdx.x >> 2);
         bool live = ii < s;
         const int64_t iis = live ? ii : 0;
-        const int64_t i = A.idx[iis];
+        const bool first = base == base0;
+        const int64_t i = first ? i0 : A.idx[iis];
         if (live && check_due && dbits(A.tn[i]) != dbits(tn)) {
             live = false;
             flags |= kStState;
         }
         const double an = A.fin[iis * kPartStride + c], kn = A.fin[iis * kPartStride + 3 + c];
         long long key = 0x7ff0000000000000LL;
-        flags |= correct_group(H, i, live, tn, an, kn, A.eta, A.dt_max, A.dt_min, &key);
+        flags |= correct_group(H, i, first ? g0 : load_group(H, i), live, tn, an, kn, A.eta, A.dt_max, A.dt_min, &key);
         kmin = key < kmin ? key : kmin;
     }
     if (lower_form) {
