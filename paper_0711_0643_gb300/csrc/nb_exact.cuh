@@ -127,9 +127,10 @@ __host__ __device__ __forceinline__ bool ds_split_int(double x, unsigned &hi, un
 // and c = RN(1/d). Markstein's theorem (IBM J. Res. Dev. 34, 1990): if c is within
 // half an ulp of 1/d and q within one ulp of y/d, the residual r = y - q d is exact
 // (one fused multiply-add) and RN(q + r c) = RN(y/d). q = RN(y c) is within one ulp
-// for d = 3 and d = 15 (RN(1/d) is off by at most 2^-54 relative, under half an ulp). Scaling by a
-// power of two is exact while the result stays normal, which the exponent window
-// [63, 2023] of y guarantees; outside it the IEEE division is used.
+// for d = 3 (RN(1/3) is off by at most 2^-54 relative, under half an ulp). Scaling
+// by a power of two is exact while the result stays normal, which the exponent
+// window [63, 2023] of y guarantees; outside it the IEEE division is used. (The
+// FP64 predictor's k d^3 / 6; the corrector uses the integer div3_int below.)
 __device__ __forceinline__ double div_const(double y, double d, double c, double scale, double full)
 {
     const int e = dexpo(y);
@@ -141,8 +142,6 @@ __device__ __forceinline__ double div_const(double y, double d, double c, double
     return y / full;
 }
 __device__ __forceinline__ double div6(double y) { return div_const(y, 3.0, 1.0 / 3.0, 0.5, 6.0); }
-__device__ __forceinline__ double div24(double y) { return div_const(y, 3.0, 1.0 / 3.0, 0.125, 24.0); }
-__device__ __forceinline__ double div120(double y) { return div_const(y, 15.0, 1.0 / 15.0, 0.125, 120.0); }
 
 // High 64 bits of the 128-bit product a b.
 __host__ __device__ __forceinline__ unsigned long long umulhi64(unsigned long long a, unsigned long long b)

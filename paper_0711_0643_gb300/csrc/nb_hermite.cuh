@@ -4,8 +4,9 @@
 // Every translation unit that includes this file is compiled with
 // -fmad=false, so each expression rounds operation by operation in the order
 // written -- the same order as the FP64 CPU oracle, giving the same bits.
-// Divisions by the constants 6, 24, 120 and by powers of two are replaced by the
-// exact equivalents of nb_exact.cuh (same bits, a fraction of the FP64 work).
+// Divisions by the constants 6, 24, 120, products with 3, 6, 12 and with powers
+// of two are replaced by the exact equivalents of nb_exact.cuh (same bits, on
+// the integer pipe or with less FP64 work).
 #pragma once
 
 #include <math_constants.h>
@@ -29,17 +30,6 @@ __device__ __forceinline__ double pow2_floor(double x)
     return ldexp(1.0, e - 1);
 }
 
-// The Aarseth step (Eq. timestep) from the squared norms A = |a|^2, K = |k|^2,
-// P = |a2p|^2, Q = |a3|^2 exactly as the oracle evaluates it:
-// sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| + |a2p|^2)); den = 0 sets no limit.
-__device__ __forceinline__ double aarseth_exact(double A, double K, double P, double Q, double eta)
-{
-    const double num = sqrt(A) * sqrt(P) + K;
-    const double den = sqrt(K) * sqrt(Q) + P;
-    if (den == 0.0) return CUDART_INF;
-    return sqrt(eta * num / den);
-}
-
 // Squared norm inside [2^-120, 2^120]: its FP32 copy, square root and the
 // products below stay normal.
 __device__ __forceinline__ bool norm2_in_range(double S)
@@ -54,7 +44,8 @@ __device__ __forceinline__ bool norm2_in_range(double S)
 // dozen correctly rounded FP32 operations). When the estimate's significand is
 // at least 2^-14 away from 1 and from 2, it has the exact step's exponent: qb is
 // that power of two and the function returns true; otherwise false, and the
-// caller evaluates aarseth_exact.
+// caller evaluates the FP64 expression sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| +
+// |a2p|^2)) as the oracle does.
 __device__ __forceinline__ bool aarseth_estimate(float rA, float rK, float rP, float rQ, float fK, float fP,
                                                  float eta_f, long long &qb)
 {
@@ -96,84 +87,6 @@ __device__ __forceinline__ void hermite_predict(const double *x, const double *v
         xp[c] = ((x[q] + v[q] * d) + (a[q] * d2) * 0.5) + div6(k[q] * d3);
         vp[c] = (v[q] + a[q] * d) + (k[q] * d2) * 0.5;
     }
-}
-
-// Hermite corrector and the new quantised step of particle i for the block time
-// tn, given the new force an, kn; updates x, v, a, k, t, dt, tn in place and the
-// double-single copies xd, vd, ad, kd when given (NULL: no copies).
-// Returns status bits (non-finite, underflow). dt is a power of two in
-// [2^-300, 2^300], so dividing by dt, dt^2, dt^3 is the same exact scaling as
-// multiplying by their reciprocals.
-__device__ __forceinline__ int hermite_correct(double *x, double *v, double *a, double *k, double *t, double *dtv,
-                                               double *tnv, float2 *xd, float2 *vd, float2 *ad, float2 *kd,
-                                               int64_t np, int64_t i, double tn, const double *an,
-                                               const double *kn, double eta, double dt_max, double dt_min)
-{
-    const double dt = dtv[i];
-    double xp[3], vp[3];
-    hermite_predict(x, v, a, k, t, np, i, tn, xp, vp);
-    const double dt2 = dt * dt;
-    const double dt3 = dt2 * dt;
-    const double dt4 = dt3 * dt;
-    const double dt5 = dt4 * dt;
-    const double idt = recip_pow2(dt);
-    const double idt2 = idt * idt;
-    const double idt3 = idt2 * idt;
-    double x1[3], v1[3], a2[3], a3[3], a2p[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double ao = a[c * np + i], ko = k[c * np + i];
-        const double da = ao - an[c];
-        a2[c] = (-6.0 * da) * idt2 - (4.0 * ko + 2.0 * kn[c]) * idt;
-        a3[c] = (12.0 * da) * idt3 + (6.0 * (ko + kn[c])) * idt2;
-        x1[c] = (xp[c] + div24(a2[c] * dt4)) + div120(a3[c] * dt5);
-        v1[c] = (vp[c] + div6(a2[c] * dt3)) + div24(a3[c] * dt4);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a2p[c] = a2[c] + a3[c] * dt;
-    const double A = dot3(an[0], an[1], an[2], an[0], an[1], an[2]);
-    const double K = dot3(kn[0], kn[1], kn[2], kn[0], kn[1], kn[2]);
-    const double P = dot3(a2p[0], a2p[1], a2p[2], a2p[0], a2p[1], a2p[2]);
-    const double Q = dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]);
-    long long qb = 0;
-    bool pos = true;
-    bool decided = norm2_in_range(A) && norm2_in_range(K) && norm2_in_range(P) && norm2_in_range(Q);
-    if (decided) {
-        const float fK = (float)K, fP = (float)P;
-        decided = aarseth_estimate(sqrtf((float)A), sqrtf(fK), sqrtf(fP), sqrtf((float)Q), fK, fP, (float)eta, qb);
-    }
-    if (!decided) {
-        const double cand = aarseth_exact(A, K, P, Q, eta);
-        qb = pow2_floor_bits(cand);
-        pos = dpositive(cand);
-    }
-    const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) finite = finite && dfinite(x1[c]) && dfinite(v1[c]) && dfinite(an[c]) && dfinite(kn[c]);
-    int flags = 0;
-    if (!finite) flags |= kStNonfinite;
-    if (dt_new == 0.0) flags |= kStUnderflow;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        x[c * np + i] = x1[c];
-        v[c * np + i] = v1[c];
-        a[c * np + i] = an[c];
-        k[c * np + i] = kn[c];
-    }
-    if (xd) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            xd[c * np + i] = ds_pack(x1[c]);
-            vd[c * np + i] = ds_pack(v1[c]);
-            ad[c * np + i] = ds_pack(an[c]);
-            kd[c * np + i] = ds_pack(kn[c]);
-        }
-    }
-    t[i] = tn;
-    dtv[i] = dt_new;
-    tnv[i] = tn + dt_new;
-    return flags;
 }
 
 __device__ __forceinline__ double pick4(double v0, double v1, double v2, double v3, int w)
