@@ -303,8 +303,11 @@ def main_gpu(args):
     bsteps = st["block_steps"]
     dE = abs(E1 - E0) / abs(E0)
     # kernels per step: layout (2) + pad, predict, iota, force, init_steps (5) + energy 2 x 2
-    # + first select (1) + 4 per block step (predict, force, correct, select)
-    launches = 2 + 5 + 4 + 1 + 4 * bsteps
+    # + the run loop's first selection (1) + 4 per loop step (selection, predictor, force,
+    # corrector); the loop runs whole passes of 16 steps, the one that finds no block due
+    # and those after it in its pass as no-ops
+    loop_steps = (bsteps // 16 + 1) * 16
+    launches = 2 + 5 + 4 + 1 + 4 * loop_steps
 
     # ---- roofline of the dominant kernel (force), same trajectory, events around each launch
     nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
