@@ -218,29 +218,42 @@ __host__ __device__ __forceinline__ bool mul3_int(double y, int s, double &out)
 
 // 1/p for a power of two p whose reciprocal is normal (biased exponent of p in
 // [1, 2045]): the exponent field reflected about the bias, no FP64 instruction.
-__device__ __forceinline__ double recip_pow2(double p) { return dfrom((0x7FEll << 52) - dbits(p)); }
+__host__ __device__ __forceinline__ double recip_pow2(double p) { return dfrom((0x7FEll << 52) - dbits(p)); }
 
 // Bits of the largest power of two <= cand for cand > 0 finite and normal,
 // +inf for +inf, 0 for subnormal cand (frexp/ldexp's answer is then below any
 // normal step bound, which is all the quantisation rule looks at).
-__device__ __forceinline__ long long pow2_floor_bits(double cand) { return dbits(cand) & (long long)0xFFF0000000000000ull; }
+__host__ __device__ __forceinline__ long long pow2_floor_bits(double cand)
+{
+    return dbits(cand) & (long long)0xFFF0000000000000ull;
+}
 
 // cand > 0 (false for NaN, zeros and negatives), on the integer pipe.
-__device__ __forceinline__ bool dpositive(double cand)
+__host__ __device__ __forceinline__ bool dpositive(double cand)
 {
     const long long b = dbits(cand);
     return b > 0 && b <= 0x7FF0000000000000ll;
 }
 
+// 1 + index of the lowest set bit of m (0 for m = 0).
+__host__ __device__ __forceinline__ int ffs64(long long m)
+{
+#ifdef __CUDA_ARCH__
+    return __ffsll(m);
+#else
+    return __builtin_ffsll(m);
+#endif
+}
+
 // Is t an integer multiple of the power of two p (p normal)? Equal to
 // u = t / p; u == floor(u) in IEEE arithmetic for finite t.
-__device__ __forceinline__ bool multiple_of_pow2(double t, double p)
+__host__ __device__ __forceinline__ bool multiple_of_pow2(double t, double p)
 {
     const long long tb = dbits(t) & 0x7FFFFFFFFFFFFFFFll;
     if (tb == 0) return true;
     const int et = (int)(tb >> 52);
     const long long m = (tb & ((1ll << 52) - 1)) | (et ? (1ll << 52) : 0ll);
-    const int low = (et ? et : 1) - 1075 + (__ffsll(m) - 1);   // exponent of t's lowest set bit
+    const int low = (et ? et : 1) - 1075 + (ffs64(m) - 1);   // exponent of t's lowest set bit
     return low >= (int)(dbits(p) >> 52) - 1023;
 }
 
@@ -249,8 +262,8 @@ __device__ __forceinline__ bool multiple_of_pow2(double t, double p)
 // when q < dt_old, double (once) when q >= 2 dt_old, 2 dt_old <= dt_max and
 // t_new is a multiple of 2 dt_old, else keep; clamp to dt_max; 0 below dt_min.
 // qb = pow2_floor_bits(cand); pos = dpositive(cand). dt_old in [2^-300, 2^300].
-__device__ __forceinline__ double quantise_bits(long long qb, bool pos, double dt_old, double t_new, double dt_max,
-                                                double dt_min)
+__host__ __device__ __forceinline__ double quantise_bits(long long qb, bool pos, double dt_old, double t_new,
+                                                         double dt_max, double dt_min)
 {
     if (!pos) return 0.0;
     const long long dto = dbits(dt_old), dt2 = dto + (1ll << 52), dmax = dbits(dt_max), dmin = dbits(dt_min);

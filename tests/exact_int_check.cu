@@ -1,11 +1,17 @@
 // Host check of the integer-pipe exact helpers of nb_exact.cuh against the host's
-// IEEE double arithmetic (correctly rounded by IEEE 754): div3_int, div15_int and
+// IEEE arithmetic (correctly rounded by IEEE 754): div3_int, div15_int and
 // mul3_int must return the bits of y / 6, y / 24, y / 120 and 3 y 2^s wherever they
-// accept y. Random and edge significands over the whole accepted exponent window.
-// Usage: exact_int_check [cases]; exits non-zero on the first mismatch.
+// accept y, and ds_split_int the bits of (float)x and (float)(x - hi). Random and
+// edge significands over the whole accepted exponent windows.
+// Usage: exact_int_check [cases]; exits non-zero on a mismatch.
+//        exact_int_check quantise < records: for each record of five doubles
+//        (candidate, dt_old, t_new, dt_max, dt_min) on standard input (after an
+//        int64 count) writes the bit-pattern quantiser's step as a double.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <string>
 
 #include "nb_exact.cuh"
 
@@ -31,8 +37,22 @@ static void check(const char *what, double y, bool ok, double got, double ref)
     }
 }
 
+static int quantise_mode()
+{
+    long long n = 0;
+    if (std::fread(&n, 8, 1, stdin) != 1 || n < 0) return 2;
+    for (long long q = 0; q < n; ++q) {
+        double r[5];
+        if (std::fread(r, 8, 5, stdin) != 5) return 2;
+        const double dt = quantise_bits(pow2_floor_bits(r[0]), dpositive(r[0]), r[1], r[2], r[3], r[4]);
+        if (std::fwrite(&dt, 8, 1, stdout) != 1) return 2;
+    }
+    return 0;
+}
+
 int main(int argc, char **argv)
 {
+    if (argc > 1 && std::string(argv[1]) == "quantise") return quantise_mode();
     const long long cases = argc > 1 ? std::atoll(argv[1]) : 4000000;
     const unsigned long long edges[] = {0ull, 1ull, 2ull, (1ull << 52) - 1, (1ull << 52) - 2, (1ull << 51),
                                         (1ull << 51) - 1, (1ull << 51) + 1, (1ull << 50), (1ull << 49),
@@ -63,6 +83,18 @@ int main(int argc, char **argv)
         for (int s = 0; s <= 3; ++s) {
             ok = mul3_int(y, s, out);
             check("3y*2^s", y, ok, out, (3.0 * y) * std::ldexp(1.0, s));
+        }
+        unsigned hi, lo;
+        if (ds_split_int(y, hi, lo)) {
+            const float h = (float)y;
+            const float l = (float)(y - (double)h);
+            unsigned hb, lb;
+            std::memcpy(&hb, &h, 4);
+            std::memcpy(&lb, &l, 4);
+            if (hi != hb || lo != lb) {
+                if (fails < 10) std::printf("MISMATCH ds_split y=%a hi %08x/%08x lo %08x/%08x\n", y, hi, hb, lo, lb);
+                ++fails;
+            }
         }
     }
     std::printf("cases %lld (div3 accepted %lld, declined %lld), mismatches %d\n", cases, accepted, declined, fails);

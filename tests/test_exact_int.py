@@ -2,9 +2,11 @@
 
 The corrector replaces the FP64 divisions by 6, 24 and 120 and the products with
 3, 6 and 12 by integer code that must give the bits of the IEEE operation
-(Granlund-Montgomery division by an invariant integer, round to nearest). The
-same header compiled for the host is checked here against the host's IEEE
-double arithmetic on random and edge significands over every exponent."""
+(Granlund-Montgomery division by an invariant integer, round to nearest), splits
+doubles into double-single pairs on the integer pipe, and quantises steps on bit
+patterns. The same header compiled for the host is checked here against the
+host's IEEE arithmetic on random and edge values over every exponent, and the
+quantiser against the oracle's."""
 import os
 import shutil
 import subprocess
@@ -15,15 +17,51 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_integer_division_and_product_match_ieee():
+def _build(d):
     nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
     if nvcc is None:
         pytest.skip("nvcc not found")
+    exe = os.path.join(d, "exact_int_check")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_0711_0643_gb300", "csrc"),
+                    "-o", exe, os.path.join(ROOT, "tests", "exact_int_check.cu")], check=True)
+    return exe
+
+
+def test_integer_division_product_and_split_match_ieee():
     with tempfile.TemporaryDirectory() as d:
-        exe = os.path.join(d, "exact_int_check")
-        subprocess.run([nvcc, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"),
-                        "-I", os.path.join(ROOT, "paper_0711_0643_gb300", "csrc"),
-                        "-o", exe, os.path.join(ROOT, "tests", "exact_int_check.cu")], check=True)
+        exe = _build(d)
         out = subprocess.run([exe, "8000000"], capture_output=True, text=True)
         assert out.returncode == 0, out.stdout + out.stderr
         assert "mismatches 0" in out.stdout
+
+
+def test_bit_pattern_quantiser_matches_oracle(orc):
+    """The corrector's quantiser works on bit patterns (largest power of two below the
+    candidate from the exponent field, the doubling test from the lowest set bit of
+    t_new); it must give the oracle's step (frexp-based, Sect. 2.1 powers of two) for
+    every candidate, including zero, negative, subnormal, infinite and NaN ones."""
+    import numpy as np
+    rng = np.random.default_rng(20071106)
+    rows = []
+    specials = [0.0, -0.0, -1.0, np.inf, np.nan, 5e-324, 2.0 ** -1030, 2.0 ** -1022, 1.0, 2.0 ** -40, 2.0 ** -41]
+    for q in range(20000):
+        lvl = int(rng.integers(4, 41))            # dt_old = 2^-lvl in [2^-40, 2^-4]
+        dt_old = 2.0 ** -lvl
+        t_new = float(rng.integers(0, 2 ** min(lvl, 30))) * dt_old
+        if q % 5 == 0:
+            cand = specials[int(rng.integers(0, len(specials)))]
+        elif q % 5 == 1:
+            cand = dt_old * float(rng.choice([0.5, 1.0, 2.0, 4.0, 0.999999, 1.000001, 2.000001, 1.999999]))
+        else:
+            cand = float(2.0 ** rng.uniform(-60, 4))
+        rows.append((cand, dt_old, t_new, 1.0 / 16, 2.0 ** -40))
+    with tempfile.TemporaryDirectory() as d:
+        exe = _build(d)
+        payload = np.array([len(rows)], dtype=np.int64).tobytes() + np.array(rows, dtype=np.float64).tobytes()
+        out = subprocess.run([exe, "quantise"], input=payload, capture_output=True, check=True)
+    got = np.frombuffer(out.stdout, dtype=np.float64)
+    assert got.size == len(rows)
+    for (cand, dt_old, t_new, dt_max, dt_min), g in zip(rows, got):
+        ref = orc.quantise(cand, dt_old, t_new, dt_max, dt_min)
+        assert np.float64(g).tobytes() == np.float64(ref).tobytes(), (cand, dt_old, t_new, g, ref)
