@@ -43,6 +43,16 @@ __host__ __device__ __forceinline__ float ffrom(unsigned u)
     return x;
 #endif
 }
+__host__ __device__ __forceinline__ int fbits(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_int(x);
+#else
+    int b;
+    std::memcpy(&b, &x, 4);
+    return b;
+#endif
+}
 __host__ __device__ __forceinline__ int clz32(unsigned u)
 {
 #ifdef __CUDA_ARCH__

@@ -32,7 +32,7 @@ __device__ __forceinline__ double pow2_floor(double x)
 
 // Squared norm inside [2^-120, 2^120]: its FP32 copy, square root and the
 // products below stay normal.
-__device__ __forceinline__ bool norm2_in_range(double S)
+__host__ __device__ __forceinline__ bool norm2_in_range(double S)
 {
     const int e = dexpo(S);
     return e >= 1023 - 120 && e <= 1023 + 120;
@@ -46,15 +46,15 @@ __device__ __forceinline__ bool norm2_in_range(double S)
 // that power of two and the function returns true; otherwise false, and the
 // caller evaluates the FP64 expression sqrt(eta (|a||a2p| + |k|^2) / (|k||a3| +
 // |a2p|^2)) as the oracle does.
-__device__ __forceinline__ bool aarseth_estimate(float rA, float rK, float rP, float rQ, float fK, float fP,
-                                                 float eta_f, long long &qb)
+__host__ __device__ __forceinline__ bool aarseth_estimate(float rA, float rK, float rP, float rQ, float fK,
+                                                          float fP, float eta_f, long long &qb)
 {
     const float num = rA * rP + fK;
     const float den = rK * rQ + fP;
     const float ratio = (eta_f * num) / den;
-    const int re = (__float_as_int(ratio) >> 23) & 0xff;
+    const int re = (fbits(ratio) >> 23) & 0xff;
     const float c32 = sqrtf(ratio);
-    const int cb = __float_as_int(c32);
+    const int cb = fbits(c32);
     const int cm = cb & 0x7fffff;
     qb = (long long)(((cb >> 23) & 0xff) - 127 + 1023) << 52;
     return re >= 127 - 120 && re <= 127 + 120 && cm >= (1 << 9) && cm <= 0x7fffff - (1 << 10);

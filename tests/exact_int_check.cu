@@ -7,6 +7,10 @@
 //        exact_int_check quantise < records: for each record of five doubles
 //        (candidate, dt_old, t_new, dt_max, dt_min) on standard input (after an
 //        int64 count) writes the bit-pattern quantiser's step as a double.
+//        exact_int_check aarseth < records: for each record (A, K, P, Q, eta) of
+//        FP64 squared norms writes (decided, bits of the power of two) as the
+//        corrector derives them: FP32 copies, their square roots, the FP32
+//        estimate and its window.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -14,6 +18,7 @@
 #include <string>
 
 #include "nb_exact.cuh"
+#include "nb_hermite.cuh"
 
 using namespace nb;
 
@@ -50,9 +55,30 @@ static int quantise_mode()
     return 0;
 }
 
+static int aarseth_mode()
+{
+    long long n = 0;
+    if (std::fread(&n, 8, 1, stdin) != 1 || n < 0) return 2;
+    for (long long q = 0; q < n; ++q) {
+        double r[5];
+        if (std::fread(r, 8, 5, stdin) != 5) return 2;
+        long long qb = 0;
+        bool decided = norm2_in_range(r[0]) && norm2_in_range(r[1]) && norm2_in_range(r[2]) && norm2_in_range(r[3]);
+        if (decided) {
+            const float fA = (float)r[0], fK = (float)r[1], fP = (float)r[2], fQ = (float)r[3];
+            decided = aarseth_estimate(std::sqrt(fA), std::sqrt(fK), std::sqrt(fP), std::sqrt(fQ), fK, fP,
+                                       (float)r[4], qb);
+        }
+        const double out[2] = {decided ? 1.0 : 0.0, dfrom(qb)};
+        if (std::fwrite(out, 8, 2, stdout) != 2) return 2;
+    }
+    return 0;
+}
+
 int main(int argc, char **argv)
 {
     if (argc > 1 && std::string(argv[1]) == "quantise") return quantise_mode();
+    if (argc > 1 && std::string(argv[1]) == "aarseth") return aarseth_mode();
     const long long cases = argc > 1 ? std::atoll(argv[1]) : 4000000;
     const unsigned long long edges[] = {0ull, 1ull, 2ull, (1ull << 52) - 1, (1ull << 52) - 2, (1ull << 51),
                                         (1ull << 51) - 1, (1ull << 51) + 1, (1ull << 50), (1ull << 49),

@@ -65,3 +65,52 @@ def test_bit_pattern_quantiser_matches_oracle(orc):
     for (cand, dt_old, t_new, dt_max, dt_min), g in zip(rows, got):
         ref = orc.quantise(cand, dt_old, t_new, dt_max, dt_min)
         assert np.float64(g).tobytes() == np.float64(ref).tobytes(), (cand, dt_old, t_new, g, ref)
+
+
+def test_fp32_aarseth_estimate_decides_like_the_fp64_step(orc):
+    """The corrector takes the new step's power of two from an FP32 estimate of the
+    Aarseth step (Eq. timestep) when the estimate is at least 2^-14 (relative) away
+    from a power of two, and from the FP64 expression otherwise. Wherever it decides,
+    its power of two must be the one below the oracle's FP64 step, also for steps
+    placed within 10^-4 or 10^-6 of a power of two (without the window, FP32 rounding
+    puts some of those on the wrong side: 54 of 4000 at 10^-6)."""
+    import math
+
+    import numpy as np
+    rng = np.random.default_rng(20071107)
+
+    def vec(scale):
+        u = rng.normal(size=3)
+        return u / np.linalg.norm(u) * scale
+
+    def n2(u):
+        return (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]   # the oracle's dot3 order
+
+    cases = []
+    for q in range(20000):
+        a, k, a2p, a3 = (vec(10.0 ** rng.uniform(-6, 6)) for _ in range(4))
+        eta = 0.01
+        if q % 2:   # move the step to within 1e-4 (or 1e-6) of a power of two through eta
+            c0 = orc.aarseth_dt(a, k, a2p, a3, eta)
+            spread = 1e-4 if q % 4 == 1 else 1e-6
+            target = 2.0 ** round(math.log2(c0)) * (1.0 + rng.uniform(-spread, spread))
+            eta = eta * (target / c0) ** 2
+        cases.append((a, k, a2p, a3, eta))
+    rows = np.array([(n2(a), n2(k), n2(a2p), n2(a3), eta) for a, k, a2p, a3, eta in cases], dtype=np.float64)
+    with tempfile.TemporaryDirectory() as d:
+        exe = _build(d)
+        payload = np.array([len(rows)], dtype=np.int64).tobytes() + rows.tobytes()
+        out = subprocess.run([exe, "aarseth"], input=payload, capture_output=True, check=True)
+    res = np.frombuffer(out.stdout, dtype=np.float64).reshape(-1, 2)
+    decided = [0, 0]   # random steps, steps near a power of two
+    for q, ((a, k, a2p, a3, eta), (dec, qb)) in enumerate(zip(cases, res)):
+        if dec == 0.0:
+            continue
+        decided[q % 2] += 1
+        cand = orc.aarseth_dt(a, k, a2p, a3, eta)
+        m, e = math.frexp(cand)
+        assert qb == math.ldexp(0.5, e), (cand, qb)
+    # away from powers of two the estimate decides almost always (the window is
+    # 2^-14 above and 2^-13 below a power of two); near them it must also decide
+    # some (the exact path is not taken for all of them)
+    assert decided[0] > 0.99 * len(cases) / 2 and decided[1] > 0.05 * len(cases) / 2, decided
