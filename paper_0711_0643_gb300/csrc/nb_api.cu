@@ -2,11 +2,12 @@
 // kernel tuner. See include/nbody.h for the contract of every entry point.
 //
 // Engine: nb_run builds (once per context) a CUDA graph
-//     select -> WHILE( predict -> force -> correct -> select )
-// where select sets the while-node condition on the device (next block time
-// <= t_end, no error). One graph launch integrates to t_end with no host
-// round trip per block step; the force kernel sizes its work from the active
-// count it reads on the device.
+//     select -> WHILE( 16 x ( [select at the known time || predict] -> force -> correct ) )
+// where each selection sets the while-node condition on the device (this block
+// is due by t_end, no error) and the corrector forms the next block time while
+// it corrects (see build_run_graph). One graph launch integrates to t_end with
+// no host round trip per block step; the force kernel sizes its work from the
+// active count it reads on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
