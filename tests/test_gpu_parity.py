@@ -402,6 +402,34 @@ def test_run_step_and_timed_paths_agree(nb):
     assert sum(hist) == states[0][1]["block_steps"] and hist[0] >= 0
 
 
+def test_run_loop_multi_chunk_selection_matches_host_steps(nb):
+    """At N = 262144 the run loop's selection at a known block time gives every CTA
+    of its cluster several 8192-key chunks (ballots recomputed chunk by chunk); a
+    short nb_run must end bitwise where host-driven nb_step does."""
+    snap = ics.plummer(262144, seed=21, eps=1.0 / 1024)
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        t1, _ = nb.nb_next_block(c.ctx)
+    t_end = 8 * t1
+    states = []
+    for mode in ("run", "step"):
+        with nb.Context(precision=0) as c:
+            c.init(snap)
+            if mode == "run":
+                nb.nb_run(c.ctx, t_end)
+            else:
+                while True:
+                    tn, _ = nb.nb_next_block(c.ctx)
+                    if tn > t_end:
+                        break
+                    nb.nb_step(c.ctx)
+            states.append((c.state(), nb.nb_stats(c.ctx)))
+    (st_run, cnt_run), (st_step, cnt_step) = states
+    assert cnt_run["block_steps"] == cnt_step["block_steps"] > 0
+    for key in ("x", "v", "a", "k", "t", "dt"):
+        np.testing.assert_array_equal(st_run[key], st_step[key])
+
+
 def test_deterministic_and_resume_bitwise(nb):
     """Two runs agree bitwise; a run checkpointed at t = 1/16 and resumed in a new context
     ends bitwise equal to an uninterrupted run."""
