@@ -234,7 +234,9 @@ const char *nb_variant_name(const nb_ctx *ctx, int32_t variant);
  * (a larger n returns NB_ERR_ARG); the j-split factor is lowered as needed so
  * that the split partials (s x split entries) fit in 2^16 slots.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make this first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make this
+ * first call before any stream capture. A cudaDeviceReset between calls is not
+ * supported (the kept address would be stale).
  * Every call reuses the same array and leaves its contents behind, so calls
  * that overlap on the GPU (other streams, other host threads) race: serialise
  * them. The call returns after the outputs are written (it synchronises the

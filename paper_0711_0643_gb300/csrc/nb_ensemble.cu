@@ -2,8 +2,10 @@
 // schedule (Sect. 2.1 applied to every member), advanced in one persistent
 // launch.
 //
-// Design: the kernel is launched with thread-block clusters of C CTAs (16 where
-// the device allows it, else 8) and one cluster per slot of the GPU. A cluster
+// Design: the kernel is launched with thread-block clusters of C CTAs (the
+// largest of 16, 8 and 4 whose co-resident clusters keep at least 90 % of the
+// kernel's CTA slots busy; see ensemble_shape) and one cluster per slot of the
+// GPU. A cluster
 // takes a whole system from an atomic queue (largest first: the host orders
 // the members by N^2) and runs that system's integration to t_end on its own:
 // selection, prediction, force, correction, repeated, with the cluster's CTAs
@@ -95,7 +97,8 @@ __device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_
         const float4 h = E.jh[base + j], l = E.jl[base + j], w = E.jv[base + j];
         jrec_store(sm->tile, q, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
     } else {
-        jrec_store(sm->tile, q, 1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        const float far = (float)kPadPos;
+        jrec_store(sm->tile, q, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     }
 }
 

@@ -15,6 +15,7 @@ constexpr int kJT = 256;             // j-records per shared-memory tile
 constexpr int kStages = 3;           // tiles in flight per CTA
 constexpr int kBuckets = 32;         // active-set size buckets (bucket b: s in (2^(b-1), 2^b])
 constexpr int kPartStride = 8;       // doubles per (i, split) partial: ax ay az kx ky kz phi pad
+constexpr double kPadPos = 1e18;     // position of the far-away, massless records padding j to whole tiles
 
 // device status bits (accumulated with atomicOr, read at sync points)
 constexpr int kStNonfinite = 1;

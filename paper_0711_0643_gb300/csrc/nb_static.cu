@@ -15,6 +15,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "nb_ds.cuh"
 #include "nb_internal.cuh"
 #include "nb_pair.cuh"
 
@@ -53,12 +54,12 @@ __global__ void static_setup_kernel(const double *m, const double *x, const doub
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride) {
         if (i < n) {
-            const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
-            const float hx = (float)px, hy = (float)py, hz = (float)pz;
-            jrec_store(rec, i, hx, hy, hz, (float)m[i], (float)(px - (double)hx), (float)(py - (double)hy),
-                       (float)(pz - (double)hz), (float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2]);
+            const DS px = ds_split(x[3 * i]), py = ds_split(x[3 * i + 1]), pz = ds_split(x[3 * i + 2]);
+            jrec_store(rec, i, px.hi, py.hi, pz.hi, (float)m[i], px.lo, py.lo, pz.lo, (float)v[3 * i],
+                       (float)v[3 * i + 1], (float)v[3 * i + 2]);
         } else {
-            jrec_store(rec, i, 1e18f, 1e18f, 1e18f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+            const float far = (float)kPadPos;
+            jrec_store(rec, i, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
         }
         tickets[i] = 0;
     }
@@ -135,9 +136,11 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     F.inject = 0;
     if (launch_force_mixed(F, num_sms * occ, st) != cudaSuccess) return NB_ERR_CUDA;
     if (launch_reduce_out(F.fin, F.s, s, a_dev, k_dev, phi_dev, F.status, st) != cudaSuccess) return NB_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return NB_ERR_CUDA;
+    // the status word is read in stream order (no wait on other streams' work)
     int32_t status = 0;
-    if (cudaMemcpy(&status, F.status, sizeof status, cudaMemcpyDeviceToHost) != cudaSuccess) return NB_ERR_CUDA;
+    if (cudaMemcpyAsync(&status, F.status, sizeof status, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return NB_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NB_ERR_CUDA;
     if (status & kStTimeout) return NB_ERR_TIMEOUT;
     if (status & kStNonfinite) return NB_ERR_NONFINITE;
     return status ? NB_ERR_CUDA : NB_OK;

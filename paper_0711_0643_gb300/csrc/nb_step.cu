@@ -33,9 +33,6 @@ __device__ __forceinline__ void predict_one(const StepArgs &A, int64_t i, double
     hermite_predict(A.x, A.v, A.a, A.k, A.t, A.n_pad, i, tn, xp, vp);
 }
 
-// The far-away, massless record used to pad the j arrays to whole tiles.
-constexpr double kPadPos = 1e18;
-
 __global__ void predict_kernel(StepArgs A, const double *t_dev, double t_host, int skip_past)
 {
     const double tn = t_dev ? *t_dev : t_host;

@@ -5,12 +5,16 @@ per-particle relative error of a, k and phi within 1e-12. Mixed path: phi within
 1e-6 relative; a and the jerk within 1e-6 of their condition scales
 A_i = sum_j |a term|, K_i = sum_j |jerk term| (any FP32 pair arithmetic has an
 error of a few u times that scale; for sums that cancel heavily, the forward
-error grows with the condition number A_i/|a_i|), and the forward relative
-error of a within 1e-6 at the 99th percentile. Forward statistics are printed.
+error grows with the condition numbers kappa_a = A_i/|a_i|, kappa_k = K_i/|k_i|);
+the forward relative errors of a and of k within 1e-6 wherever the condition
+number is at most 16, and that of a within 1e-6 at the 99th percentile.
+Forward statistics are printed.
 Predictor, corrector, time steps and block selection: bit-exact against the
-oracle given the same inputs. Integration: the FP64 path reproduces the
-oracle's block schedule for the first 16 steps; both paths keep |dE/E| at
-t = 1 within 2x the oracle's.
+oracle given the same inputs (the mixed predictor within its derived FP32
+bounds). Integration: the FP64 path reproduces the oracle's block schedule for
+the first 16 steps; both paths keep |dE/E| at t = 1 within 2x the oracle's.
+The mixed path's schedule over the first 16 steps is tested in
+tests/test_gpu_schedule.py.
 """
 import math
 import zlib
@@ -24,6 +28,7 @@ from tests.nbtools import condition_scales, rel_errors, rel_scalar, stats
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-6, 1: 1e-12}   # precision -> relative force/jerk tolerance
+KAPPA_MAX = 16.0             # mixed path: forward bounds where kappa_a, kappa_k <= this
 
 
 @pytest.fixture(scope="module")
@@ -42,8 +47,9 @@ def _cond_scaled(x, xr, scale):
 
 
 def _errors(prec, a, k, phi, ar, kr, pr, A, K):
-    """(e_a, e_k, e_phi, forward e_a, forward e_k): e_* are what the tolerance applies to
-    (forward for FP64, condition-scaled for the mixed path)."""
+    """Error set of one comparison: e_a, e_k, e_phi (what the tolerance applies to:
+    forward for FP64, condition-scaled for the mixed path), the forward e_a and e_k,
+    and the condition numbers kappa_a = A_i/|a_i|, kappa_k = K_i/|k_i|."""
     ea_fwd = rel_errors(a, ar, A)
     ek_fwd = rel_errors(k, kr, K)
     if prec == 1:
@@ -51,14 +57,21 @@ def _errors(prec, a, k, phi, ar, kr, pr, A, K):
     else:
         ea, ek = _cond_scaled(a, ar, A), _cond_scaled(k, kr, K)
     ep = rel_scalar(phi, pr)
-    return ea, ek, ep, ea_fwd, ek_fwd
+    with np.errstate(divide="ignore"):
+        kap_a = A / np.linalg.norm(ar, axis=1)
+        kap_k = K / np.linalg.norm(kr, axis=1)
+    return {"ea": ea, "ek": ek, "ep": ep, "eaf": ea_fwd, "ekf": ek_fwd, "kap_a": kap_a, "kap_k": kap_k}
 
 
-def _check(prec, ea, ek, ep, eaf, where):
+def _check(prec, e, where):
     tol = TOL[prec]
+    ea, ek, ep = e["ea"], e["ek"], e["ep"]
     assert ea.max() < tol and ek.max() < tol and ep.max() < tol, (where, stats(ea), stats(ek), stats(ep))
     if prec == 0:
-        assert np.percentile(eaf, 99) < tol, (where, stats(eaf))
+        assert np.percentile(e["eaf"], 99) < tol, (where, stats(e["eaf"]))
+        well_a, well_k = e["kap_a"] <= KAPPA_MAX, e["kap_k"] <= KAPPA_MAX
+        assert np.all(e["eaf"][well_a] < tol), (where, "a forward, kappa <= 16", e["eaf"][well_a].max())
+        assert np.all(e["ekf"][well_k] < tol), (where, "k forward, kappa <= 16", e["ekf"][well_k].max())
 
 
 def _forces_vs_oracle(nb, orc, c, snap, idx, prec):
@@ -67,7 +80,7 @@ def _forces_vs_oracle(nb, orc, c, snap, idx, prec):
     a, k, phi = nb.nb_force_jerk(c.ctx, idx)
     ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, idx, nthreads=orc.default_threads())
     A, K = condition_scales(snap.m, xp, vp, snap.eps2, idx)
-    return _errors(prec, a, k, phi, ar, kr, pr, A, K)[:4]
+    return _errors(prec, a, k, phi, ar, kr, pr, A, K)
 
 
 SIZES = [(1, 0.01), (2, 0.0), (7, 0.05), (300, 0.01), (1000, 1.0 / 64), (2049, 1.0 / 256)]
@@ -88,8 +101,8 @@ def test_force_all_variants(nb, orc, prec, n, eps):
                     nb.nb_set_tuning(c.ctx, b, v, split)
                 for sub in subsets:
                     idx = np.unique(sub).astype(np.int32)
-                    ea, ek, ep, eaf = _forces_vs_oracle(nb, orc, c, snap, idx, prec)
-                    _check(prec, ea, ek, ep, eaf, (nb.nb_variant_name(c.ctx, v), split, idx.size))
+                    e = _forces_vs_oracle(nb, orc, c, snap, idx, prec)
+                    _check(prec, e, (nb.nb_variant_name(c.ctx, v), split, idx.size))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -109,16 +122,23 @@ def test_force_plummer_16k_all_blocks(nb, orc, prec):
             pos = np.searchsorted(idx, sample)
             ar, kr, pr = orc.force(snap.m, xp, vp, snap.eps2, sample, nthreads=orc.default_threads())
             A, K = condition_scales(snap.m, xp, vp, snap.eps2, sample)
-            ea, ek, ep, eaf, ekf = _errors(prec, a[pos], k[pos], phi[pos], ar, kr, pr, A, K)
-            print(f"prec {prec} s {s}: a {stats(ea)} k {stats(ek)} a(forward) {stats(eaf)} "
-                  f"k(forward) {stats(ekf)} phi {stats(ep)}")
-            _check(prec, ea, ek, ep, eaf, s)
+            e = _errors(prec, a[pos], k[pos], phi[pos], ar, kr, pr, A, K)
+            print(f"prec {prec} s {s}: a {stats(e['ea'])} k {stats(e['ek'])} a(forward) {stats(e['eaf'])} "
+                  f"k(forward) {stats(e['ekf'])} phi {stats(e['ep'])}")
+            _check(prec, e, s)
 
 
 def test_predictor_bit_exact(nb, orc):
-    """FP64 predicted records equal the oracle's predictor bit for bit; the mixed records
-    (a double-single Horner evaluation, split into hi + lo) agree with it to 2^-45 of each
-    particle's |x| and to FP32 rounding in v."""
+    """FP64 predicted records equal the oracle's predictor bit for bit. The mixed records:
+    positions (a double-single Horner evaluation, split into hi + lo) within 2^-45 of each
+    particle's |x|; velocities, stored in FP32, within the bound of the FP32 expression
+    that forms them, per component c (u = 2^-24, d = t - t_j):
+        |v_gpu - v_ref| <= 2u |v_ref| + 4u |d| |a| + 4u d^2 |k| + 2^-46 |v|
+    -- the last two roundings (adding the increment to the high part of v, then the low
+    part) cost u |v_ref| each; the increment d (a + d k / 2) carries the FP32 rounding of
+    d, a and k and three rounded operations (at most 6u of each term); the double-single
+    v itself is exact to ~2^-48. A single rounding to FP32 already costs up to u |v_ref|, so
+    no FP32 record can meet a 2^-24 bound per component."""
     snap = ics.config(1)
     for prec in (1, 0):
         with nb.Context(precision=prec) as c:
@@ -135,9 +155,14 @@ def test_predictor_bit_exact(nb, orc):
                 np.testing.assert_array_equal(vp, vr)
             else:
                 ex = np.linalg.norm(xp - xr, axis=1) / np.linalg.norm(xr, axis=1)
-                ev = np.linalg.norm(vp - vr, axis=1) / np.linalg.norm(vr, axis=1)
                 assert ex.max() < 2.0 ** -45, ex.max()
-                assert ev.max() < 2.0 ** -22, ev.max()
+                u = 2.0 ** -24
+                d = np.abs(t_new - st["t"])[:, None]
+                bound = (2 * u * np.abs(vr) + 4 * u * d * np.abs(st["a"]) + 4 * u * d * d * np.abs(st["k"])
+                         + 2.0 ** -46 * np.abs(st["v"]))
+                dv = np.abs(vp - vr)
+                assert np.all(dv <= bound), float((dv / bound).max())
+                print(f"mixed predictor: velocity error / bound, max {(dv / bound).max():.3f}")
 
 
 def test_corrector_and_steps_bit_exact(nb, orc):
@@ -263,66 +288,6 @@ def test_block_schedule_matches_oracle_16k_fp64(nb, orc):
         st, tn, idx = sysr.step()
         want = (tn, idx.size, zlib.crc32(np.ascontiguousarray(idx, dtype=np.int32).tobytes()))
         assert got == want, (k, got, want)
-
-
-def _oracle_step_with_candidates(orc, st, eps2):
-    """One oracle block step on the state dict st (in place), returning the active list and
-    the unquantised Aarseth candidate of each active particle."""
-    tn, idx = orc.next_block(st["t"], st["dt"])
-    xp, vp = orc.predict(st["x"], st["v"], st["a"], st["k"], st["t"], tn)
-    an, kn, _ = orc.force(st["m"], xp, vp, eps2, idx, nthreads=orc.default_threads())
-    cands = np.zeros(idx.size)
-    for q, i in enumerate(idx):
-        dt = st["dt"][i]
-        x1, v1, cand = orc.correct_particle(xp[i], vp[i], st["a"][i], st["k"][i], an[q], kn[q], dt, 0.01)
-        st["x"][i], st["v"][i], st["a"][i], st["k"][i] = x1, v1, an[q], kn[q]
-        st["dt"][i] = orc.quantise(cand, dt, tn)
-        st["t"][i] = tn
-        cands[q] = cand
-    return tn, idx, cands
-
-
-@pytest.mark.parametrize("cfg", [1, 2])
-def test_block_schedule_mixed(nb, orc, cfg):
-    """Mixed path against the oracle in lockstep from the same initial state: identical first
-    steps and block selections while the time steps agree; at the first step where a time
-    step differs, the GPU's choice is exactly the oracle's rule applied to the GPU's own
-    forces (so the divergence comes from FP32 force rounding, which the corrector's finite
-    differences amplify by ~1/(omega dt)^2, not from the block logic). The step index of the
-    first divergence is printed."""
-    snap = ics.config(cfg)
-    ref = {"m": snap.m.copy(), "x": snap.x.copy(), "v": snap.v.copy()}
-    sysr = orc.System(snap.m, snap.x, snap.v, snap.eps2, nthreads=orc.default_threads())
-    ref.update({"a": sysr.a.copy(), "k": sysr.k.copy(), "t": sysr.t.copy(), "dt": sysr.dt.copy()})
-    with nb.Context(precision=0) as c:
-        c.init(snap)
-        g = c.state()
-        np.testing.assert_array_equal(g["dt"], ref["dt"])
-        for k in range(16):
-            before = c.state()
-            tn, s = nb.nb_next_block(c.ctx)
-            idx = nb.nb_get_active(c.ctx, s)
-            nb.nb_predict(c.ctx, tn)
-            a_new, k_new, _ = nb.nb_force_jerk(c.ctx, idx)
-            nb.nb_correct(c.ctx, tn)
-            g = c.state()
-            tr, ir, cands = _oracle_step_with_candidates(orc, ref, snap.eps2)
-            assert tr == tn and np.array_equal(ir, idx), k
-            if np.array_equal(g["dt"], ref["dt"]):
-                continue
-            bad = np.nonzero(g["dt"] != ref["dt"])[0]
-            xr, vr = orc.predict(before["x"], before["v"], before["a"], before["k"], before["t"], tn)
-            for i in bad:
-                q = int(np.searchsorted(idx, i))
-                assert idx[q] == i
-                dt = before["dt"][i]
-                _, _, cand_g = orc.correct_particle(xr[i], vr[i], before["a"][i], before["k"][i],
-                                                     a_new[q], k_new[q], dt, 0.01)
-                assert orc.quantise(cand_g, dt, tn) == g["dt"][i]
-            print(f"config {cfg}: time steps identical through block step {k - 1}; "
-                  f"{bad.size} differ after step {k}")
-            return
-        print(f"config {cfg}: time steps identical for all 16 block steps")
 
 
 def _energy_cases():
@@ -513,7 +478,10 @@ def test_dev_entry_points_match_host(nb):
         np.testing.assert_array_equal(a_d.cpu().numpy(), a_h)
         np.testing.assert_array_equal(k_d.cpu().numpy(), k_h)
         np.testing.assert_array_equal(p_d.cpu().numpy(), p_h)
+        st_dev = c.state()
     with nb.Context() as c:
         c.init(snap)
         st_host = c.state()
-    np.testing.assert_array_equal(st_host["dt"], st_host["dt"])
+    # nb_init (host buffers) and nb_init_dev (device buffers) load the same state
+    for key in ("m", "x", "v", "a", "k", "t", "dt"):
+        np.testing.assert_array_equal(st_dev[key], st_host[key])

@@ -39,17 +39,26 @@ def _with_ctx(nb, torch, snap, dev, idx):
     return out
 
 
-def test_static_entry_matches_context_entry_twice():
+@pytest.mark.parametrize("n", [5000, 65536])
+def test_static_entry_matches_context_entry_twice(n):
+    """n = 5000: the whole system, then about 40 particles. n = NB_STATIC_MAX_N: the whole
+    system (one split: s x 8 words fill the partial area exactly) and 21845 particles (the
+    split factor lowered to what the partial area holds), which also uses the array's top
+    offsets."""
     torch = pytest.importorskip("torch")
     import paper_0711_0643_gb300 as pkg
     pkg.build()
     from paper_0711_0643_gb300 import nbody as nb
     nb.load()
     dev = torch.device("cuda:0")
-    snap = ics.plummer(5000, seed=21, eps=1.0 / 512)
+    snap = ics.plummer(n, seed=21, eps=1.0 / 512)
     rng = ics.SplitMix64(22)
-    idx = [np.arange(snap.n, dtype=np.int32),
-           np.unique(rng.next_u64(40) % snap.n).astype(np.int32)]
+    if n == nb.NB_STATIC_MAX_N:
+        idx = [np.arange(snap.n, dtype=np.int32),
+               np.sort(np.argsort(rng.uniform(n))[:21845]).astype(np.int32)]
+    else:
+        idx = [np.arange(snap.n, dtype=np.int32),
+               np.unique(rng.next_u64(40) % snap.n).astype(np.int32)]
     ref = _with_ctx(nb, torch, snap, dev, idx)
     m = torch.tensor(snap.m, device=dev)
     x = torch.tensor(snap.x, device=dev)
@@ -64,6 +73,9 @@ def test_static_entry_matches_context_entry_twice():
                                      ix.size, a.data_ptr(), k.data_ptr(), p.data_ptr(), stream)
         assert st == nb.NB_OK
         a, k, p = a.cpu().numpy(), k.cpu().numpy(), p.cpu().numpy()
+        if ix.size > 4096:   # compare a seeded sample against the context entry point's sums
+            sel = np.unique(np.linspace(0, ix.size - 1, 4096).astype(np.int64))
+            a, k, p, ar, kr, pr, ix = a[sel], k[sel], p[sel], ar[sel], kr[sel], pr[sel], ix[sel]
         A, K = condition_scales(snap.m, snap.x, snap.v, snap.eps2, ix)
         assert (np.linalg.norm(a - ar, axis=1) / A).max() < 1e-6
         assert np.percentile(rel_errors(a, ar, A), 99) < 1e-6
