@@ -313,7 +313,7 @@ def main_gpu(args):
     nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
     torch.cuda.synchronize(dev)
     clk_rf = ClockSampler(local).start()
-    force_ms, nlaunch, phase_ms = nb.nb_run_timed(c.ctx, T_END, phases=True)
+    force_ms, nlaunch, eng_steps, phase_ms = nb.nb_run_timed(c.ctx, T_END, phases=True)
     clk_rf_s = clk_rf.stop()
     st_rf = nb.nb_stats(c.ctx)
     sm_mhz = clk["sm_mhz"] or clk_rf_s["sm_mhz"] or load_peaks().get("clocks_under_load", {}).get("sm_mhz_median")
@@ -736,7 +736,7 @@ def main_model(args):
         c.init(snap)
         nb.nb_autotune(c.ctx)
         c.init(snap)
-        _, nl, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
+        _, nl, _, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
         st = nb.nb_stats(c.ctx)
         c.init(snap)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)

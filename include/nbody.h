@@ -159,27 +159,51 @@ nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, doub
 nb_status nb_correct(nb_ctx *ctx, double t_block);
 
 /* One block step on the device: select, predict all, force on the block,
- * correct (no host round trip). */
+ * correct (no host round trip); a small block runs inside the small-block
+ * engine (nb_set_engine), as it does in nb_run. */
 nb_status nb_step(nb_ctx *ctx);
 
 /* Block steps until the next block time exceeds t_end (t_end must be a multiple
  * of dt_max for every particle to land on it). One CUDA-graph launch: a full
- * selection, then a while node whose body runs 16 block steps of
- * [selection at the known block time || predictor] -> force -> corrector on
- * the device (the corrector forms the next block time; steps past t_end are
- * no-ops). Same trajectory, bit for bit, as repeated nb_step.
+ * selection, then a while node whose body runs block steps on the device with
+ * no host round trip. In mixed precision, block steps whose block is small
+ * (see nb_set_engine) run inside the small-block engine: one thread-block
+ * cluster doing selection, predictor, force and corrector in one kernel, step
+ * after step, until a block it does not take; every other block step runs as
+ * [selection at the known block time || predictor] -> force -> corrector (the
+ * corrector forms the next block time; steps past t_end are no-ops). Same
+ * trajectory, bit for bit, as repeated nb_step.
  * One call runs at most 2^22 block steps (then NB_ERR_STATE, "block-step cap"). */
 nb_status nb_run(nb_ctx *ctx, double t_end);
 
 /* Same trajectory as nb_run, driven from the host one block step at a time, with
- * CUDA events around every force launch (a short, time-bounded wait kernel
- * precedes the start event so that it is processed only once the launch is
- * queued). *force_ms = summed force-kernel time, *launches = number of force
- * launches. phase_ms: NULL, or 4 doubles receiving the summed times of the
- * select, predict, force and correct kernels, each bracketed the same way (the
- * select that ends the loop is not counted). Every pointer may be NULL. For
- * measurement; slower than nb_run. */
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms);
+ * CUDA events around every force launch and every engine step (a short,
+ * time-bounded wait kernel precedes each start event so that it is processed
+ * only once the launch is queued). *force_ms = summed time of the force kernel
+ * (blocks the engine does not take), *launches = number of those force
+ * launches, *engine_steps = block steps done by the small-block engine.
+ * phase_ms: NULL, or 5 doubles receiving the summed times of the select,
+ * predict, force, correct kernels and of the engine's steps, each bracketed the
+ * same way (the select that ends the loop is not counted). Every pointer may
+ * be NULL. For measurement; slower than nb_run. */
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms,
+                       int64_t *engine_steps);
+
+/* Small-block engine (mixed precision): the largest block s_max (<= 256) that
+ * nb_step / nb_run / nb_run_timed run inside the one-cluster engine kernel
+ * instead of the four-kernel step (a block is also left to the four-kernel
+ * step when more than 64 of its members fall into one CTA's share of the
+ * particles). The paper has the step of Sect. 2.1 only; the engine is the same
+ * step with the j-split of Sect. 3 across the cluster's CTAs and the partial
+ * forces summed in a fixed order. s_max = 0 switches it off, -1 restores the
+ * default (the largest s with s N <= 2^22, at least 16, at most 256). Without a
+ * co-schedulable 16- or 8-CTA cluster, or above 4096 particles per CTA
+ * (n > 65536 on 16-CTA clusters), there is no engine.
+ * Errors: NB_ERR_ARG (s_max out of range, or s_max > 0 in FP64 precision).
+ * nb_get_engine: the largest block the engine takes for the loaded system
+ * (0 = no engine) and its cluster size; either pointer may be NULL. */
+nb_status nb_set_engine(nb_ctx *ctx, int32_t s_max);
+nb_status nb_get_engine(nb_ctx *ctx, int32_t *s_max, int32_t *cluster);
 
 /* Kinetic, potential (softened, W = sum m_i phi_i / 2) and total energy of the
  * current state, on the device: K in FP64; the pair terms of W in double-single

@@ -27,6 +27,7 @@ SOURCES = [
     ("nb_api.cu", []),
     ("nb_ensemble.cu", ["-fmad=false", "-ftz=true"]),
     ("nb_static.cu", ["-ftz=true"]),
+    ("nb_engine.cu", ["-fmad=false", "-ftz=true"]),
 ]
 
 

@@ -2,12 +2,15 @@
 // kernel tuner. See include/nbody.h for the contract of every entry point.
 //
 // Engine: nb_run builds (once per context) a CUDA graph
-//     select -> WHILE( 16 x ( [select at the known time || predict] -> force -> correct ) )
+//     select -> WHILE( U x ( [engine] -> [select at the known time || predict] -> force -> correct ) )
 // where each selection sets the while-node condition on the device (this block
 // is due by t_end, no error) and the corrector forms the next block time while
-// it corrects (see build_run_graph). One graph launch integrates to t_end with
-// no host round trip per block step; the force kernel sizes its work from the
-// active count it reads on the device.
+// it corrects (see build_run_graph). The small-block engine (nb_engine.cu, mixed
+// precision) runs every block step whose block is small inside one cluster
+// launch and stops at the first block it does not take, which the four kernels
+// after it then do. One graph launch integrates to t_end with no host round trip
+// per block step; the force kernel sizes its work from the active count it reads
+// on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,6 +77,14 @@ struct nb_ctx {
     std::string err;
     int inject_pending = 0;
     nb_ensemble *ens = nullptr;   // batched ensemble state (nb_ensemble.cu)
+
+    // small-block engine (mixed precision): cluster size, particles per CTA, the
+    // largest block it takes (0 = off; -1 = the default for n); t_eng is the
+    // block time it leaves behind in host-driven steps
+    int eng_C = 0;
+    int64_t eng_chunk = 0;
+    int32_t eng_smax = -1;
+    double *t_eng = nullptr;
 };
 
 // Accessors used by the ensemble translation unit.
@@ -98,7 +109,9 @@ namespace {
 
 constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
 constexpr int kRunUnroll = 16;                         // block steps per pass of the nb_run while node
-static_assert(kRunUnroll % 2 == 0, "the loop's steps alternate two block-time slots");
+constexpr int kRunUnrollEngine = 4;                    // the same with the engine (each runs many steps)
+static_assert(kRunUnroll % 2 == 0 && kRunUnrollEngine % 2 == 0,
+              "the loop's steps alternate two block-time slots");
 
 nb_status fail(nb_ctx *c, nb_status st, const char *fmt, ...)
 {
@@ -197,6 +210,53 @@ cudaError_t launch_force_ctx(nb_ctx *c)
         c->inject_pending = 0;
     }
     return launch_force(c, F);
+}
+
+// The engine's default largest block: its force phase runs on the cluster's
+// SMs only, so it takes blocks whose s N is small (2^22 pair evaluations: the
+// force phase then stays near the full path's per-step overhead).
+int32_t default_engine_smax(int64_t n)
+{
+    int64_t s = (int64_t(1) << 22) / std::max<int64_t>(n, 1);
+    s = std::max<int64_t>(16, std::min<int64_t>(s, kEngMaxS));
+    return (int32_t)s;
+}
+
+// Engine shape for the loaded system: mixed precision, a co-schedulable
+// cluster, and each CTA's chunk of pair records within its shared memory.
+void engine_setup(nb_ctx *c)
+{
+    c->eng_C = 0;
+    c->eng_chunk = 0;
+    if (c->cfg.precision != NB_PREC_MIXED || c->n < 1) return;
+    const int C = engine_cluster();
+    if (C < 1) return;
+    const int64_t chunk = engine_chunk(c->n_pad, C);
+    if (chunk < 16 || chunk > kEngMaxChunk) return;
+    c->eng_C = C;
+    c->eng_chunk = chunk;
+}
+
+bool engine_on(const nb_ctx *c)
+{
+    const int32_t smax = c->eng_smax < 0 ? default_engine_smax(c->n) : c->eng_smax;
+    return c->eng_C > 0 && smax > 0;
+}
+
+EngineArgs engine_args(nb_ctx *c, const StepArgs &A, const double *t_in, double *t_out, int64_t *s_clear,
+                       bool check_end, int64_t max_steps)
+{
+    EngineArgs e{};
+    e.S = A;
+    e.t_in = t_in;
+    e.t_out = t_out;
+    e.s_clear = s_clear;
+    e.eps2f = (float)c->eps2;
+    e.chunk = c->eng_chunk;
+    e.s_max = c->eng_smax < 0 ? default_engine_smax(c->n) : c->eng_smax;
+    e.check_end = check_end ? 1 : 0;
+    e.max_steps = max_steps;
+    return e;
 }
 
 void free_system(nb_ctx *c)
@@ -327,6 +387,7 @@ nb_status prepare_system(nb_ctx *ctx, int64_t n, double eps2)
 // Common tail of nb_init / nb_init_dev: state x, v, m loaded (SoA), a = k = 0.
 nb_status init_forces(nb_ctx *ctx)
 {
+    engine_setup(ctx);
     StepArgs A = step_args(ctx);
     CK(launch_pad_records(A, ctx->stream));
     CK(launch_state_to_ds(A, ctx->stream));
@@ -412,11 +473,19 @@ nb_status build_run_graph(nb_ctx *ctx)
     if (eb == cudaSuccess) {
         eb = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (eb == cudaSuccess) {
-            for (int u = 0; u < kRunUnroll && eb == cudaSuccess; ++u) {
+            const bool eng = engine_on(ctx);
+            const int unroll = eng ? kRunUnrollEngine : kRunUnroll;
+            for (int u = 0; u < unroll && eb == cudaSuccess; ++u) {
                 StepArgs Au = A;   // step u reads slot u % 2 and forms slot (u + 1) % 2
                 Au.t_known = ctx->t_slot + (u & 1);
                 Au.t_form = ctx->t_slot + ((u + 1) & 1);
-                eb = cudaEventRecord(fork, ctx->stream);
+                if (eng) {
+                    // the small blocks from this block time on; the engine leaves the time of
+                    // the first block it does not take in the same slot
+                    eb = launch_engine(engine_args(ctx, Au, Au.t_known, Au.t_known, nullptr, true, kMaxRunSteps),
+                                       ctx->eng_C, ctx->stream);
+                }
+                if (eb == cudaSuccess) eb = cudaEventRecord(fork, ctx->stream);
                 if (eb == cudaSuccess) eb = cudaStreamWaitEvent(side, fork, 0);
                 if (eb == cudaSuccess) eb = launch_predict(Au, Au.t_known, 0.0, true, side);
                 if (eb == cudaSuccess) eb = cudaEventRecord(join, side);
@@ -519,12 +588,13 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
     ctx->inject_pending = c.inject;
     (void)force_mixed_ctas_per_sm();   // sets kernel attributes before any graph capture
     (void)force_f64_ctas_per_sm();
+    if (c.precision == NB_PREC_MIXED) (void)engine_cluster();
     bool ok = dalloc(&ctx->s, 1) == cudaSuccess && dalloc(&ctx->t_next, 1) == cudaSuccess &&
               dalloc(&ctx->t_slot, 2) == cudaSuccess &&
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
               dalloc(&ctx->counters, 3 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
-              dalloc(&ctx->en_out, 2) == cudaSuccess;
+              dalloc(&ctx->en_out, 2) == cudaSuccess && dalloc(&ctx->t_eng, 1) == cudaSuccess;
     if (!ok) {
         nb_destroy(ctx);
         return NB_ERR_CUDA;
@@ -552,7 +622,7 @@ void nb_destroy(nb_ctx *ctx)
     free_system(ctx);
     nb_ctx_set_ensemble(ctx, nullptr);
     void *ptrs[] = {ctx->s, ctx->t_next, ctx->t_slot, ctx->t_end, ctx->split_used, ctx->tune_dev, ctx->status,
-                    ctx->counters, ctx->interactions, ctx->en_out};
+                    ctx->counters, ctx->interactions, ctx->en_out, ctx->t_eng};
     for (void *p : ptrs) dfree(p);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -714,7 +784,13 @@ nb_status nb_step(nb_ctx *ctx)
     if (st != NB_OK) return st;
     StepArgs A = step_args(ctx);
     CK(launch_select(A, SEL_FULL, 0, false, ctx->stream));
-    CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream));
+    const bool eng = engine_on(ctx);
+    if (eng) {
+        // the engine takes the block if it is small (then s = 0 and the kernels below
+        // do nothing), as inside nb_run
+        CK(launch_engine(engine_args(ctx, A, ctx->t_next, ctx->t_eng, ctx->s, false, 1), ctx->eng_C, ctx->stream));
+    }
+    CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream, eng));
     CK(launch_force_ctx(ctx));
     CK(launch_correct(A, false, false, false, ctx->stream));
     ctx->forces_pending = false;
@@ -750,20 +826,23 @@ nb_status nb_run(nb_ctx *ctx, double t_end)
     return sync_status(ctx);
 }
 
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms)
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms,
+                       int64_t *engine_steps)
 {
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!std::isfinite(t_end)) return fail(ctx, NB_ERR_ARG, "t_end must be finite");
     StepArgs A = step_args(ctx);
     const bool phases = phase_ms != nullptr;
-    int64_t nl = 0;
-    double total[4] = {0.0, 0.0, 0.0, 0.0};   // select, predict, force, correct
-    if (ctx->ev.size() < 8) {
+    const bool eng = engine_on(ctx);
+    const int32_t smax = eng ? engine_args(ctx, A, nullptr, nullptr, nullptr, false, 1).s_max : 0;
+    int64_t nl = 0, ne = 0;
+    double total[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // select, predict, force, correct, engine
+    if (ctx->ev.size() < 10) {
         for (cudaEvent_t e : ctx->ev)
             if (e) cudaEventDestroy(e);
-        ctx->ev.assign(8, nullptr);
-        for (int q = 0; q < 8; ++q) CK(cudaEventCreate(&ctx->ev[q]));
+        ctx->ev.assign(10, nullptr);
+        for (int q = 0; q < 10; ++q) CK(cudaEventCreate(&ctx->ev[q]));
     }
     // A phase is bracketed by events only after a short, time-bounded wait
     // kernel holds the stream, so that the launch and its end event are queued
@@ -791,10 +870,26 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
         CK(cudaMemcpyAsync(&ss, ctx->s, sizeof ss, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         if (!(tn <= t_end) || ss <= 0) break;
-        if (phases) {
-            CK(elapsed(0));
-            CK(open(1));
+        if (phases) CK(elapsed(0));
+        if (eng && ss <= smax) {
+            // the engine decides (block size and members per chunk) as it does in nb_run
+            CK(open(4));
+            CK(launch_engine(engine_args(ctx, A, ctx->t_next, ctx->t_eng, ctx->s, false, 1), ctx->eng_C,
+                             ctx->stream));
+            CK(close(4));
+            int64_t left = 0;
+            int32_t stw = 0;
+            CK(cudaMemcpyAsync(&left, ctx->s, sizeof left, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(&stw, ctx->status, sizeof stw, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            CK(elapsed(4));
+            if (left == 0) {
+                ++ne;
+                if (stw) break;
+                continue;
+            }
         }
+        if (phases) CK(open(1));
         CK(launch_predict(A, A.t_next, 0.0, false, ctx->stream));
         if (phases) CK(close(1));
         CK(open(2));
@@ -816,8 +911,9 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
     }
     if (force_ms) *force_ms = total[2];
     if (launches) *launches = nl;
+    if (engine_steps) *engine_steps = ne;
     if (phases)
-        for (int q = 0; q < 4; ++q) phase_ms[q] = total[q];
+        for (int q = 0; q < 5; ++q) phase_ms[q] = total[q];
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);
@@ -964,6 +1060,32 @@ nb_status nb_get_tuning(nb_ctx *ctx, int32_t *variant, int32_t *split)
     if (st != NB_OK) return st;
     if (variant) std::memcpy(variant, ctx->tune.variant, sizeof ctx->tune.variant);
     if (split) std::memcpy(split, ctx->tune.split, sizeof ctx->tune.split);
+    return NB_OK;
+}
+
+nb_status nb_set_engine(nb_ctx *ctx, int32_t s_max)
+{
+    nb_status st = check_ctx(ctx, false);
+    if (st != NB_OK) return st;
+    if (s_max > kEngMaxS || s_max < -1) return fail(ctx, NB_ERR_ARG, "s_max must be in [-1, %d]", kEngMaxS);
+    if (s_max > 0 && ctx->cfg.precision != NB_PREC_MIXED)
+        return fail(ctx, NB_ERR_ARG, "the small-block engine exists for mixed precision only");
+    if (s_max != ctx->eng_smax && ctx->run_exec) {   // the run graph holds the engine's launch
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaGraphExecDestroy(ctx->run_exec);
+        ctx->run_exec = nullptr;
+    }
+    ctx->eng_smax = s_max;
+    return NB_OK;
+}
+
+nb_status nb_get_engine(nb_ctx *ctx, int32_t *s_max, int32_t *cluster)
+{
+    nb_status st = check_ctx(ctx, false);
+    if (st != NB_OK) return st;
+    const bool on = ctx->have_state ? engine_on(ctx) : false;
+    if (s_max) *s_max = on ? (ctx->eng_smax < 0 ? default_engine_smax(ctx->n) : ctx->eng_smax) : 0;
+    if (cluster) *cluster = on ? ctx->eng_C : 0;
     return NB_OK;
 }
 

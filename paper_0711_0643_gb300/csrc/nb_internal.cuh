@@ -131,8 +131,10 @@ struct StepArgs {
     double *interactions;                 // sum s*n
 };
 
-// predictor to *t_dev (non-null; with skip_past also *t_dev <= *t_end, else no-op) or t_host
-cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st);
+// predictor to *t_dev (non-null; with skip_past also *t_dev <= *t_end, else no-op) or t_host;
+// skip_empty: no-op when the active count *a.s is 0 (the engine did the step)
+cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st,
+                           bool skip_empty = false);
 // Selection. SEL_FULL: the smallest key is the block time. SEL_KNOWN (nb_run
 // loop body): the block time is *t_known; also writes *t_form and, when the
 // block is not to be done (past *t_end, an error, the step cap), s = 0.
@@ -163,5 +165,28 @@ cudaError_t launch_check_active(const int32_t *idx, int64_t s, int64_t n, int32_
                                 cudaStream_t st);
 cudaError_t launch_check_due(const StepArgs &a, double t_block, cudaStream_t st);
 cudaError_t launch_delay(uint64_t ns, cudaStream_t st);
+
+// ------------------------------------------------------- small-block engine
+// One thread-block cluster runs consecutive block steps whose blocks are small
+// (select, predict, force, correct inside one kernel; nb_engine.cu).
+constexpr int kEngMaxS = 256;             // largest block the engine takes
+constexpr int kEngCap = 64;               // most members of one CTA's chunk in a block it takes
+constexpr int64_t kEngMaxChunk = 4096;    // particles per CTA (their pair records sit in shared memory)
+
+struct EngineArgs {
+    StepArgs S;
+    const double *t_in;    // block time of the first step
+    double *t_out;         // at exit: the block time of the first block not done
+    int64_t *s_clear;      // non-null: set to 0 when at least one step was done
+    float eps2f;
+    int64_t chunk;         // particles per CTA, a multiple of 16
+    int32_t s_max;         // largest block taken (<= kEngMaxS)
+    int32_t check_end;     // stop before a block past *S.t_end
+    int64_t max_steps;     // steps of this launch (the call's cap in S.counters applies too)
+};
+int engine_cluster();                          // CTAs per cluster on this device, 0 = no engine
+int64_t engine_chunk(int64_t n_pad, int C);    // particles per CTA
+size_t engine_smem_bytes(int64_t chunk);
+cudaError_t launch_engine(const EngineArgs &e, int C, cudaStream_t st);
 
 }  // namespace nb

@@ -33,11 +33,13 @@ __device__ __forceinline__ void predict_one(const StepArgs &A, int64_t i, double
     hermite_predict(A.x, A.v, A.a, A.k, A.t, A.n_pad, i, tn, xp, vp);
 }
 
-__global__ void predict_kernel(StepArgs A, const double *t_dev, double t_host, int skip_past)
+__global__ void predict_kernel(StepArgs A, const double *t_dev, double t_host, int skip_past, int skip_empty)
 {
     const double tn = t_dev ? *t_dev : t_host;
     // nb_run loop: no block is due at a time past t_end (the loop's last pass)
     if (skip_past && !(tn <= *A.t_end)) return;
+    // nb_step: the small-block engine has done this step
+    if (skip_empty && *A.s == 0) return;
     const int64_t np = A.n_pad;
     for (int64_t i = gtid(); i < A.n; i += gstride()) {
         if (A.precision == NB_PREC_MIXED) {
@@ -813,10 +815,11 @@ int grid_for(int64_t n, int threads, int max_grid = 4096)
 
 // -------------------------------------------------------------------- launchers
 
-cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st)
+cudaError_t launch_predict(const StepArgs &a, const double *t_dev, double t_host, bool skip_past, cudaStream_t st,
+                           bool skip_empty)
 {
     // FP64-heavy: small CTAs so that the work spreads over every SM
-    predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, t_dev, t_host, skip_past ? 1 : 0);
+    predict_kernel<<<grid_for(a.n, 64, 8192), 64, 0, st>>>(a, t_dev, t_host, skip_past ? 1 : 0, skip_empty ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,9 @@ _SIGS = [
     ("nb_correct", C.c_int, [_P, _D]),
     ("nb_step", C.c_int, [_P]),
     ("nb_run", C.c_int, [_P, _D]),
-    ("nb_run_timed", C.c_int, [_P, _D, _P, _P, _P]),
+    ("nb_run_timed", C.c_int, [_P, _D, _P, _P, _P, _P]),
+    ("nb_set_engine", C.c_int, [_P, _I32]),
+    ("nb_get_engine", C.c_int, [_P, _P, _P]),
     ("nb_energy", C.c_int, [_P, _P, _P, _P]),
     ("nb_get_state", C.c_int, [_P, _P]),
     ("nb_set_state", C.c_int, [_P, _P]),
@@ -215,15 +217,29 @@ def nb_run(ctx, t_end):
     return _check(ctx, load().nb_run(ctx, float(t_end)))
 
 
+PHASES = ("select", "predict", "force", "correct", "engine")
+
+
 def nb_run_timed(ctx, t_end, phases=False):
-    """Returns (force_ms, launches), plus a dict of summed phase times in ms
-    (select, predict, force, correct) when phases is true."""
-    ms = C.c_double(); nl = C.c_int64()
-    ph = (C.c_double * 4)() if phases else None
-    _check(ctx, load().nb_run_timed(ctx, float(t_end), C.byref(ms), C.byref(nl), ph))
+    """Returns (force_ms, launches, engine_steps), plus a dict of summed phase times in ms
+    (select, predict, force, correct, engine) when phases is true."""
+    ms = C.c_double(); nl = C.c_int64(); ne = C.c_int64()
+    ph = (C.c_double * 5)() if phases else None
+    _check(ctx, load().nb_run_timed(ctx, float(t_end), C.byref(ms), C.byref(nl), ph, C.byref(ne)))
     if phases:
-        return ms.value, nl.value, dict(zip(("select", "predict", "force", "correct"), list(ph)))
-    return ms.value, nl.value
+        return ms.value, nl.value, ne.value, dict(zip(PHASES, list(ph)))
+    return ms.value, nl.value, ne.value
+
+
+def nb_set_engine(ctx, s_max):
+    return _check(ctx, load().nb_set_engine(ctx, int(s_max)))
+
+
+def nb_get_engine(ctx):
+    """Returns (s_max, cluster): the largest block the small-block engine takes (0 = none)."""
+    sm = C.c_int32(); cl = C.c_int32()
+    _check(ctx, load().nb_get_engine(ctx, C.byref(sm), C.byref(cl)))
+    return sm.value, cl.value
 
 
 def nb_energy(ctx):

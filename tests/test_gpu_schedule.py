@@ -18,6 +18,11 @@ quantisation). Then, at every one of the 16 steps (and for the start steps of nb
     keeps going through all 16 steps.
 The oracle integrating its own state (free running) is run beside it; the step at which its
 block schedule first differs from the GPU's is printed.
+
+Two drivers: "explicit" calls nb_next_block, nb_predict, nb_force_jerk and nb_correct (the
+four-kernel step); "step" calls nb_step, which runs small blocks inside the small-block
+engine (its new forces are read back from the corrected state, where the corrector stores
+them; its potential is not compared).
 """
 import numpy as np
 import pytest
@@ -52,8 +57,8 @@ def _force_errors(m, xr, vr, eps2, idx, a_g, k_g, phi_g, ar, kr, pr, where):
     return ea + 1e-14 * A, ek + 1e-14 * K
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
-def test_block_schedule_mixed_lockstep(nb, orc, cfg):
+@pytest.mark.parametrize("cfg,driver", [(1, "explicit"), (2, "explicit"), (1, "step"), (2, "step")])
+def test_block_schedule_mixed_lockstep(nb, orc, cfg, driver):
     snap = ics.config(cfg)
     n = snap.n
     nth = orc.default_threads()
@@ -82,16 +87,22 @@ def test_block_schedule_mixed_lockstep(nb, orc, cfg):
             before = c.state()
             tn, s = nb.nb_next_block(c.ctx)
             idx = nb.nb_get_active(c.ctx, s)
-            nb.nb_predict(c.ctx, tn)
-            a_g, k_g, phi_g = nb.nb_force_jerk(c.ctx, None, s)
-            nb.nb_correct(c.ctx, tn)
-            after = c.state()
+            if driver == "explicit":
+                nb.nb_predict(c.ctx, tn)
+                a_g, k_g, phi_g = nb.nb_force_jerk(c.ctx, None, s)
+                nb.nb_correct(c.ctx, tn)
+                after = c.state()
+            else:
+                nb.nb_step(c.ctx)
+                after = c.state()
+                a_g, k_g, phi_g = after["a"][idx], after["k"][idx], None
             # the oracle's block step on the same state
             tr, ir = orc.next_block(before["t"], before["dt"])
             assert tr == tn and np.array_equal(ir, idx), (step, tr, tn)
             xr, vr = orc.predict(before["x"], before["v"], before["a"], before["k"], before["t"], tn)
             ar, kr, pr = orc.force(snap.m, xr, vr, snap.eps2, idx, nthreads=nth)
-            ea, ek = _force_errors(snap.m, xr, vr, snap.eps2, idx, a_g, k_g, phi_g, ar, kr, pr, step)
+            ea, ek = _force_errors(snap.m, xr, vr, snap.eps2, idx, a_g, k_g, pr if phi_g is None else phi_g,
+                                   ar, kr, pr, step)
             for q, i in enumerate(idx):
                 dt = before["dt"][i]
                 x1, v1, a2, a3 = orc.correct_one(xr[i], vr[i], before["a"][i], before["k"][i], ar[q], kr[q], dt)
@@ -115,7 +126,7 @@ def test_block_schedule_mixed_lockstep(nb, orc, cfg):
             if free_diverged is None and not (tf == tn and np.array_equal(idx_f, idx)):
                 free_diverged = step
     w = np.array(windows)
-    print(f"config {cfg}: 16 lockstep block steps, {w.size} corrections; tie window delta_i "
+    print(f"config {cfg}, {driver}: 16 lockstep block steps, {w.size} corrections; tie window delta_i "
           f"median {np.median(w):.2e}, max {w.max():.2e}; candidates inside their window {in_window}; "
           f"time steps differing from the oracle's (all ties) {ties}; free-running oracle schedule "
           f"{'identical for all 16 steps' if free_diverged is None else f'differs from block step {free_diverged}'}")
