@@ -150,6 +150,31 @@ nb_status nb_force_jerk(nb_ctx *ctx, const int32_t *idx, int64_t s, double *a, d
 nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, double *a_dev,
                             double *k_dev, double *phi_dev);
 
+/* The j-parallel block step of Sect. 3 (Flowchart): every rank holds the whole
+ * system, sums the forces on the active block over its own share of j, the
+ * partial forces are added over the ranks (the paper's MPI_Allreduce; the
+ * binding's jparallel module gathers them and adds them in rank order), and
+ * every rank corrects identically.
+ *
+ * nb_j_range: the share [*j_begin, *j_end) of rank `rank` of `world` (whole
+ * 256-particle tiles, balanced; the last share ends at n).
+ * nb_force_jerk_range / _dev: as nb_force_jerk / nb_force_jerk_dev, with the
+ * sums over j in [j_begin, j_end) only (j_begin and j_end multiples of 256,
+ * j_end may be n; an empty range gives zeros). idx NULL = the active list of
+ * the last nb_next_block. The results are partial sums: nb_correct does not take
+ * them (NB_ERR_STATE); add them over the ranks and pass the totals to
+ * nb_correct_forces.
+ * nb_correct_forces / _dev: nb_correct with the new a[s][3], k[s][3] given by
+ * the caller (host / device arrays, in the order of the active list of the last
+ * nb_next_block or force call). Same errors as nb_correct. */
+nb_status nb_j_range(nb_ctx *ctx, int32_t rank, int32_t world, int64_t *j_begin, int64_t *j_end);
+nb_status nb_force_jerk_range(nb_ctx *ctx, const int32_t *idx, int64_t s, int64_t j_begin, int64_t j_end,
+                              double *a, double *k, double *phi);
+nb_status nb_force_jerk_range_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, int64_t j_begin,
+                                  int64_t j_end, double *a_dev, double *k_dev, double *phi_dev);
+nb_status nb_correct_forces(nb_ctx *ctx, double t_block, const double *a, const double *k);
+nb_status nb_correct_forces_dev(nb_ctx *ctx, double t_block, const double *a_dev, const double *k_dev);
+
 /* Hermite corrector and new steps (Sect. 2.1, Eq. timestep) for the active list
  * of the last nb_force_jerk, whose members must all have t_i + dt_i == t_block
  * (the paper's "dt" argument is read as the block time; each particle's own

@@ -168,6 +168,8 @@ ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
     ForceArgs F{};
     F.n = c->n;
     F.n_tiles = c->n_tiles;
+    F.tile_lo = 0;
+    F.tile_hi = c->n_tiles;
     F.j = c->j;
     F.xp = c->xp; F.vp = c->vp; F.m = c->m;
     F.eps2f = (float)c->eps2;
@@ -213,11 +215,12 @@ cudaError_t launch_force_ctx(nb_ctx *c)
 }
 
 // The engine's default largest block: its force phase runs on the cluster's
-// SMs only, so it takes blocks whose s N is small (2^22 pair evaluations: the
-// force phase then stays near the full path's per-step overhead).
+// SMs only, so it takes blocks whose s N is small (2^19 pair evaluations: the
+// force phase then takes a few microseconds, below the full path's per-step
+// overhead).
 int32_t default_engine_smax(int64_t n)
 {
-    int64_t s = (int64_t(1) << 22) / std::max<int64_t>(n, 1);
+    int64_t s = (int64_t(1) << 19) / std::max<int64_t>(n, 1);
     s = std::max<int64_t>(16, std::min<int64_t>(s, kEngMaxS));
     return (int32_t)s;
 }
@@ -761,6 +764,144 @@ nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, doub
     if (!idx_dev) return fail(ctx, NB_ERR_ARG, "null idx_dev");
     CK(launch_set_active(idx_dev, ctx->idx, s, ctx->s, ctx->stream));
     return force_common(ctx, s, a, k, phi);
+}
+
+// ----- the j-parallel step (Sect. 3): partial forces over a share of j, and the
+// corrector with forces summed elsewhere (over ranks)
+
+static nb_status range_tiles(nb_ctx *ctx, int64_t j_begin, int64_t j_end, int64_t *t_lo, int64_t *t_hi)
+{
+    if (j_begin < 0 || j_end > ctx->n || j_begin > j_end)
+        return fail(ctx, NB_ERR_ARG, "j range [%lld, %lld) outside [0, %lld)", (long long)j_begin, (long long)j_end,
+                    (long long)ctx->n);
+    if (j_begin % kJT != 0 || (j_end % kJT != 0 && j_end != ctx->n))
+        return fail(ctx, NB_ERR_ARG, "j_begin and j_end must be multiples of %d (j_end may be n)", kJT);
+    *t_lo = j_begin / kJT;
+    *t_hi = (j_end + kJT - 1) / kJT;
+    return NB_OK;
+}
+
+static nb_status force_range_common(nb_ctx *ctx, int64_t s, int64_t t_lo, int64_t t_hi, double *a_dev,
+                                    double *k_dev, double *phi_dev)
+{
+    if (t_hi == t_lo) {   // an empty share: zero partial sums
+        if (a_dev) CK(cudaMemsetAsync(a_dev, 0, 3 * s * sizeof(double), ctx->stream));
+        if (k_dev) CK(cudaMemsetAsync(k_dev, 0, 3 * s * sizeof(double), ctx->stream));
+        if (phi_dev) CK(cudaMemsetAsync(phi_dev, 0, s * sizeof(double), ctx->stream));
+    } else {
+        ForceArgs F = force_args(ctx);
+        F.tile_lo = t_lo;
+        F.tile_hi = t_hi;
+        if (ctx->inject_pending) {
+            F.inject = 1;
+            ctx->inject_pending = 0;
+        }
+        CK(launch_force(ctx, F));
+        CK(launch_reduce_out(ctx->fin, nullptr, s, a_dev, k_dev, phi_dev, ctx->status, ctx->stream));
+    }
+    ctx->forces_pending = false;   // partial sums: nb_correct does not take them
+    ctx->block_s = s;
+    return NB_OK;
+}
+
+nb_status nb_j_range(nb_ctx *ctx, int32_t rank, int32_t world, int64_t *j_begin, int64_t *j_end)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (world < 1 || rank < 0 || rank >= world) return fail(ctx, NB_ERR_ARG, "rank %d of %d", rank, world);
+    const int64_t lo = ctx->n_tiles * rank / world, hi = ctx->n_tiles * (rank + 1) / world;
+    if (j_begin) *j_begin = std::min<int64_t>(lo * kJT, ctx->n);
+    if (j_end) *j_end = std::min<int64_t>(hi * kJT, ctx->n);
+    return NB_OK;
+}
+
+nb_status nb_force_jerk_range(nb_ctx *ctx, const int32_t *idx, int64_t s, int64_t j_begin, int64_t j_end, double *a,
+                              double *k, double *phi)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
+    int64_t t_lo = 0, t_hi = 0;
+    if ((st = range_tiles(ctx, j_begin, j_end, &t_lo, &t_hi)) != NB_OK) return st;
+    if (s == 0) return NB_OK;
+    if (idx) {
+        for (int64_t q = 0; q < s; ++q) {
+            if (idx[q] < 0 || idx[q] >= ctx->n) return fail(ctx, NB_ERR_ARG, "idx[%lld] out of range", (long long)q);
+            if (q > 0 && idx[q] <= idx[q - 1]) return fail(ctx, NB_ERR_ARG, "idx not strictly ascending");
+        }
+        CK(cudaMemcpyAsync(ctx->idx, idx, s * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->s, &s, sizeof s, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else if (s != ctx->block_s) {
+        return fail(ctx, NB_ERR_ARG, "s does not match the last nb_next_block");
+    }
+    st = force_range_common(ctx, s, t_lo, t_hi, ctx->out_a, ctx->out_k, ctx->out_phi);
+    if (st != NB_OK) return st;
+    if (a) CK(cudaMemcpyAsync(a, ctx->out_a, 3 * s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (k) CK(cudaMemcpyAsync(k, ctx->out_k, 3 * s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, ctx->out_phi, s * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
+}
+
+nb_status nb_force_jerk_range_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, int64_t j_begin, int64_t j_end,
+                                  double *a_dev, double *k_dev, double *phi_dev)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
+    int64_t t_lo = 0, t_hi = 0;
+    if ((st = range_tiles(ctx, j_begin, j_end, &t_lo, &t_hi)) != NB_OK) return st;
+    if (s == 0) return NB_OK;
+    if (idx_dev) {
+        CK(launch_set_active(idx_dev, ctx->idx, s, ctx->s, ctx->stream));
+    } else if (s != ctx->block_s) {
+        return fail(ctx, NB_ERR_ARG, "s does not match the last nb_next_block");
+    }
+    return force_range_common(ctx, s, t_lo, t_hi, a_dev, k_dev, phi_dev);
+}
+
+static nb_status correct_with(nb_ctx *ctx, double t_block)
+{
+    CK(cudaMemcpyAsync(ctx->t_next, &t_block, sizeof t_block, cudaMemcpyHostToDevice, ctx->stream));
+    StepArgs A = step_args(ctx);
+    CK(launch_check_due(A, t_block, ctx->stream));
+    nb_status st = sync_status(ctx);
+    if (st != NB_OK) return st;
+    CK(launch_correct(A, true, false, false, ctx->stream));
+    ctx->forces_pending = false;
+    ctx->block_s = -1;
+    return sync_status(ctx);
+}
+
+nb_status nb_correct_forces(nb_ctx *ctx, double t_block, const double *a, const double *k)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (ctx->block_s < 0) return fail(ctx, NB_ERR_STATE, "no active list (call nb_next_block)");
+    if (!a || !k) return fail(ctx, NB_ERR_ARG, "null forces");
+    const int64_t s = ctx->block_s;
+    if (s == 0) return NB_OK;
+    std::vector<double> fin((size_t)s * kPartStride, 0.0);
+    for (int64_t q = 0; q < s; ++q)
+        for (int c = 0; c < 3; ++c) {
+            fin[q * kPartStride + c] = a[3 * q + c];
+            fin[q * kPartStride + 3 + c] = k[3 * q + c];
+        }
+    CK(cudaMemcpyAsync(ctx->fin, fin.data(), fin.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));   // fin is host stack memory
+    return correct_with(ctx, t_block);
+}
+
+nb_status nb_correct_forces_dev(nb_ctx *ctx, double t_block, const double *a_dev, const double *k_dev)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (ctx->block_s < 0) return fail(ctx, NB_ERR_STATE, "no active list (call nb_next_block)");
+    if (!a_dev || !k_dev) return fail(ctx, NB_ERR_ARG, "null forces");
+    const int64_t s = ctx->block_s;
+    if (s == 0) return NB_OK;
+    CK(launch_forces_in(a_dev, k_dev, s, ctx->fin, ctx->stream));
+    return correct_with(ctx, t_block);
 }
 
 nb_status nb_correct(nb_ctx *ctx, double t_block)

@@ -57,10 +57,9 @@ __device__ __forceinline__ DS ds_scale2(DS x, float pow2) { return DS{x.hi * pow
 // Hermite predictor of one particle in double-single for the mixed j-record:
 // xp = x + d (v + d (a/2 + d k/6)) per component (the same polynomial as
 // x + v d + a d^2/2 + k d^3/6, in Horner form), vp = v + d (a + d k/2) in FP32.
-// x2, v2, a2, k2: double-single state [3][np] as float2 (hi, lo).
-__device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, const float2 *a2, const float2 *k2,
-                                           int64_t np, int64_t i, double d64, float4 &hi, float4 &lo, float4 &vel,
-                                           float m)
+// X, V, A, K: the particle's double-single x, v, a, k per component.
+__device__ __forceinline__ void ds_predict_vals(const float2 *X, const float2 *V, const float2 *A, const float2 *K,
+                                                double d64, float4 &hi, float4 &lo, float4 &vel, float m)
 {
     const DS d = ds_split(d64);
     const DS sixth = {0.166666671633720398f, -4.967053879e-09f};   // 1/6 = hi + lo to ~2^-53
@@ -68,20 +67,36 @@ __device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, c
     float ph[3], pl[3], pv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float2 X = x2[c * np + i], V = v2[c * np + i], A = a2[c * np + i], K = k2[c * np + i];
-        DS t = ds_mul(DS{K.x, K.y}, d6);
-        t = ds_add(ds_scale2(DS{A.x, A.y}, 0.5f), t);
+        DS t = ds_mul(DS{K[c].x, K[c].y}, d6);
+        t = ds_add(ds_scale2(DS{A[c].x, A[c].y}, 0.5f), t);
         t = ds_mul(t, d);
-        t = ds_add(DS{V.x, V.y}, t);
+        t = ds_add(DS{V[c].x, V[c].y}, t);
         t = ds_mul(t, d);
-        const DS xp = ds_add(DS{X.x, X.y}, t);
+        const DS xp = ds_add(DS{X[c].x, X[c].y}, t);
         ph[c] = xp.hi;
         pl[c] = xp.lo;
-        pv[c] = __fadd_rn(__fadd_rn(V.x, __fmul_rn(d.hi, __fadd_rn(A.x, __fmul_rn(d.hi, __fmul_rn(0.5f, K.x))))), V.y);
+        pv[c] = __fadd_rn(__fadd_rn(V[c].x, __fmul_rn(d.hi, __fadd_rn(A[c].x, __fmul_rn(d.hi, __fmul_rn(0.5f, K[c].x))))),
+                          V[c].y);
     }
     hi = make_float4(ph[0], ph[1], ph[2], m);
     lo = make_float4(pl[0], pl[1], pl[2], 0.f);
     vel = make_float4(pv[0], pv[1], pv[2], 0.f);
+}
+
+// The same from the state arrays x2, v2, a2, k2 ([3][np] float2 (hi, lo)) of particle i.
+__device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, const float2 *a2, const float2 *k2,
+                                           int64_t np, int64_t i, double d64, float4 &hi, float4 &lo, float4 &vel,
+                                           float m)
+{
+    float2 X[3], V[3], A[3], K[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        X[c] = x2[c * np + i];
+        V[c] = v2[c * np + i];
+        A[c] = a2[c * np + i];
+        K[c] = k2[c * np + i];
+    }
+    ds_predict_vals(X, V, A, K, d64, hi, lo, vel, m);
 }
 
 }  // namespace nb

@@ -65,15 +65,19 @@ struct __align__(16) IRec {
     float4 h, l, w;
 };
 
+// Shared memory of one CTA. Everything another CTA needs is pushed into the
+// reader's shared memory (distributed shared-memory stores) before a cluster
+// barrier, so every read after a barrier is local.
 struct __align__(16) EngSmem {
-    float2 part[kEngMaxS][8];      // this CTA's partial sums (hi, lo) per block position; 7 used
-    IRec ilist[kEngMaxS];          // every member's predicted record, in block order
-    IRec own[kEngCap];             // this chunk's members (read by every CTA)
-    int own_idx[kEngCap];          // their particle indices, ascending
-    float2 red[kEngWarps][14];     // per-warp sums (blocks of up to 16)
-    long long slot_min[kEngMaxC];  // written by rank q: the smallest key of its chunk after the step
-    int slot_err[kEngMaxC];        // written by rank q: its status bits of the step
-    int slot_cnt[kEngMaxC];        // written by rank q: its chunk's members of the block
+    IRec inbox[kEngMaxC][kEngCap];          // [q][k]: member k of rank q's chunk, pushed by rank q
+    IRec ilist[kEngMaxS];                   // all members in block order (copied from the inbox)
+    float2 part_in[kEngCap][kEngMaxC][8];   // [k][q]: rank q's partial sums (hi, lo) for this chunk's member k
+    int2 qmap[kEngMaxS];                    // block position -> (owner rank, member index there)
+    int own_idx[kEngCap];                   // this chunk's members (particle indices, ascending)
+    float2 red[kEngWarps][7];               // per-warp sums (blocks of up to 16)
+    long long slot_min[kEngMaxC];           // written by rank q: the smallest key of its chunk after the step
+    int slot_err[kEngMaxC];                 // written by rank q: its status bits of the step
+    int slot_cnt[kEngMaxC];                 // written by rank q: its chunk's members of the block
     int wcnt[kEngWarps];
     long long wmin[kEngWarps];
     int wflags[kEngWarps];
@@ -91,6 +95,16 @@ __device__ __forceinline__ long long warp_min(long long v)
 __device__ __forceinline__ IPk ipk_of_rec(const IRec &R)
 {
     return ipk_of(IPart{R.h.x, R.h.y, R.h.z, R.l.x, R.l.y, R.l.z, R.w.x, R.w.y, R.w.z});
+}
+
+// Sends the (hi, lo) partial sums of block position q to the member's owner.
+__device__ __forceinline__ void push_part(cg::cluster_group &cluster, EngSmem *sm, int q, int rank, const Acc7 &hi,
+                                          const Acc7 &lo)
+{
+    const int2 o = sm->qmap[q];
+    float2 *dst = cluster.map_shared_rank(&sm->part_in[o.y][rank][0], o.x);
+#pragma unroll
+    for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi, c), acc_get(lo, c));
 }
 
 // Partial sums of one member (predicted record ip, index gi) over pair records
@@ -120,7 +134,8 @@ __device__ __forceinline__ void sweep(const JPair *recs, int64_t j0, int rb, int
 // Blocks of more than 16: TJ lanes per member, each CTA thread group takes
 // members in rounds; the group's lanes reduce with two-sums in a fixed order.
 template <int TJ>
-__device__ void force_groups(EngSmem *sm, const JPair *recs, int64_t j0, int64_t j1, int nrec, int s, float2 e2)
+__device__ void force_groups(cg::cluster_group &cluster, EngSmem *sm, const JPair *recs, int64_t j0, int64_t j1,
+                             int nrec, int s, float2 e2, int rank)
 {
     constexpr int kGroups = kEngThreads / TJ;
     const int tid = threadIdx.x, tj = tid % TJ, g = tid / TJ;
@@ -138,10 +153,7 @@ __device__ void force_groups(EngSmem *sm, const JPair *recs, int64_t j0, int64_t
         else
             sweep<false, TJ>(recs, j0, 0, nrec, tj, ip, gi, e2, hi, lo);
         ds_group_reduce7<TJ>(hi, lo);
-        if (tj == 0 && q < s) {
-#pragma unroll
-            for (int c = 0; c < 7; ++c) sm->part[q][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
-        }
+        if (tj == 0 && q < s) push_part(cluster, sm, q, rank, hi, lo);
     }
 }
 
@@ -209,60 +221,85 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             hits += tot;
             __syncthreads();   // wcnt is rewritten by the next segment
         }
+        const int hk = hits < kEngCap ? hits : kEngCap;
+
+        // ---- 2. predict the chunk into pair records (all loads of a thread's two
+        // particles in flight together), then push the members' records to every CTA
+        for (int64_t i0 = j0 + tid; i0 < j1; i0 += 2 * kEngThreads) {
+            const int64_t i1 = i0 + kEngThreads;
+            float2 X[2][3], V[2][3], Ac[2][3], K[2][3];
+            double ti[2];
+            float mi[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t i = u == 0 ? i0 : i1;
+                const int64_t ii = i < n ? i : 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X[u][c] = A.x2[c * np + ii];
+                    V[u][c] = A.v2[c * np + ii];
+                    Ac[u][c] = A.a2[c * np + ii];
+                    K[u][c] = A.k2[c * np + ii];
+                }
+                ti[u] = A.t[ii];
+                mi[u] = (float)A.m[ii];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t i = u == 0 ? i0 : i1;
+                if (i >= j1) continue;
+                if (i < n) {
+                    float4 h, l, w;
+                    ds_predict_vals(X[u], V[u], Ac[u], K[u], tbd - ti[u], h, l, w, mi[u]);
+                    jrec_store(recs, i - j0, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
+                } else {
+                    const float far = (float)kPadPos;
+                    jrec_store(recs, i - j0, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        // the corrector's FP64 state of this thread's member (four lanes per member),
+        // in flight during the force phase; a quad past the members works on member 0
+        // without storing (correct_group needs a valid particle, and one with the
+        // members' step keeps its fast path)
+        const int hq = tid >> 2;
+        const bool qlive = hq < hk;
+        const int icor = hk > 0 ? sm->own_idx[qlive ? hq : 0] : (int)j0;
+        GroupState gs{};
+        if (hk > 0 && warp * 8 < hk) gs = load_group(H, icor);
+        __syncthreads();
         if (!waited) {
             asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
             waited = true;
         }
         if (tid < C) *cluster.map_shared_rank(&sm->slot_cnt[rank], tid) = hits;
-        const int hk = hits < kEngCap ? hits : kEngCap;
-
-        // ---- 2. predict the chunk into pair records; the members' records for the other CTAs
-        for (int64_t i = j0 + tid; i < j1; i += kEngThreads) {
-            if (i < n) {
-                float4 h, l, w;
-                ds_predict(A.x2, A.v2, A.a2, A.k2, np, i, tbd - A.t[i], h, l, w, (float)A.m[i]);
-                jrec_store(recs, i - j0, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
-            } else {
-                const float far = (float)kPadPos;
-                jrec_store(recs, i - j0, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        // the corrector's FP64 state of this thread's member (four lanes per member),
-        // in flight during the force phase
-        const int hq = tid >> 2;
-        const bool qlive = hq < hk;
-        // a quad past the members works on member 0 without storing (correct_group
-        // needs a valid particle, and one with the members' step keeps the fast path)
-        const int icor = hk > 0 ? sm->own_idx[qlive ? hq : 0] : (int)j0;
-        GroupState gs{};
-        if (hk > 0 && warp * 8 < hk) gs = load_group(H, icor);
-        __syncthreads();
-        for (int q = tid; q < hk; q += kEngThreads) {
-            const int i = sm->own_idx[q];
+        if (tid < hk * C) {
+            const int k = tid / C, dst = tid % C;
+            const int i = sm->own_idx[k];
             const IPart P = jrec_load(recs, i - j0);
-            sm->own[q] = IRec{make_float4(P.xh, P.yh, P.zh, __int_as_float(i)), make_float4(P.xl, P.yl, P.zl, 0.f),
-                              make_float4(P.vx, P.vy, P.vz, 0.f)};
+            *cluster.map_shared_rank(&sm->inbox[rank][k], dst) =
+                IRec{make_float4(P.xh, P.yh, P.zh, __int_as_float(i)), make_float4(P.xl, P.yl, P.zl, 0.f),
+                     make_float4(P.vx, P.vy, P.vz, 0.f)};
         }
         cluster.sync();
 
         // ---- the block: its size, this chunk's offset; does the engine take it?
-        int s = 0, off = 0, mx = 0;
+        int s = 0, mx = 0;
         {
             const int cq = lane < C ? sm->slot_cnt[lane] : 0;
-            int lower = lane < rank ? cq : 0, total = cq, big = cq;
+            int total = cq, big = cq;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) {
-                lower += __shfl_xor_sync(full, lower, o);
                 total += __shfl_xor_sync(full, total, o);
                 big = max(big, __shfl_xor_sync(full, big, o));
             }
             s = total;
-            off = lower;
             mx = big;
         }
         if (s < 1 || s > E.s_max || mx > kEngCap) break;
 
-        // ---- 3. every member's record from its owner, then the partial sums over this chunk
+        // ---- 3. the members in block order (rank by rank), then the partial sums
+        // over this chunk, pushed to each member's owner
         for (int q = tid; q < s; q += kEngThreads) {
             int r = 0, base = 0;
             while (r < C - 1) {
@@ -271,7 +308,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
                 base += cr;
                 ++r;
             }
-            sm->ilist[q] = *cluster.map_shared_rank(&sm->own[q - base], r);
+            sm->ilist[q] = sm->inbox[r][q - base];
+            sm->qmap[q] = make_int2(r, q - base);
         }
         __syncthreads();
         if (s <= 16) {
@@ -295,7 +333,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
                 ds_group_reduce7<32>(hi, lo);
                 if (lane == 0) {
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) sm->red[warp][2 * c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+                    for (int c = 0; c < 7; ++c) sm->red[warp][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
                 }
             }
             __syncthreads();
@@ -303,32 +341,41 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
                 const int qq = tid / 7, c = tid % 7;
                 float h = 0.f, l = 0.f;
                 for (int p = 0; p < G; ++p) {
-                    const float2 v = sm->red[qq * G + p][2 * c];
+                    const float2 v = sm->red[qq * G + p][c];
                     ds_add(h, l, v.x, v.y);
                 }
-                sm->part[qq][c] = make_float2(h, l);
+                const int2 o = sm->qmap[qq];
+                *cluster.map_shared_rank(&sm->part_in[o.y][rank][c], o.x) = make_float2(h, l);
             }
         } else if (s <= 32) {
-            force_groups<16>(sm, recs, j0, j1, nrec, s, e2);
+            force_groups<16>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
         } else if (s <= 64) {
-            force_groups<8>(sm, recs, j0, j1, nrec, s, e2);
+            force_groups<8>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
         } else {
-            force_groups<4>(sm, recs, j0, j1, nrec, s, e2);
+            force_groups<4>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
         }
         cluster.sync();
 
-        // ---- 4. correct this chunk's members: partial sums in rank order, FP64 corrector
+        // ---- 4. correct this chunk's members: the ranks' partial sums in rank order,
+        // then the FP64 corrector
         int flags = 0;
         long long tmin = m2;
         if (warp * 8 < hk) {   // warps holding at least one member (quads 8w .. 8w + 7)
             const int c = (tid & 3) < 3 ? (tid & 3) : 2;
-            const int pos = off + (qlive ? hq : 0);
+            const int k = qlive ? hq : 0;
+            float2 va[kEngMaxC], vk[kEngMaxC];
+#pragma unroll
+            for (int r = 0; r < kEngMaxC; ++r) {
+                va[r] = r < C ? sm->part_in[k][r][c] : make_float2(0.f, 0.f);
+                vk[r] = r < C ? sm->part_in[k][r][3 + c] : make_float2(0.f, 0.f);
+            }
             float ha = 0.f, la = 0.f, hk_ = 0.f, lk = 0.f;
-            for (int r = 0; r < C; ++r) {
-                const float2 *pr = cluster.map_shared_rank(&sm->part[pos][0], r);
-                const float2 va = pr[c], vk = pr[3 + c];
-                ds_add(ha, la, va.x, va.y);
-                ds_add(hk_, lk, vk.x, vk.y);
+#pragma unroll
+            for (int r = 0; r < kEngMaxC; ++r) {
+                if (r < C) {
+                    ds_add(ha, la, va[r].x, va[r].y);
+                    ds_add(hk_, lk, vk[r].x, vk[r].y);
+                }
             }
             const double an = (double)ha + (double)la, kn = (double)hk_ + (double)lk;
             long long newkey = kInfBits;
@@ -336,7 +383,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             tmin = min_ll(tmin, newkey);
         }
         tmin = warp_min(tmin);
-        flags = __reduce_or_sync(full, flags);
+        flags = (int)__reduce_or_sync(full, (unsigned)flags);
         if (lane == 0) {
             sm->wmin[warp] = tmin;
             sm->wflags[warp] = flags;
@@ -346,7 +393,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             long long mm = lane < kEngWarps ? sm->wmin[lane] : kInfBits;
             int ff = lane < kEngWarps ? sm->wflags[lane] : 0;
             mm = warp_min(mm);
-            ff = __reduce_or_sync(full, ff);
+            ff = (int)__reduce_or_sync(full, (unsigned)ff);
             if (lane < C) {
                 *cluster.map_shared_rank(&sm->slot_min[rank], lane) = mm;
                 *cluster.map_shared_rank(&sm->slot_err[rank], lane) = ff;
@@ -367,7 +414,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         long long nxt = lane < C ? sm->slot_min[lane] : kInfBits;
         int err = lane < C ? sm->slot_err[lane] : 0;
         nxt = warp_min(nxt);
-        err = __reduce_or_sync(full, err);
+        err = (int)__reduce_or_sync(full, (unsigned)err);
         tb = nxt;
         if (err) {
             if (rank == 0 && tid == 0) atomicOr(A.status, err);

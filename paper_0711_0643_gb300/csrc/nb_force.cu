@@ -228,9 +228,9 @@ template <int R>
 __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t tper = qdiv(A.tile_hi - A.tile_lo + S - 1, S);
+    const int64_t t0 = A.tile_lo + (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.tile_hi ? t0 + tper : A.tile_hi;
     const int64_t p0 = t0 * kPT, p1 = t1 * kPT;
     // this thread's first pair record moves into L1 while the i-particle loads
     // are in flight (a prefetch holds no registers)
@@ -336,9 +336,9 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
     constexpr int kFoldTiles = PPT >= kFoldPairs / 2 ? 0 : (kFoldPairs / 2) / PPT;   // 0: folded inside the sweep
     static_assert(TJ <= 32 && (32 % TJ) == 0, "TJ must divide a warp");
     const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
-    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t tper = qdiv(A.tile_hi - A.tile_lo + S - 1, S);
+    const int64_t t0 = A.tile_lo + (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.tile_hi ? t0 + tper : A.tile_hi;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
     // the first tiles are in flight before the i-particle loads
     if (tid == 0) {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         S = table_split(sm->tune.split[b], b, s, A.n, mixed_I(variant));
     }
     if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
-    S = clamp_split(S, A.n_tiles, s, A.part_cap);
+    S = clamp_split(S, A.tile_hi - A.tile_lo, s, A.part_cap);
     if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
     const int64_t I = mixed_I(variant);
     const int64_t nib = qdiv(s + I - 1, I);
@@ -531,9 +531,9 @@ __device__ void work_f64_stream(const ForceArgs &A, int64_t s, int64_t bx, int b
     double xi[6];
     load_i64(A, gi, xi);
     const int64_t np = A.n_tiles * kJT;
-    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t tper = qdiv(A.tile_hi - A.tile_lo + S - 1, S);
+    const int64_t t0 = A.tile_lo + (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.tile_hi ? t0 + tper : A.tile_hi;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t j = t0 * kJT + tid; j < t1 * kJT; j += kThreads)
         pair_f64(__ldg(A.xp + j), __ldg(A.xp + np + j), __ldg(A.xp + 2 * np + j), __ldg(A.m + j),
@@ -562,9 +562,9 @@ __device__ void work_f64_iloop(const ForceArgs &A, int64_t s, int64_t bx, int by
     double xi[6];
     load_i64(A, gi, xi);
     const int64_t np = A.n_tiles * kJT;
-    const int64_t tper = qdiv(A.n_tiles + S - 1, S);
-    const int64_t t0 = (int64_t)by * tper;
-    const int64_t t1 = t0 + tper < A.n_tiles ? t0 + tper : A.n_tiles;
+    const int64_t tper = qdiv(A.tile_hi - A.tile_lo + S - 1, S);
+    const int64_t t0 = A.tile_lo + (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.tile_hi ? t0 + tper : A.tile_hi;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t j = t0 * kJT; j < t1 * kJT; ++j)
         pair_f64(__ldg(A.xp + j), __ldg(A.xp + np + j), __ldg(A.xp + 2 * np + j), __ldg(A.m + j),
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
         S = table_split(A.tune->split[b], b, s, A.n, f64_I(variant));
     }
     if (variant < 0 || variant >= kF64Variants) variant = kF64Variants - 1;
-    S = clamp_split(S, A.n_tiles, s, A.part_cap);
+    S = clamp_split(S, A.tile_hi - A.tile_lo, s, A.part_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) *A.split_used = S;
     const int64_t I = f64_I(variant);
     const int64_t W = qdiv(s + I - 1, I) * S;

@@ -58,6 +58,8 @@ struct HState {
 struct ForceArgs {
     int64_t n;            // particles
     int64_t n_tiles;      // ceil(n / kJT); j arrays are padded to n_tiles * kJT
+    int64_t tile_lo;      // the sums run over j in tiles [tile_lo, tile_hi) only (all: 0, n_tiles);
+    int64_t tile_hi;      // a sub-range gives one rank's partial forces of the j-parallel step
     JRecs j;              // mixed records
     const double *xp;     // FP64 predicted positions [3][n_pad]
     const double *vp;     // FP64 predicted velocities [3][n_pad]
@@ -158,6 +160,8 @@ cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st);
 // copies the device list src[s] to dst and writes s to *s_dev (one launch)
 cudaError_t launch_set_active(const int32_t *src, int32_t *dst, int64_t s, int64_t *s_dev, cudaStream_t st);
 cudaError_t launch_pad_records(const StepArgs &a, cudaStream_t st);
+// caller's forces a[s][3], k[s][3] into the final-sum layout fin[s][8]
+cudaError_t launch_forces_in(const double *a, const double *k, int64_t s, double *fin, cudaStream_t st);
 // energy: writes K, W to out[0], out[1] (fixed-order sums)
 cudaError_t launch_energy(const StepArgs &a, double *scratch, int scratch_ctas, double *out,
                           cudaStream_t st);
@@ -170,8 +174,8 @@ cudaError_t launch_delay(uint64_t ns, cudaStream_t st);
 // One thread-block cluster runs consecutive block steps whose blocks are small
 // (select, predict, force, correct inside one kernel; nb_engine.cu).
 constexpr int kEngMaxS = 256;             // largest block the engine takes
-constexpr int kEngCap = 64;               // most members of one CTA's chunk in a block it takes
-constexpr int64_t kEngMaxChunk = 4096;    // particles per CTA (their pair records sit in shared memory)
+constexpr int kEngCap = 32;               // most members of one CTA's chunk in a block it takes
+constexpr int64_t kEngMaxChunk = 2048;    // particles per CTA (their pair records sit in shared memory)
 
 struct EngineArgs {
     StepArgs S;

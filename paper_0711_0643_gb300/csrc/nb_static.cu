@@ -117,6 +117,8 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     ForceArgs F{};
     F.n = n;
     F.n_tiles = n_tiles;
+    F.tile_lo = 0;
+    F.tile_hi = n_tiles;
     F.j.p = reinterpret_cast<JPair *>(base + kOffRec);
     F.eps2f = (float)eps2;
     F.eps2 = eps2;

@@ -621,6 +621,16 @@ __global__ void iota_kernel(int32_t *idx, int64_t n)
     for (int64_t i = gtid(); i < n; i += gstride()) idx[i] = (int32_t)i;
 }
 
+// Forces supplied by the caller (a[s][3], k[s][3]) into the corrector's layout [s][8].
+__global__ void forces_in_kernel(const double *a, const double *k, int64_t s, double *fin)
+{
+    for (int64_t q = gtid(); q < s * kPartStride; q += gstride()) {
+        const int64_t ii = q / kPartStride;
+        const int c = (int)(q % kPartStride);
+        fin[q] = c < 3 ? a[ii * 3 + c] : (c < 6 ? k[ii * 3 + c - 3] : 0.0);
+    }
+}
+
 // A caller's device active list and its length into the context (one launch
 // instead of a device copy and a host-to-device copy of the count).
 __global__ void set_active_kernel(const int32_t *src, int32_t *dst, int64_t s, int64_t *s_dev)
@@ -982,6 +992,12 @@ cudaError_t launch_records_to_aos(const StepArgs &a, double *xp_aos, double *vp_
 cudaError_t launch_fill_iota(int32_t *idx, int64_t n, cudaStream_t st)
 {
     iota_kernel<<<grid_for(n, kStepThreads), kStepThreads, 0, st>>>(idx, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces_in(const double *a, const double *k, int64_t s, double *fin, cudaStream_t st)
+{
+    forces_in_kernel<<<grid_for(s * kPartStride, kStepThreads, 1216), kStepThreads, 0, st>>>(a, k, s, fin);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,11 @@ _SIGS = [
     ("nb_force_jerk", C.c_int, [_P, _P, _I64, _P, _P, _P]),
     ("nb_force_jerk_dev", C.c_int, [_P, _P, _I64, _P, _P, _P]),
     ("nb_correct", C.c_int, [_P, _D]),
+    ("nb_j_range", C.c_int, [_P, _I32, _I32, _P, _P]),
+    ("nb_force_jerk_range", C.c_int, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
+    ("nb_force_jerk_range_dev", C.c_int, [_P, _P, _I64, _I64, _I64, _P, _P, _P]),
+    ("nb_correct_forces", C.c_int, [_P, _D, _P, _P]),
+    ("nb_correct_forces_dev", C.c_int, [_P, _D, _P, _P]),
     ("nb_step", C.c_int, [_P]),
     ("nb_run", C.c_int, [_P, _D]),
     ("nb_run_timed", C.c_int, [_P, _D, _P, _P, _P, _P]),
@@ -207,6 +212,42 @@ def nb_force_jerk_dev(ctx, idx_dev, s, a_dev=0, k_dev=0, phi_dev=0):
 
 def nb_correct(ctx, t_block):
     return _check(ctx, load().nb_correct(ctx, float(t_block)))
+
+
+def nb_j_range(ctx, rank, world):
+    """(j_begin, j_end): the share of j of rank `rank` of `world` in the j-parallel step."""
+    b = C.c_int64(); e = C.c_int64()
+    _check(ctx, load().nb_j_range(ctx, int(rank), int(world), C.byref(b), C.byref(e)))
+    return b.value, e.value
+
+
+def nb_force_jerk_range(ctx, idx, s, j_begin, j_end, want=(True, True, True)):
+    """Partial (a[s,3], k[s,3], phi[s]) over j in [j_begin, j_end); idx None = the last block."""
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        s = idx.shape[0]
+    s = int(s)
+    a = np.zeros((s, 3)) if want[0] else None
+    k = np.zeros((s, 3)) if want[1] else None
+    phi = np.zeros(s) if want[2] else None
+    _check(ctx, load().nb_force_jerk_range(ctx, _ptr(idx), s, int(j_begin), int(j_end), _ptr(a), _ptr(k),
+                                           _ptr(phi)))
+    return a, k, phi
+
+
+def nb_force_jerk_range_dev(ctx, idx_dev, s, j_begin, j_end, a_dev=0, k_dev=0, phi_dev=0):
+    return _check(ctx, load().nb_force_jerk_range_dev(ctx, C.c_void_p(idx_dev or None), int(s), int(j_begin),
+                                                      int(j_end), C.c_void_p(a_dev or None),
+                                                      C.c_void_p(k_dev or None), C.c_void_p(phi_dev or None)))
+
+
+def nb_correct_forces(ctx, t_block, a, k):
+    a = _f64(a, (-1, 3)); k = _f64(k, (-1, 3))
+    return _check(ctx, load().nb_correct_forces(ctx, float(t_block), _ptr(a), _ptr(k)))
+
+
+def nb_correct_forces_dev(ctx, t_block, a_dev, k_dev):
+    return _check(ctx, load().nb_correct_forces_dev(ctx, float(t_block), C.c_void_p(a_dev), C.c_void_p(k_dev)))
 
 
 def nb_step(ctx):
