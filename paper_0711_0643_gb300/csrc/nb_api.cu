@@ -177,6 +177,7 @@ ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
     F.idx = c->idx;
     F.idx_cap = c->n_pad;
     F.s = c->s;
+    F.s_host = -1;
     F.part = c->part;
     F.part_cap = c->part_cap;
     F.fin = c->fin;
@@ -762,8 +763,25 @@ nb_status nb_force_jerk_dev(nb_ctx *ctx, const int32_t *idx_dev, int64_t s, doub
     if (s < 0 || s > ctx->n) return fail(ctx, NB_ERR_ARG, "s = %lld out of range", (long long)s);
     if (s == 0) return NB_OK;
     if (!idx_dev) return fail(ctx, NB_ERR_ARG, "null idx_dev");
-    CK(launch_set_active(idx_dev, ctx->idx, s, ctx->s, ctx->stream));
-    return force_common(ctx, s, a, k, phi);
+    // one launch: the kernel reads the caller's list, copies it into the context (for
+    // nb_correct) and writes the sums in the caller's layouts
+    ForceArgs F = force_args(ctx);
+    F.idx = idx_dev;
+    F.idx_cap = s;
+    F.s_host = s;
+    F.idx_copy = ctx->idx;
+    F.s_copy = ctx->s;
+    F.out_a = a;
+    F.out_k = k;
+    F.out_phi = phi;
+    if (ctx->inject_pending) {
+        F.inject = 1;
+        ctx->inject_pending = 0;
+    }
+    CK(launch_force(ctx, F));
+    ctx->forces_pending = true;
+    ctx->block_s = s;
+    return NB_OK;
 }
 
 // ----- the j-parallel step (Sect. 3): partial forces over a share of j, and the

@@ -17,7 +17,7 @@
 //      every CTA's shared memory;
 //   2. predicts its whole chunk to the block time into pair records in shared
 //      memory (the double-single predictor of the full path, same bits) and
-//      keeps its members' predicted records for the other CTAs;
+//      pushes its members' predicted records to every CTA;
 //   -- cluster barrier: every CTA knows every chunk's count, hence the block
 //      size s and each chunk's offset; if the block is too large for the engine
 //      (s > s_max, or more than kEngCap members in one chunk), past t_end, or
@@ -34,6 +34,10 @@
 //      (same bits given the same forces); the smallest key of its chunk after the
 //      step is pushed into every CTA;
 //   -- cluster barrier: the smallest of those is the next block time.
+// Each CTA keeps its chunk's double-single state, times and keys in shared memory
+// for the whole launch (loaded once; the corrector updates its members' copies as
+// it writes the FP64 state), so the per-step selection and prediction read only
+// shared memory.
 // No software spin-wait exists: every branch is taken identically by all CTAs
 // (each decision uses values every CTA holds), so every CTA reaches every
 // barrier. Results are bitwise reproducible and do not depend on how many steps
@@ -162,6 +166,13 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EngSmem *sm = reinterpret_cast<EngSmem *>(smem_raw);
     JPair *recs = reinterpret_cast<JPair *>(smem_raw + sizeof(EngSmem));
+    const int64_t ch = E.chunk;
+    // this chunk's double-single state [3][ch], times, keys and masses
+    float2 *cx = reinterpret_cast<float2 *>(recs + ch / 2);
+    float2 *cv = cx + 3 * ch, *ca = cv + 3 * ch, *ck = ca + 3 * ch;
+    double *ct = reinterpret_cast<double *>(ck + 3 * ch);
+    long long *ckey = reinterpret_cast<long long *>(ct + ch);
+    float *cm = reinterpret_cast<float *>(ckey + ch);
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -174,6 +185,22 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
     const int nrec = (int)((j1 - j0) / 2);
     const long long *key = reinterpret_cast<const long long *>(A.tn);
     const HState H{A.x, A.v, A.a, A.k, A.t, A.dt, A.tn, A.x2, A.v2, A.a2, A.k2, A.n_pad};
+    const DsMirror mir{cx, cv, ca, ck, ct, ckey, ch, j0};
+    for (int64_t i = j0 + tid; i < j0 + ch; i += kEngThreads) {
+        const int64_t li = i - j0;
+        const bool real = i < n;   // padding (and a short last chunk): +inf keys, never selected
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx[c * ch + li] = real ? A.x2[c * np + i] : make_float2(0.f, 0.f);
+            cv[c * ch + li] = real ? A.v2[c * np + i] : make_float2(0.f, 0.f);
+            ca[c * ch + li] = real ? A.a2[c * np + i] : make_float2(0.f, 0.f);
+            ck[c * ch + li] = real ? A.k2[c * np + i] : make_float2(0.f, 0.f);
+        }
+        ct[li] = real ? A.t[i] : 0.0;
+        ckey[li] = real ? key[i] : kInfBits;
+        cm[li] = real ? (float)A.m[i] : 0.f;
+    }
+    __syncthreads();
     const float2 e2 = make_float2(E.eps2f, E.eps2f);
     // step budget of this launch (this call's cap on block steps included), the
     // block time and a pending error: the same values in every thread of the cluster
@@ -199,8 +226,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         int hits = 0;
         for (int64_t c0 = j0; c0 < j1; c0 += 2 * kEngThreads) {
             const int64_t e = c0 + 2 * (int64_t)tid;
-            const longlong2 kv =
-                e < j1 ? *reinterpret_cast<const longlong2 *>(key + e) : make_longlong2(kInfBits, kInfBits);
+            const longlong2 kv = e < j1 ? *reinterpret_cast<const longlong2 *>(ckey + (e - j0))
+                                        : make_longlong2(kInfBits, kInfBits);
             const bool h0 = kv.x == tb, h1 = kv.y == tb;
             m2 = min_ll(m2, h0 ? kInfBits : kv.x);
             m2 = min_ll(m2, h1 ? kInfBits : kv.y);
@@ -223,39 +250,25 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         }
         const int hk = hits < kEngCap ? hits : kEngCap;
 
-        // ---- 2. predict the chunk into pair records (all loads of a thread's two
-        // particles in flight together), then push the members' records to every CTA
-        for (int64_t i0 = j0 + tid; i0 < j1; i0 += 2 * kEngThreads) {
-            const int64_t i1 = i0 + kEngThreads;
-            float2 X[2][3], V[2][3], Ac[2][3], K[2][3];
-            double ti[2];
-            float mi[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int64_t i = u == 0 ? i0 : i1;
-                const int64_t ii = i < n ? i : 0;
+        // ---- 2. predict the chunk into pair records from the shared-memory state,
+        // then push the members' records to every CTA
+        for (int64_t i = j0 + tid; i < j1; i += kEngThreads) {
+            const int64_t li = i - j0;
+            if (i < n) {
+                float2 X[3], V[3], Ac[3], K[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    X[u][c] = A.x2[c * np + ii];
-                    V[u][c] = A.v2[c * np + ii];
-                    Ac[u][c] = A.a2[c * np + ii];
-                    K[u][c] = A.k2[c * np + ii];
+                    X[c] = cx[c * ch + li];
+                    V[c] = cv[c * ch + li];
+                    Ac[c] = ca[c * ch + li];
+                    K[c] = ck[c * ch + li];
                 }
-                ti[u] = A.t[ii];
-                mi[u] = (float)A.m[ii];
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int64_t i = u == 0 ? i0 : i1;
-                if (i >= j1) continue;
-                if (i < n) {
-                    float4 h, l, w;
-                    ds_predict_vals(X[u], V[u], Ac[u], K[u], tbd - ti[u], h, l, w, mi[u]);
-                    jrec_store(recs, i - j0, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
-                } else {
-                    const float far = (float)kPadPos;
-                    jrec_store(recs, i - j0, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
-                }
+                float4 h, l, w;
+                ds_predict_vals(X, V, Ac, K, tbd - ct[li], h, l, w, cm[li]);
+                jrec_store(recs, li, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
+            } else {
+                const float far = (float)kPadPos;
+                jrec_store(recs, li, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
             }
         }
         // the corrector's FP64 state of this thread's member (four lanes per member),
@@ -379,7 +392,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             }
             const double an = (double)ha + (double)la, kn = (double)hk_ + (double)lk;
             long long newkey = kInfBits;
-            flags |= correct_group(H, icor, gs, qlive, tbd, an, kn, A.eta, A.dt_max, A.dt_min, &newkey);
+            flags |= correct_group(H, icor, gs, qlive, tbd, an, kn, A.eta, A.dt_max, A.dt_min, &newkey, &mir);
             tmin = min_ll(tmin, newkey);
         }
         tmin = warp_min(tmin);
@@ -432,7 +445,13 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
 
 // ------------------------------------------------------------------ host side
 
-size_t engine_smem_bytes(int64_t chunk) { return sizeof(EngSmem) + (size_t)(chunk / 2) * sizeof(JPair); }
+// shared memory: the exchange areas, the chunk's pair records, and its state copy
+// (x, v, a, k double-single [3][chunk] float2 each, times, keys, masses)
+size_t engine_smem_bytes(int64_t chunk)
+{
+    return sizeof(EngSmem) + (size_t)(chunk / 2) * sizeof(JPair) +
+           (size_t)chunk * (12 * sizeof(float2) + sizeof(double) + sizeof(long long) + sizeof(float));
+}
 
 // Cluster size of the engine for this device (16 if co-schedulable with the
 // largest shared-memory footprint, else 8, else 0 = no engine); queried once.

@@ -168,6 +168,30 @@ __device__ __forceinline__ void write_part(const ForceArgs &A, int64_t ii, int b
     for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi, c), acc_get(lo, c));
 }
 
+// Final sum of component c (ax ay az kx ky kz phi) of active particle ii: into
+// fin and, when the launch has them, the caller's layouts.
+__device__ __forceinline__ void put_final(const ForceArgs &A, int64_t ii, int c, double v)
+{
+    A.fin[ii * kPartStride + c] = v;
+    double *dst = c < 3 ? A.out_a : (c < 6 ? A.out_k : A.out_phi);
+    if (dst) {
+        dst[c < 6 ? ii * 3 + (c % 3) : ii] = v;
+        if (!isfinite(v)) atomicOr(A.status, kStNonfinite);
+    }
+}
+
+// Active count of a launch and the optional copy of the caller's list into the
+// context (grid-stride; every CTA takes part).
+__device__ __forceinline__ int64_t launch_s(const ForceArgs &A) { return A.s_host >= 0 ? A.s_host : *A.s; }
+
+__device__ __forceinline__ void copy_list(const ForceArgs &A, int64_t s)
+{
+    if (!A.idx_copy) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < s; q += (int64_t)gridDim.x * blockDim.x)
+        A.idx_copy[q] = A.idx[q];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.s_copy = s;
+}
+
 // Called by every thread after a work item has written its partials. The CTA
 // that completes the i-block (ticket S - 1) adds the block's S partials in split
 // order with two-sums and writes the FP64 results; it then re-arms the ticket.
@@ -196,7 +220,7 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
                     const float2 v = __ldcg(src + sp * kPartStride);
                     ds_add(h, l, v.x, v.y);
                 }
-                A.fin[ii * kPartStride + c] = (double)h + (double)l;
+                put_final(A, ii, c, (double)h + (double)l);
             }
         } else {
             // many splits: one warp per (particle, component); lanes stride over the
@@ -212,7 +236,7 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
                     ds_add(h, l, v.x, v.y);
                 }
                 ds_group_reduce<32>(h, l);
-                if (lane == 0) A.fin[ii * kPartStride + c] = (double)h + (double)l;
+                if (lane == 0) put_final(A, ii, c, (double)h + (double)l);
             }
         }
         if (threadIdx.x == 0) A.tickets[bx] = 0;
@@ -252,17 +276,28 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
     Acc7 hi[R], lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { zero(p[r]); zero(hi[r]); zero(lo[r]); }
+    // two pair records per thread in flight (their loads are issued together),
+    // a fold after every kFoldPairs / 2 records
     int cnt = 0;
-    for (int64_t pp = p0 + tid; pp < p1; pp += kThreads) {
-        float4 q0, q1, q2, q3, q4;
+    for (int64_t pp = p0 + tid; pp < p1; pp += 2 * kThreads) {
+        const int64_t pq = pp + kThreads < p1 ? pp + kThreads : pp;
+        float4 a0, a1, a2, a3, a4, b0, b1, b2, b3, b4;
         {
             const float4 *q = A.j.p[pp].q;
-            q0 = __ldg(q); q1 = __ldg(q + 1); q2 = __ldg(q + 2); q3 = __ldg(q + 3); q4 = __ldg(q + 4);
+            const float4 *w = A.j.p[pq].q;
+            a0 = __ldg(q); a1 = __ldg(q + 1); a2 = __ldg(q + 2); a3 = __ldg(q + 3); a4 = __ldg(q + 4);
+            b0 = __ldg(w); b1 = __ldg(w + 1); b2 = __ldg(w + 2); b3 = __ldg(w + 3); b4 = __ldg(w + 4);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            pair_packed<true>(q0, q1, q2, q3, q4, ip[r], e2, p[r], 2 * pp == gi[r], 2 * pp + 1 == gi[r]);
-        if (++cnt == kFoldPairs / 2) {
+            pair_packed<true>(a0, a1, a2, a3, a4, ip[r], e2, p[r], 2 * pp == gi[r], 2 * pp + 1 == gi[r]);
+        if (pq != pp) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                pair_packed<true>(b0, b1, b2, b3, b4, ip[r], e2, p[r], 2 * pq == gi[r], 2 * pq + 1 == gi[r]);
+        }
+        cnt += 2;
+        if (cnt >= kFoldPairs / 2) {
             cnt = 0;
 #pragma unroll
             for (int r = 0; r < R; ++r) fold(hi[r], lo[r], p[r]);
@@ -437,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         mbar_init(&sm->inject_bar, 1);
         fence_mbar_init();
         sm->abort = 0;
-        sm->s = *A.s;
+        sm->s = launch_s(A);
     }
     // the active count and the whole tuning table in one round trip
     if (A.force_variant < 0 && tid < 2 * kBuckets) {
@@ -450,6 +485,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     __syncthreads();
     const int64_t s = sm->s;
     if (s <= 0) return;
+    copy_list(A, s);
     if (A.inject) {
         // Test hook: wait on a barrier that no one arrives on; the spin limit must
         // expire and the kernel must report it. No copy is in flight here.
@@ -595,7 +631,7 @@ __device__ void finish_item_f64(const ForceArgs &A, int64_t s, int64_t bx, int S
             const int c = (int)(q % 7);
             double x = 0.0;
             for (int sp = 0; sp < S; ++sp) x += __ldcg(A.part + (ii * S + sp) * kPartStride + c);
-            A.fin[ii * kPartStride + c] = x;
+            put_final(A, ii, c, x);
         }
         if (threadIdx.x == 0) A.tickets[bx] = 0;
     }
@@ -610,8 +646,9 @@ __global__ void __launch_bounds__(kThreads) force_f64_kernel(ForceArgs A)
     __shared__ uint64_t inject_bar;
     __shared__ int last;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int64_t s = *A.s;
+    const int64_t s = launch_s(A);
     if (s <= 0) return;
+    copy_list(A, s);
     if (A.inject) {
         if (threadIdx.x == 0) {
             mbar_init(&inject_bar, 1);

@@ -144,6 +144,16 @@ __device__ __forceinline__ float2 rn_ds_pack(double x)
 }
 __device__ __forceinline__ double pow2_of(int e) { return dfrom((long long)(1023 + e) << 52); }
 
+// A second copy of the double-single state, the times and the keys that
+// correct_group also writes when given one (the small-block engine keeps its
+// particles' copy in shared memory): element (c, i) at c * np + (i - base).
+struct DsMirror {
+    float2 *x2, *v2, *a2, *k2;
+    double *t;
+    long long *key;
+    int64_t np, base;
+};
+
 // The state correct_group reads for particle i (lane q: component min(q, 2)).
 struct GroupState {
     double ti, dt, x, v, ao, ko;
@@ -157,7 +167,7 @@ __device__ __forceinline__ GroupState load_group(const HState &H, int64_t i)
 
 __device__ __forceinline__ int correct_group(const HState &H, int64_t i, const GroupState &g, bool live, double tn,
                                              double an, double kn, double eta, double dt_max, double dt_min,
-                                             long long *key_out = nullptr)
+                                             long long *key_out = nullptr, const DsMirror *mir = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int q = lane & 3;
@@ -261,10 +271,18 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, const G
             H.a[o] = an;
             H.k[o] = kn;
             if (H.x2) {
-                H.x2[o] = rn_ds_pack(x1);
-                H.v2[o] = rn_ds_pack(v1);
-                H.a2[o] = rn_ds_pack(an);
-                H.k2[o] = rn_ds_pack(kn);
+                const float2 px = rn_ds_pack(x1), pv = rn_ds_pack(v1), pa = rn_ds_pack(an), pk = rn_ds_pack(kn);
+                H.x2[o] = px;
+                H.v2[o] = pv;
+                H.a2[o] = pa;
+                H.k2[o] = pk;
+                if (mir) {
+                    const int64_t om = c * mir->np + (i - mir->base);
+                    mir->x2[om] = px;
+                    mir->v2[om] = pv;
+                    mir->a2[om] = pa;
+                    mir->k2[om] = pk;
+                }
             }
         } else {
             const double dt_new = quantise_bits(qb, pos, dt, tn, dt_max, dt_min);
@@ -274,6 +292,10 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, const G
             H.dt[i] = dt_new;
             H.tn[i] = key;
             if (key_out) *key_out = dbits(key);
+            if (mir) {
+                mir->t[i - mir->base] = tn;
+                mir->key[i - mir->base] = dbits(key);
+            }
         }
     }
     return flags;

@@ -69,6 +69,12 @@ struct ForceArgs {
     const int32_t *idx;   // active list (ascending), length *s
     int64_t idx_cap;      // readable entries of idx (>= *s): the kernel reads ahead before *s arrives
     const int64_t *s;     // active count (device)
+    int64_t s_host;       // >= 0: the active count, given at launch (s is then not read)
+    int32_t *idx_copy;    // non-null: the kernel copies idx[0 .. s) here and s to *s_copy
+    int64_t *s_copy;      //   (a caller's device list becomes the context's without a separate launch)
+    double *out_a;        // non-null: the final sums also in the caller's layouts a[s][3],
+    double *out_k;        //   k[s][3], phi[s] (any may be null), with non-finite results
+    double *out_phi;      //   flagged, so no separate reduction launch is needed
     double *part;         // split partials [s][split][8] (mixed: float2 (hi, lo) pairs)
     int64_t part_cap;     // capacity of part in 8-byte words
     double *fin;          // final sums [s][8]: ax ay az kx ky kz phi pad
@@ -174,8 +180,8 @@ cudaError_t launch_delay(uint64_t ns, cudaStream_t st);
 // One thread-block cluster runs consecutive block steps whose blocks are small
 // (select, predict, force, correct inside one kernel; nb_engine.cu).
 constexpr int kEngMaxS = 256;             // largest block the engine takes
-constexpr int kEngCap = 32;               // most members of one CTA's chunk in a block it takes
-constexpr int64_t kEngMaxChunk = 2048;    // particles per CTA (their pair records sit in shared memory)
+constexpr int kEngCap = 16;               // most members of one CTA's chunk in a block it takes
+constexpr int64_t kEngMaxChunk = 1024;    // particles per CTA (their state and pair records sit in shared memory)
 
 struct EngineArgs {
     StepArgs S;

@@ -125,6 +125,7 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     F.idx = idx_dev;
     F.idx_cap = s;
     F.s = reinterpret_cast<const int64_t *>(base + kOffS);
+    F.s_host = -1;
     F.part = reinterpret_cast<double *>(base + kOffPart);
     F.part_cap = kStaticPartWords;
     F.fin = reinterpret_cast<double *>(base + kOffFin);
