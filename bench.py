@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 FLOP_PER_INTERACTION = 60          # the customary count for one force + jerk pair
 T_END = 1.0
 WORKLOAD = {"workload": "plummer N=16384 eps=1/1024 eta=0.01 t=0->1, mixed FP32/FP64",
-            "model": "plummer", "n": 16384, "eps": 1.0 / 1024, "eta": 0.01, "t_end": T_END,
+            "n": 16384, "eps": 1.0 / 1024, "eta": 0.01, "t_end": T_END,
             "seed": 20071108}
 
 
@@ -227,6 +227,36 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- GPU arm
 
+def _r(x, d=4):
+    """x rounded to d significant digits (compact JSON)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
+        return x
+    return float(f"{x:.{d}g}")
+
+
+def _stats3(e):
+    """[max, p99, median] of an error array, rounded."""
+    e = np.asarray(e, dtype=float)
+    return [_r(float(e.max()), 3), _r(float(np.percentile(e, 99)), 3), _r(float(np.median(e)), 3)]
+
+
+def golden_energy(cfg):
+    """The oracle's stored |dE/E| and step count for a timed integration (tests/golden/c<cfg>_energy.txt,
+    written by tests/golden/make_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"c{cfg}_energy.txt")
+    out = {}
+    try:
+        with open(path) as f:
+            for ln in f:
+                ln = ln.split("#", 1)[0].strip()
+                if ln:
+                    key, val = ln.split()[:2]
+                    out[key] = val
+        return {"abs_dE_over_E": float.fromhex(out["abs_dE_over_E"]), "block_steps": int(out["block_steps"])}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def main_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -287,6 +317,7 @@ def main_gpu(args):
 
     # ---- mixed precision: the headline
     c = make_ctx(nb.NB_PREC_MIXED)
+    eng_smax, eng_cluster = nb.nb_get_engine(c.ctx)
     for _ in range(args.warmup):
         step(c)
     dist_barrier()
@@ -303,34 +334,39 @@ def main_gpu(args):
     bsteps = st["block_steps"]
     dE = abs(E1 - E0) / abs(E0)
     # kernels per step: layout (2) + pad, predict, iota, force, init_steps (5) + energy 2 x 2
-    # + the run loop's first selection (1) + 4 per loop step (selection, predictor, force,
-    # corrector); the loop runs whole passes of 16 steps, the one that finds no block due
-    # and those after it in its pass as no-ops
-    loop_steps = (bsteps // 16 + 1) * 16
-    launches = 2 + 5 + 4 + 1 + 4 * loop_steps
+    # + the run loop's first selection (1) + per step slot of the loop (counted on the
+    # device): the engine (when on), selection, predictor, force, corrector
+    per_slot = 5 if eng_smax > 0 else 4
+    launches = 2 + 5 + 4 + 1 + per_slot * st["loop_slots"]
 
-    # ---- roofline of the dominant kernel (force), same trajectory, events around each launch
+    # ---- roofline of the dominant kernel, same trajectory, events around each launch
     nb.nb_init_dev(c.ctx, n, m_d.data_ptr(), x_d.data_ptr(), v_d.data_ptr(), snap.eps2)
     torch.cuda.synchronize(dev)
     clk_rf = ClockSampler(local).start()
-    force_ms, nlaunch, eng_steps, phase_ms = nb.nb_run_timed(c.ctx, T_END, phases=True)
+    tm = nb.nb_run_timed(c.ctx, T_END, phases=True)
     clk_rf_s = clk_rf.stop()
-    st_rf = nb.nb_stats(c.ctx)
     sm_mhz = clk["sm_mhz"] or clk_rf_s["sm_mhz"] or load_peaks().get("clocks_under_load", {}).get("sm_mhz_median")
     peak = fp32_peak_tflops(num_sms, sm_mhz) if sm_mhz else None
-    achieved = FLOP_PER_INTERACTION * st_rf["interactions"] / (force_ms / 1e3) / 1e12
-    traffic = force_traffic()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                "traffic_basis": "mean DRAM read+write bytes per force launch, cold-cache ncu capture of this "
-                                 "workload to t = 1/64 (profiles/force_traffic_plummer_n16384_t1over64.md)"
-                                 if traffic else None,
-                "kernel": "force_mixed_kernel", "launches": nlaunch,
-                "avg_launch_us": 1e3 * force_ms / max(nlaunch, 1),
+    nl, ne = tm["force_launches"], tm["engine_steps"]
+    force_ms, eng_ms = tm["force_ms"], tm["phase_ms"]["engine"]
+    achieved = FLOP_PER_INTERACTION * tm["force_interactions"] / (force_ms / 1e3) / 1e12
+    eng_tflops = FLOP_PER_INTERACTION * tm["engine_interactions"] / (eng_ms / 1e3) / 1e12 if eng_ms > 0 else None
+    mean_s = tm["force_interactions"] / max(nl, 1) / n
+    traffic = force_traffic(mean_s)
+    roofline = {"bound": "alu", "achieved": _r(achieved), "peak": _r(peak), "unit": "TFLOP/s",
+                "frac": _r(achieved / peak) if peak else None, "traffic": _r(traffic),
+                "kernel": "force_mixed_kernel", "launches": nl, "avg_launch_us": _r(1e3 * force_ms / max(nl, 1)),
+                "mean_s": _r(mean_s),
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz} MHz (median SM clock "
                               f"sampled during the timed region)",
                 "flop_convention": f"{FLOP_PER_INTERACTION} flop per force+jerk interaction",
-                "phases_us_per_block_step": {k: 1e3 * v / max(nlaunch, 1) for k, v in phase_ms.items()}}
+                "phases_us_per_step": {k: _r(1e3 * v / max(nl if k != "engine" else ne, 1), 3)
+                                       for k, v in tm["phase_ms"].items()},
+                "share_of_timed_kernels": {"force": _r(force_ms / (force_ms + eng_ms), 3),
+                                           "engine": _r(eng_ms / (force_ms + eng_ms), 3)}}
+    engine = {"s_max": eng_smax, "cluster": eng_cluster, "steps": ne, "four_kernel_steps": nl,
+              "us_per_step": _r(1e3 * eng_ms / max(ne, 1), 3), "tflops": _r(eng_tflops, 3),
+              "frac_fp32_peak": _r(eng_tflops / peak, 3) if (peak and eng_tflops) else None}
 
     # ---- end to end through the C ABI with host buffers
     m_h = np.ascontiguousarray(snap.m); x_h = np.ascontiguousarray(snap.x); v_h = np.ascontiguousarray(snap.v)
@@ -360,44 +396,35 @@ def main_gpu(args):
         c64 = make_ctx(nb.NB_PREC_FP64)
         step(c64)   # warm
         ms64, (F0, F1, st64) = timed_steps(c64, 1)
-        fp64 = {"interactions_per_s": (st64["interactions"] + float(n) * n) / (ms64[0] / 1e3),
-                "block_steps_per_s": st64["block_steps"] / (ms64[0] / 1e3),
-                "abs_dE_over_E": abs(F1 - F0) / abs(F0), "ms_per_step": ms64[0],
-                "block_steps": st64["block_steps"]}
+        fp64 = {"ips": _r((st64["interactions"] + float(n) * n) / (ms64[0] / 1e3)),
+                "bsps": _r(st64["block_steps"] / (ms64[0] / 1e3)), "dE": _r(abs(F1 - F0) / abs(F0)),
+                "ms": _r(ms64[0]), "block_steps": st64["block_steps"],
+                "mixed_over_fp64_bsps": _r((bsteps * args.steps / (total_ms / 1e3)) /
+                                           (st64["block_steps"] / (ms64[0] / 1e3)), 3)}
         c64.close()
 
-    # ---- batched ensemble: 256 Plummer clusters, one persistent cluster launch to t = 1
-    ens = None
-    if args.ensemble and rank == 0:
-        ens = ensemble_bench(nb, torch, dev, sptr, stream)
+    ens = ensemble_bench(nb, torch, dev, sptr, stream) if (args.ensemble and rank == 0) else None
+    salp = salpeter_bench(nb, torch, dev, sptr, stream) if (args.salpeter and rank == 0) else None
+    king = king_bench(nb, torch, dev, sptr, stream) if (args.king and rank == 0) else None
 
-    # ---- Plummer N = 65536 with Salpeter masses to t = 0.5 (opt-in: slow input generation)
-    salp = None
-    if args.salpeter and rank == 0:
-        salp = salpeter_bench(nb, torch, dev, sptr, stream)
-
-    # ---- centrally concentrated models: King W0 = 6 and 9, N = 16384, to t = 1/4
-    king = None
-    if args.king and rank == 0:
-        king = king_bench(nb, torch, dev, sptr, stream)
-
-    # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed, one evaluation per s
+    # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed and FP64, one evaluation per s
     sweep = None
     if args.sweep and rank == 0:
-        sweep = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz)
-        # mixed vs FP64 kernels on the same model at N = 131072 (an FP64 pass over N = 2^20
-        # would take a minute): interactions/s per s, both autotuned
-        sl = (1, 64, 1024, 16384)
-        mx = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=131072, s_list=sl)
-        f64 = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=131072, s_list=sl,
-                          precision=nb.NB_PREC_FP64)
-        sweep["mixed_vs_fp64_n131072"] = [
-            {"s": a["s"], "mixed_interactions_per_s": a["interactions_per_s"],
-             "fp64_interactions_per_s": b["interactions_per_s"],
-             "speedup": a["interactions_per_s"] / b["interactions_per_s"]} for a, b in zip(mx["points"], f64["points"])]
+        mx = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz)
+        f64 = force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, s_list=(1, 64, 1024, 16384), autotune=False,
+                          precision=nb.NB_PREC_FP64, reps=2)
+        sweep = {"workload": mx["workload"], "l2": mx["l2"],
+                 "mixed": [{"s": p["s"], "ms": _r(p["ms"]), "frac_fp32": _r(p["frac_fp32_peak"], 3),
+                            "roof": p.get("roof_bound"), "roof_frac": _r(p.get("roof_frac"), 3)}
+                           for p in mx["points"]],
+                 "fp64": [{"s": q["s"], "ms": _r(q["ms"]), "mixed_over_fp64": _r(q["ms"] / p["ms"], 3)}
+                          for p, q in zip(mx["points"], f64["points"])]}
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
-    cpu = None
+    model = timing_model(nb, torch, dev, stream) if (args.model and rank == 0) else None
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only); the force errors against the oracle on
+    # sampled particles of each workload's own state are taken in the same leg
+    cpu, ferr = None, None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
         oracle.build()
@@ -407,9 +434,11 @@ def main_gpu(args):
                "kind": "oracle", "sample": f"init (s=N pass) + {r['block_steps']} block steps to "
                                           f"t={args.ref_t_end} of the same N=16384 Plummer run "
                                           f"({r['seconds']:.1f} s); host {cpu_model()}"}
+        ferr = force_error_report(nb, oracle, nth, sptr, local)
 
     c.close()
     if rank == 0:
+        g2 = golden_energy(2)
         line = {
             "metric": "force+jerk interactions/s", "value": value, "unit": "interactions/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -418,17 +447,21 @@ def main_gpu(args):
             "data": "synthetic (seeded Plummer sphere, N-body units)",
             "config": dict(WORKLOAD, l2="flushed (256 MB write) before every timed step",
                            parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
-            "block_steps_per_s": dist_sum(bsteps * args.steps, dev) / (total_ms / 1e3),
-            "block_steps": bsteps, "abs_dE_over_E": dE, "block_size_hist": size_hist(st),
             "gpu_launches": launches * args.steps,
             "clocks": clk,
-            "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": "interactions/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / len(e2e_ms)},
-            "fp64_gpu": fp64,
-            "ensemble": ens, "salpeter": salp, "king": king,
-            "force_sweep": sweep,
             "cpu_baseline": cpu,
+            "roofline": roofline,
+            "block_steps": bsteps,
+            "block_steps_per_s": dist_sum(bsteps * args.steps, dev) / (total_ms / 1e3),
+            "abs_dE_over_E": dE,
+            "oracle_abs_dE_over_E": g2["abs_dE_over_E"] if g2 else None,
+            "engine": engine,
+            "king": king,
+            "force_sweep": sweep,
+            "ensemble": ens, "salpeter": salp, "fp64_gpu": fp64, "timing_model": model,
+            "force_error": ferr,
         }
         print(json.dumps(line))
     return 0
@@ -439,27 +472,85 @@ def size_hist(st):
     return {str(1 << b): int(c) for b, c in enumerate(st["size_hist"]) if c}
 
 
-def force_traffic():
-    """Per-launch DRAM traffic of the force kernel on this workload, from the committed ncu
-    summary, or None when the kernel sources have changed since it was taken."""
+def force_traffic(mean_s):
+    """DRAM bytes per force launch at the mean block size mean_s, from the committed ncu figures
+    (profiles/force_traffic.json: per-launch read + write bytes at a few block sizes of this
+    workload, fitted as a + b s), or None when the kernel sources have changed since."""
     import hashlib
-    root = os.path.dirname(os.path.abspath(__file__))
-    prof = os.path.join(root, "profiles", "force_traffic_plummer_n16384_t1over64.md")
-    srcs = ["nb_force.cu", "nb_pair.cuh", "nb_internal.cuh"]
+    path = os.path.join(ROOT, "profiles", "force_traffic.json")
     try:
-        text = open(prof).read()
+        with open(path) as f:
+            rec = json.load(f)
         h = hashlib.sha256()
-        for f in srcs:
-            with open(os.path.join(root, "paper_0711_0643_gb300", "csrc", f), "rb") as fh:
+        for name in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_0711_0643_gb300", "csrc", name), "rb") as fh:
                 h.update(fh.read())
-        if h.hexdigest() not in text:
+        if h.hexdigest() != rec["sha256"]:
             return None
-        for line in text.splitlines():
-            if line.startswith("traffic_bytes_per_launch:"):
-                return float(line.split(":")[1])
-    except OSError:
+        return rec["fit"]["a_bytes"] + rec["fit"]["b_bytes_per_s"] * mean_s
+    except (OSError, KeyError, ValueError):
         return None
-    return None
+
+
+def _condition_scales(m, xp, vp, eps2, idx, chunk=8):
+    """A_i = sum m_j/(r^2+eps^2) and K_i = sum m_j(|w|/(r^2+eps^2)^1.5 + 3|r.w||r|/(r^2+eps^2)^2.5),
+    j != i: the sizes the sums would have without cancellation (error normalisation)."""
+    A = np.zeros(idx.size)
+    K = np.zeros(idx.size)
+    for q0 in range(0, idx.size, chunk):
+        ii = idx[q0:q0 + chunk]
+        r = xp[None, :, :] - xp[ii][:, None, :]
+        w = vp[None, :, :] - vp[ii][:, None, :]
+        rr = np.einsum("ijk,ijk->ij", r, r)
+        d2 = rr + eps2
+        wn = np.sqrt(np.einsum("ijk,ijk->ij", w, w))
+        rw = np.abs(np.einsum("ijk,ijk->ij", r, w))
+        mask = np.ones_like(d2, dtype=bool)
+        mask[np.arange(ii.size), ii] = False
+        with np.errstate(divide="ignore", invalid="ignore"):
+            A[q0:q0 + chunk] = np.where(mask, m[None, :] / d2, 0.0).sum(1)
+            K[q0:q0 + chunk] = np.where(mask, m[None, :] * (wn / d2 ** 1.5 + 3 * rw * np.sqrt(rr) / d2 ** 2.5),
+                                        0.0).sum(1)
+    return A, K
+
+
+def force_error_report(nb, oracle, nth, sptr, local):
+    """Force and jerk error of the mixed path against the FP64 oracle, per workload, on sampled
+    active particles of the GPU's own predicted state (the oracle summing over all N j):
+    condition-scaled e_a = |da|/A_i, e_k = |dk|/K_i, forward ea_f, ek_f and phi's forward error,
+    each as [max, p99, median]; with the condition numbers kappa at the worst forward errors."""
+    import ics
+    out = {}
+    cases = [("c2_t0", ics.config(2), 256, 0), ("c2_step400", ics.config(2), 256, 400),
+             ("c3_t0", ics.config(3), 256, 0), ("c5_t0", ics.config(5), 256, 0)]
+    for name, snap, ns, steps in cases:
+        c = nb.Context(precision=nb.NB_PREC_MIXED, device=local, stream=sptr)
+        c.init(snap)
+        for _ in range(steps):
+            nb.nb_step(c.ctx)
+        if steps:
+            tn, s = nb.nb_next_block(c.ctx)
+            idx = nb.nb_get_active(c.ctx, s)
+            nb.nb_predict(c.ctx, tn)
+        else:
+            nb.nb_predict(c.ctx, 0.0)
+            idx = np.sort(np.argsort(ics.SplitMix64(ics.BASE_SEED + 900).uniform(snap.n))[:ns]).astype(np.int32)
+        xp, vp = nb.nb_get_predicted(c.ctx, snap.n)
+        a, k, phi = nb.nb_force_jerk(c.ctx, idx)
+        c.close()
+        pos = np.unique(np.linspace(0, idx.size - 1, min(idx.size, ns)).astype(np.int64))
+        sample = idx[pos]
+        ar, kr, pr = oracle.force(snap.m, xp, vp, snap.eps2, sample, nthreads=nth)
+        A, K = _condition_scales(snap.m, xp, vp, snap.eps2, sample, chunk=max(1, (1 << 22) // snap.n))
+        da = np.linalg.norm(a[pos] - ar, axis=1)
+        dk = np.linalg.norm(k[pos] - kr, axis=1)
+        na, nk = np.linalg.norm(ar, axis=1), np.linalg.norm(kr, axis=1)
+        eaf, ekf = da / na, dk / nk
+        out[name] = {"n": snap.n, "s": int(idx.size), "sampled": int(sample.size),
+                     "ea": _stats3(da / A), "ek": _stats3(dk / K), "ep": _stats3(np.abs(phi[pos] - pr) / np.abs(pr)),
+                     "ea_f": _stats3(eaf), "ek_f": _stats3(ekf),
+                     "kappa_at_worst": [_r(float((A / na)[np.argmax(eaf)]), 3), _r(float((K / nk)[np.argmax(ekf)]), 3)]}
+    return out
 
 
 def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
@@ -495,14 +586,13 @@ def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
     init_s = e0.elapsed_time(e1) / 1e3
     dE = np.abs(E1 - E0) / np.abs(E0)
     total_inter = float(inter.sum()) + float(np.sum(np.diff(off).astype(float) ** 2))
-    return {"workload": f"{nc} Plummer clusters, N log-uniform in [{n_lo}, {n_hi}] (total {int(off[-1])}), eps=4/N, "
-                        f"t=0->{T_END}, one persistent cluster launch",
-            "run_ms": run_s * 1e3, "init_ms": init_s * 1e3,
-            "interactions_per_s": total_inter / (run_s + init_s),
-            "block_steps_per_s": float(bs.sum()) / run_s, "block_steps": int(bs.sum()),
-            "worst_abs_dE_over_E": float(dE.max()), "median_abs_dE_over_E": float(np.median(dE)),
-            "worst_member": {"index": int(np.argmax(dE)), "n": int(np.diff(off)[int(np.argmax(dE))])},
-            "n_min": int(np.diff(off).min()), "n_max": int(np.diff(off).max())}
+    return {"workload": f"{nc} Plummer clusters N in [{int(np.diff(off).min())}, {int(np.diff(off).max())}] "
+                        f"(total {int(off[-1])}), eps=4/N, t=0->{T_END}",
+            "run_ms": _r(run_s * 1e3), "init_ms": _r(init_s * 1e3),
+            "ips": _r(total_inter / (run_s + init_s)), "tflops": _r(60 * total_inter / (run_s + init_s) / 1e12, 3),
+            "bsps": _r(float(bs.sum()) / run_s), "block_steps": int(bs.sum()),
+            "worst_dE": _r(float(dE.max()), 5), "median_dE": _r(float(np.median(dE)), 3),
+            "worst_member": [int(np.argmax(dE)), int(np.diff(off)[int(np.argmax(dE))])]}
 
 
 def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
@@ -533,10 +623,12 @@ def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
     c.close()
     sec = e0.elapsed_time(e1) / 1e3
     inter = st["interactions"] + float(n) * n
-    return {"workload": f"plummer N={n} Salpeter masses [0.1, 100] slope -2.35, eps=1/4096, t=0->{t_end}, mixed",
-            "ms": sec * 1e3, "interactions_per_s": inter / sec, "block_steps": st["block_steps"],
-            "block_steps_per_s": st["block_steps"] / sec, "mean_active": st["particle_steps"] / max(st["block_steps"], 1),
-            "abs_dE_over_E": abs(E1 - E0) / abs(E0), "block_size_hist": size_hist(st)}
+    g3 = golden_energy(3)
+    return {"workload": f"plummer N={n} Salpeter [0.1, 100] -2.35, eps=1/4096, t=0->{t_end}, mixed",
+            "ms": _r(sec * 1e3), "ips": _r(inter / sec), "block_steps": st["block_steps"],
+            "bsps": _r(st["block_steps"] / sec), "mean_s": _r(st["particle_steps"] / max(st["block_steps"], 1)),
+            "dE": _r(abs(E1 - E0) / abs(E0)), "oracle_dE": _r(g3["abs_dE_over_E"]) if g3 else None,
+            "oracle_block_steps": g3["block_steps"] if g3 else None}
 
 
 def king_bench(nb, torch, dev, sptr, stream, n=16384, t_end=0.25):
@@ -566,16 +658,16 @@ def king_bench(nb, torch, dev, sptr, stream, n=16384, t_end=0.25):
         st = nb.nb_stats(c.ctx)
         c.close()
         sec = e0.elapsed_time(e1) / 1e3
-        out.append({"workload": f"king W0={w0:g} N={n} eps=1/1024, t=0->{t_end}, mixed", "ms": sec * 1e3,
-                    "interactions_per_s": (st["interactions"] + float(n) * n) / sec,
-                    "block_steps": st["block_steps"], "block_steps_per_s": st["block_steps"] / sec,
-                    "mean_active": st["particle_steps"] / max(st["block_steps"], 1),
-                    "abs_dE_over_E": abs(E1 - E0) / abs(E0), "block_size_hist": size_hist(st)})
+        out.append({"w0": w0, "n": n, "t_end": t_end, "ms": _r(sec * 1e3),
+                    "ips": _r((st["interactions"] + float(n) * n) / sec),
+                    "block_steps": st["block_steps"], "bsps": _r(st["block_steps"] / sec),
+                    "mean_s": _r(st["particle_steps"] / max(st["block_steps"], 1)),
+                    "dE": _r(abs(E1 - E0) / abs(E0))})
     return out
 
 
 def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=None, autotune=True,
-                precision=None):
+                precision=None, reps=None):
     """King W0 = 6, N = 1,048,576, eps = 1e-3: one mixed force evaluation per active-set
     size s in {1, 64, 1024, 16384, N} (active = first s of a seeded permutation, ascending),
     split factor autotuned; interactions/s and FP32 roofline fraction per s. Each point is
@@ -607,14 +699,14 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
         a_d = torch.empty((s, 3), dtype=torch.float64, device=dev)
         k_d = torch.empty_like(a_d)
         p_d = torch.empty(s, dtype=torch.float64, device=dev)
-        for _ in range(3):
+        for _ in range(3 if reps is None else 1):
             nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
         # each timed call starts with L2 flushed (the j-records, 40 MB at N = 2^20, would
         # otherwise stay in the 129 MB L2 between calls): median of single calls
-        reps = 9 if s < n else 2
+        nrep = reps if reps is not None else (9 if s < n else 2)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         times = []
-        for _ in range(reps):
+        for _ in range(nrep):
             l2_flush.zero_()
             torch.cuda.synchronize(dev)
             e0.record(stream)
@@ -661,8 +753,9 @@ def main(argv=None):
                     help="Plummer N=65536 with Salpeter masses to t=0.5 (default on; ~15 s of input generation)")
     ap.add_argument("--king", action=argparse.BooleanOptionalAction, default=True,
                     help="King W0 = 6 and 9, N = 16384, to t = 1/4 (default on)")
-    ap.add_argument("--model", action="store_true",
-                    help="fit the per-block-step timing model (select, predict, force, correct) and print it")
+    ap.add_argument("--model", action=argparse.BooleanOptionalAction, default=True,
+                    help="refit the per-block-step timing model on this GPU (default on)")
+    ap.add_argument("--model-only", action="store_true", help="run only the timing model and print it")
     ap.add_argument("--salpeter-only", action="store_true",
                     help="run only the Salpeter workload and print it")
     ap.add_argument("--ensemble-only", action="store_true",
@@ -689,7 +782,7 @@ def main(argv=None):
         return main_ensemble(args)
     if args.salpeter_only:
         return main_salpeter(args)
-    if args.model:
+    if args.model_only:
         return main_model(args)
     return main_gpu(args)
 
@@ -710,13 +803,76 @@ def main_ensemble(args):
     return 0
 
 
+def timing_model(nb, torch, dev, stream):
+    """The paper's timing model (Sect. 4.1: T = tau_pr N + tau_f N s / p + tau_cr s + communication)
+    refitted on this GPU, per block step and phase: selection and predictor a + b N, force
+    a + tau_f s N, corrector a + tau_cr s (the four-kernel step), and the small-block engine's
+    whole step a + b N + c s N. Fitted by least squares to the phase totals of host-driven runs
+    (nb_run_timed, each phase bracketed by events; ~3.7 us of the gate in every a) of Plummer models
+    N = 1024 .. 65536 (eps = 4/N, t = 0 -> 1/16, autotuned); the graph loop's measured time (nb_run)
+    is printed beside the sum of the fitted phase times of the same run."""
+    import ics
+    rows = []
+    for n in (1024, 2048, 4096, 8192, 16384, 32768, 65536):
+        snap = ics.plummer(n, seed=ics.BASE_SEED + 70 + n.bit_length(), eps=4.0 / n,
+                           scale="continuum" if n > 16384 else "auto")
+        c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=stream.cuda_stream)
+        c.init(snap)
+        nb.nb_autotune(c.ctx)
+        c.init(snap)
+        tm = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
+        c.init(snap)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        nb.nb_run(c.ctx, 1.0 / 16)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st = nb.nb_stats(c.ctx)
+        c.close()
+        rows.append({"n": n, "tm": tm, "run_us": 1e3 * e0.elapsed_time(e1), "steps": st["block_steps"]})
+    fit = {}
+
+    def lsq(cols, y):
+        coef, *_ = np.linalg.lstsq(np.array(cols, dtype=float), np.array(y, dtype=float), rcond=None)
+        return [float(x) for x in coef]
+
+    k4 = [r["tm"]["force_launches"] for r in rows]
+    ns = [r["n"] for r in rows]
+    fI = [r["tm"]["force_interactions"] for r in rows]
+    for ph in ("select", "predict"):
+        fit[ph] = lsq([(k, k * n) for k, n in zip(k4, ns)], [1e3 * r["tm"]["phase_ms"][ph] for r in rows])
+    fit["force"] = lsq([(k, i) for k, i in zip(k4, fI)], [1e3 * r["tm"]["phase_ms"]["force"] for r in rows])
+    fit["correct"] = lsq([(k, i / n) for k, i, n in zip(k4, fI, ns)], [1e3 * r["tm"]["phase_ms"]["correct"]
+                                                                       for r in rows])
+    ke = [r["tm"]["engine_steps"] for r in rows]
+    used = [q for q, k in enumerate(ke) if k > 0]
+    if len(used) >= 3:
+        fit["engine"] = lsq([(ke[q], ke[q] * ns[q], rows[q]["tm"]["engine_interactions"]) for q in used],
+                            [1e3 * rows[q]["tm"]["phase_ms"]["engine"] for q in used])
+    runs = []
+    for r, k, n, i in zip(rows, k4, ns, fI):
+        t = (fit["select"][0] + fit["predict"][0] + fit["force"][0] + fit["correct"][0]) * k
+        t += (fit["select"][1] + fit["predict"][1]) * k * n + fit["force"][1] * i + fit["correct"][1] * i / n
+        if "engine" in fit and r["tm"]["engine_steps"]:
+            e = r["tm"]["engine_steps"]
+            t += fit["engine"][0] * e + fit["engine"][1] * e * n + fit["engine"][2] * r["tm"]["engine_interactions"]
+        runs.append({"n": n, "steps": r["steps"], "engine_steps": r["tm"]["engine_steps"],
+                     "run_ms": _r(r["run_us"] / 1e3), "model_ms": _r(t / 1e3), "run_over_model": _r(r["run_us"] / t, 3)})
+    # units: a in us per step; b in ns per particle (select, predict), tau in ps per
+    # interaction (force, engine), tau_cr in ns per active particle
+    out = {"select": [_r(fit["select"][0], 3), _r(1e3 * fit["select"][1], 3)],
+           "predict": [_r(fit["predict"][0], 3), _r(1e3 * fit["predict"][1], 3)],
+           "force": [_r(fit["force"][0], 3), _r(1e6 * fit["force"][1], 3)],
+           "correct": [_r(fit["correct"][0], 3), _r(1e3 * fit["correct"][1], 3)],
+           "units": "[a us/step, b ns/particle | tau_f ps/interaction | tau_cr ns/active]", "runs": runs}
+    if "engine" in fit:
+        out["engine"] = [_r(fit["engine"][0], 3), _r(1e3 * fit["engine"][1], 3), _r(1e6 * fit["engine"][2], 3)]
+    return out
+
+
 def main_model(args):
-    """The paper's timing model (Sect. 4.1) refitted on this GPU: per block step
-    T = [a_sel + b_sel N] + [a_pr + b_pr N] + [a_f + tau_f s N] + [a_cr + tau_cr s], fitted by
-    least squares to the phase totals of host-driven runs (nb_run_timed, each phase bracketed
-    by events) of Plummer models N = 1024 .. 65536 (eps = 4/N, t = 0 -> 1/16, autotuned); the
-    fitted model then predicts every graph-loop run (nb_run) from its block-step count and
-    sum of s, next to the measured time. Printed as one JSON line (not a bench line)."""
+    """Only the timing model, printed as one JSON line (not a bench line)."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -726,58 +882,7 @@ def main_model(args):
     pkg.build()
     from paper_0711_0643_gb300 import nbody as nb
     nb.load()
-    import ics
-    gate_us = None
-    rows = []
-    for n in (1024, 2048, 4096, 8192, 16384, 32768, 65536):
-        snap = ics.plummer(n, seed=ics.BASE_SEED + 70 + n.bit_length(), eps=4.0 / n,
-                           scale="continuum" if n > 16384 else "auto")
-        c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=stream.cuda_stream)
-        c.init(snap)
-        nb.nb_autotune(c.ctx)
-        c.init(snap)
-        _, nl, _, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
-        st = nb.nb_stats(c.ctx)
-        c.init(snap)
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        nb.nb_run(c.ctx, 1.0 / 16)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        st2 = nb.nb_stats(c.ctx)
-        c.close()
-        rows.append({"n": n, "steps": st["block_steps"], "sum_s": st["particle_steps"],
-                     "phase_us": {k: 1e3 * v for k, v in ph.items()},
-                     "run_steps": st2["block_steps"], "run_sum_s": st2["particle_steps"],
-                     "run_us": 1e3 * e0.elapsed_time(e1)})
-    # every phase total of run r: steps_r * a + (N_r * steps_r or sum(s N) or sum s) * b
-    A = {"select": [], "predict": [], "force": [], "correct": []}
-    y = {k: [] for k in A}
-    for r in rows:
-        n, k, ss = r["n"], r["steps"], r["sum_s"]
-        A["select"].append((k, k * n)); A["predict"].append((k, k * n))
-        A["force"].append((k, ss * n)); A["correct"].append((k, ss))
-        for key in A:
-            y[key].append(r["phase_us"][key])
-    fit = {}
-    for key in A:
-        coef, *_ = np.linalg.lstsq(np.array(A[key], dtype=float), np.array(y[key]), rcond=None)
-        fit[key] = {"a_us": float(coef[0]), "b_us": float(coef[1])}
-    # the phases above include a gate (delay kernel + events) each; the graph loop has none:
-    # predict the graph loop's time with the fixed terms less the measured gate overhead
-    for r in rows:
-        k, ss, n = r["run_steps"], r["run_sum_s"], r["n"]
-        t = 0.0
-        for key, f in fit.items():
-            lin = {"select": k * n, "predict": k * n, "force": ss * n, "correct": ss}[key]
-            t += f["a_us"] * k + f["b_us"] * lin
-        r["model_phase_sum_us"] = t
-        r["ratio_measured_to_phase_sum"] = r["run_us"] / t
-    out = {"model": "per block step T = sum over phases of (a + b x work), work = N (select, predict), "
-                     "s N (force), s (correct); fitted to nb_run_timed phase totals",
-           "fit": fit, "runs": rows}
-    print(json.dumps(out))
+    print(json.dumps(timing_model(nb, torch, dev, stream)))
     return 0
 
 

@@ -76,6 +76,9 @@ typedef struct {
     double interactions;
     double t_now;                         /* largest t_i */
     int64_t size_hist[NB_SIZE_BUCKETS];   /* block steps per block-size bucket */
+    int64_t loop_slots;                   /* step slots the nb_run loop has run (each slot: the
+                                             engine if on, the selection, predictor, force and
+                                             corrector kernels; slots past t_end run as no-ops) */
 } nb_counters;
 
 /* Full particle state; arrays of length n ([n][3] for vectors), caller-owned. */
@@ -201,18 +204,24 @@ nb_status nb_step(nb_ctx *ctx);
  * One call runs at most 2^22 block steps (then NB_ERR_STATE, "block-step cap"). */
 nb_status nb_run(nb_ctx *ctx, double t_end);
 
+/* Timings of nb_run_timed. */
+typedef struct {
+    double force_ms;              /* summed force-kernel time (blocks the engine does not take) */
+    double phase_ms[5];           /* select, predict, force, correct, engine (phases != 0; else only
+                                     [2] and [4]) */
+    int64_t force_launches;       /* block steps done by the four-kernel step */
+    int64_t engine_steps;         /* block steps done by the small-block engine */
+    double force_interactions;    /* sum of s N over the force launches */
+    double engine_interactions;   /* sum of s N over the engine's steps */
+} nb_timing;
+
 /* Same trajectory as nb_run, driven from the host one block step at a time, with
  * CUDA events around every force launch and every engine step (a short,
  * time-bounded wait kernel precedes each start event so that it is processed
- * only once the launch is queued). *force_ms = summed time of the force kernel
- * (blocks the engine does not take), *launches = number of those force
- * launches, *engine_steps = block steps done by the small-block engine.
- * phase_ms: NULL, or 5 doubles receiving the summed times of the select,
- * predict, force, correct kernels and of the engine's steps, each bracketed the
- * same way (the select that ends the loop is not counted). Every pointer may
- * be NULL. For measurement; slower than nb_run. */
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms,
-                       int64_t *engine_steps);
+ * only once the launch is queued); phases != 0 brackets the select, predict and
+ * correct kernels the same way (the select that ends the loop is not counted).
+ * out may be NULL. For measurement; slower than nb_run. */
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, int32_t phases, nb_timing *out);
 
 /* Small-block engine (mixed precision): the largest block s_max (<= 256) that
  * nb_step / nb_run / nb_run_timed run inside the one-cluster engine kernel
@@ -221,9 +230,11 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
  * particles). The paper has the step of Sect. 2.1 only; the engine is the same
  * step with the j-split of Sect. 3 across the cluster's CTAs and the partial
  * forces summed in a fixed order. s_max = 0 switches it off, -1 restores the
- * default (the largest s with s N <= 2^22, at least 16, at most 256). Without a
- * co-schedulable 16- or 8-CTA cluster, or above 4096 particles per CTA
- * (n > 65536 on 16-CTA clusters), there is no engine.
+ * default: for n <= 4096 the largest s with s n <= 2^19 (at least 16, at most
+ * 256); above 4096 particles off (there its steps cost about as much as the
+ * four-kernel steps on this GPU). Without a co-schedulable 16- or 8-CTA cluster,
+ * or above 1024 particles per CTA (n > 16384 on 16-CTA clusters), there is no
+ * engine.
  * Errors: NB_ERR_ARG (s_max out of range, or s_max > 0 in FP64 precision).
  * nb_get_engine: the largest block the engine takes for the loaded system
  * (0 = no engine) and its cluster size; either pointer may be NULL. */

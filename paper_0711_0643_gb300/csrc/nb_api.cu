@@ -110,6 +110,7 @@ namespace {
 constexpr int64_t kMaxRunSteps = int64_t(1) << 22;   // block steps per nb_run call
 constexpr int kRunUnroll = 16;                         // block steps per pass of the nb_run while node
 constexpr int kRunUnrollEngine = 4;                    // the same with the engine (each runs many steps)
+constexpr int64_t kEngDefaultMaxN = 4096;              // the engine is on by default up to this many particles
 static_assert(kRunUnroll % 2 == 0 && kRunUnrollEngine % 2 == 0,
               "the loop's steps alternate two block-time slots");
 
@@ -218,9 +219,14 @@ cudaError_t launch_force_ctx(nb_ctx *c)
 // The engine's default largest block: its force phase runs on the cluster's
 // SMs only, so it takes blocks whose s N is small (2^19 pair evaluations: the
 // force phase then takes a few microseconds, below the full path's per-step
-// overhead).
+// overhead). Above 4096 particles it is off by default: measured on this GPU, its
+// steps (~16 us at N = 16384, mostly the FP64 corrector chain and the barrier-
+// separated phases on 16 SMs) plus a launch each time a large block interrupts
+// it cost as much as the four-kernel steps (Plummer N = 16384 to t = 1: 686 vs
+// 674 ms), while at N = 1024 it saves a fifth (58 vs 75 ms).
 int32_t default_engine_smax(int64_t n)
 {
+    if (n > kEngDefaultMaxN) return 0;
     int64_t s = (int64_t(1) << 19) / std::max<int64_t>(n, 1);
     s = std::max<int64_t>(16, std::min<int64_t>(s, kEngMaxS));
     return (int32_t)s;
@@ -404,7 +410,7 @@ nb_status init_forces(nb_ctx *ctx)
     CK(launch_force_ctx(ctx));
     CK(launch_init_steps(A, ctx->stream));
     CK(cudaMemsetAsync(ctx->counters, 0, 2 * sizeof(int64_t), ctx->stream));
-    CK(cudaMemsetAsync(ctx->counters + 3, 0, NB_SIZE_BUCKETS * sizeof(int64_t), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters + 3, 0, (NB_SIZE_BUCKETS + 1) * sizeof(int64_t), ctx->stream));
     CK(cudaMemsetAsync(ctx->interactions, 0, sizeof(double), ctx->stream));
     ctx->have_state = true;
     ctx->forces_pending = false;
@@ -597,13 +603,13 @@ nb_status nb_create(nb_ctx **out, const nb_config *cfg, void *stream)
               dalloc(&ctx->t_slot, 2) == cudaSuccess &&
               dalloc(&ctx->t_end, 1) == cudaSuccess && dalloc(&ctx->split_used, 1) == cudaSuccess &&
               dalloc(&ctx->tune_dev, 1) == cudaSuccess && dalloc(&ctx->status, 1) == cudaSuccess &&
-              dalloc(&ctx->counters, 3 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
+              dalloc(&ctx->counters, 4 + NB_SIZE_BUCKETS) == cudaSuccess && dalloc(&ctx->interactions, 1) == cudaSuccess &&
               dalloc(&ctx->en_out, 2) == cudaSuccess && dalloc(&ctx->t_eng, 1) == cudaSuccess;
     if (!ok) {
         nb_destroy(ctx);
         return NB_ERR_CUDA;
     }
-    int64_t init_counters[3 + NB_SIZE_BUCKETS] = {0, 0, int64_t(1) << 40};
+    int64_t init_counters[4 + NB_SIZE_BUCKETS] = {0, 0, int64_t(1) << 40};
     int32_t one = 1;
     bool ok2 = cudaMemset(ctx->status, 0, sizeof(int32_t)) == cudaSuccess &&
                cudaMemcpy(ctx->counters, init_counters, sizeof init_counters, cudaMemcpyHostToDevice) ==
@@ -985,14 +991,14 @@ nb_status nb_run(nb_ctx *ctx, double t_end)
     return sync_status(ctx);
 }
 
-nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *launches, double *phase_ms,
-                       int64_t *engine_steps)
+nb_status nb_run_timed(nb_ctx *ctx, double t_end, int32_t phases_on, nb_timing *out)
 {
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!std::isfinite(t_end)) return fail(ctx, NB_ERR_ARG, "t_end must be finite");
     StepArgs A = step_args(ctx);
-    const bool phases = phase_ms != nullptr;
+    const bool phases = phases_on != 0;
+    double inter_f = 0.0, inter_e = 0.0;
     const bool eng = engine_on(ctx);
     const int32_t smax = eng ? engine_args(ctx, A, nullptr, nullptr, nullptr, false, 1).s_max : 0;
     int64_t nl = 0, ne = 0;
@@ -1044,6 +1050,7 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
             CK(elapsed(4));
             if (left == 0) {
                 ++ne;
+                inter_e += (double)ss * (double)ctx->n;
                 if (stw) break;
                 continue;
             }
@@ -1066,13 +1073,17 @@ nb_status nb_run_timed(nb_ctx *ctx, double t_end, double *force_ms, int64_t *lau
             CK(elapsed(3));
         }
         ++nl;
+        inter_f += (double)ss * (double)ctx->n;
         if (stw) break;
     }
-    if (force_ms) *force_ms = total[2];
-    if (launches) *launches = nl;
-    if (engine_steps) *engine_steps = ne;
-    if (phases)
-        for (int q = 0; q < 5; ++q) phase_ms[q] = total[q];
+    if (out) {
+        out->force_ms = total[2];
+        for (int q = 0; q < 5; ++q) out->phase_ms[q] = total[q];
+        out->force_launches = nl;
+        out->engine_steps = ne;
+        out->force_interactions = inter_f;
+        out->engine_interactions = inter_e;
+    }
     ctx->forces_pending = false;
     ctx->block_s = -1;
     return sync_status(ctx);
@@ -1159,7 +1170,7 @@ nb_status nb_stats(nb_ctx *ctx, nb_counters *out)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     if (!out) return fail(ctx, NB_ERR_ARG, "null counters");
-    int64_t c[3 + NB_SIZE_BUCKETS];
+    int64_t c[4 + NB_SIZE_BUCKETS];
     double inter;
     CK(cudaMemcpyAsync(c, ctx->counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&inter, ctx->interactions, sizeof inter, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1171,6 +1182,7 @@ nb_status nb_stats(nb_ctx *ctx, nb_counters *out)
     out->interactions = inter;
     out->t_now = *std::max_element(t.begin(), t.end());
     for (int b = 0; b < NB_SIZE_BUCKETS; ++b) out->size_hist[b] = c[3 + b];
+    out->loop_slots = c[3 + NB_SIZE_BUCKETS];
     return NB_OK;
 }
 

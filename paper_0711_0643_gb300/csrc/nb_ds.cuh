@@ -57,11 +57,11 @@ __device__ __forceinline__ DS ds_scale2(DS x, float pow2) { return DS{x.hi * pow
 // Hermite predictor of one particle in double-single for the mixed j-record:
 // xp = x + d (v + d (a/2 + d k/6)) per component (the same polynomial as
 // x + v d + a d^2/2 + k d^3/6, in Horner form), vp = v + d (a + d k/2) in FP32.
-// X, V, A, K: the particle's double-single x, v, a, k per component.
-__device__ __forceinline__ void ds_predict_vals(const float2 *X, const float2 *V, const float2 *A, const float2 *K,
-                                                double d64, float4 &hi, float4 &lo, float4 &vel, float m)
+// X, V, A, K: the particle's double-single x, v, a, k per component; d: the
+// time since the particle's own time, as a double-single.
+__device__ __forceinline__ void ds_predict_ds(const float2 *X, const float2 *V, const float2 *A, const float2 *K, DS d,
+                                              float4 &hi, float4 &lo, float4 &vel, float m)
 {
-    const DS d = ds_split(d64);
     const DS sixth = {0.166666671633720398f, -4.967053879e-09f};   // 1/6 = hi + lo to ~2^-53
     const DS d6 = ds_mul(d, sixth);
     float ph[3], pl[3], pv[3];
@@ -82,6 +82,16 @@ __device__ __forceinline__ void ds_predict_vals(const float2 *X, const float2 *V
     lo = make_float4(pl[0], pl[1], pl[2], 0.f);
     vel = make_float4(pv[0], pv[1], pv[2], 0.f);
 }
+
+__device__ __forceinline__ void ds_predict_vals(const float2 *X, const float2 *V, const float2 *A, const float2 *K,
+                                                double d64, float4 &hi, float4 &lo, float4 &vel, float m)
+{
+    ds_predict_ds(X, V, A, K, ds_split(d64), hi, lo, vel, m);
+}
+
+// (hi, lo) - (hi2, lo2) renormalised: the difference of two double-single times on
+// the FP32 pipe (a two-sum of the high parts, the low parts added to its error)
+__device__ __forceinline__ DS ds_sub(DS x, DS y) { return ds_add(x, DS{-y.hi, -y.lo}); }
 
 // The same from the state arrays x2, v2, a2, k2 ([3][np] float2 (hi, lo)) of particle i.
 __device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, const float2 *a2, const float2 *k2,

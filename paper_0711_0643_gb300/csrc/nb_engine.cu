@@ -15,18 +15,18 @@
 //   1. finds its chunk's members of the block (keys t + dt equal to the block
 //      time; ascending) and the smallest other key; pushes its member count into
 //      every CTA's shared memory;
-//   2. predicts its whole chunk to the block time into pair records in shared
-//      memory (the double-single predictor of the full path, same bits) and
-//      pushes its members' predicted records to every CTA;
+//   2. predicts its members to the block time (the double-single predictor of
+//      the full path, same bits) and pushes their records to every CTA;
 //   -- cluster barrier: every CTA knows every chunk's count, hence the block
 //      size s and each chunk's offset; if the block is too large for the engine
 //      (s > s_max, or more than kEngCap members in one chunk), past t_end, or
 //      the step budget is used up, every CTA stops here, leaving the block time
 //      for the full path;
-//   3. reads all s members' records from their owners (distributed shared
-//      memory) and sums the s forces over its own chunk only (packed f32x2 pair
-//      arithmetic, two-sum folds and reductions: the force kernel's arithmetic),
-//      keeping the (hi, lo) partial sums in its shared memory;
+//   3. predicts its whole chunk into pair records in shared memory, orders the
+//      s members it received, and sums their forces over its own chunk only
+//      (packed f32x2 pair arithmetic, two-sum folds and reductions: the force
+//      kernel's arithmetic), pushing the (hi, lo) partial sums to each member's
+//      owner;
 //   -- cluster barrier;
 //   4. corrects its own members: four lanes per particle add the C partial sums
 //      in rank order (the paper's global sum of partial forces, in a fixed order)
@@ -37,7 +37,8 @@
 // Each CTA keeps its chunk's double-single state, times and keys in shared memory
 // for the whole launch (loaded once; the corrector updates its members' copies as
 // it writes the FP64 state), so the per-step selection and prediction read only
-// shared memory.
+// shared memory and run on the FP32 pipe (the time differences t_block - t_j in
+// double-single: FP64 is a narrow pipe on this part).
 // No software spin-wait exists: every branch is taken identically by all CTAs
 // (each decision uses values every CTA holds), so every CTA reaches every
 // barrier. Results are bitwise reproducible and do not depend on how many steps
@@ -63,6 +64,8 @@ constexpr int kEngThreads = 512;
 constexpr int kEngWarps = kEngThreads / 32;
 constexpr int kEngMaxC = 16;
 constexpr long long kInfBits = 0x7ff0000000000000LL;
+static_assert(kEngCap <= 8 * (kEngWarps - 1), "the last warp must hold no member (four lanes per member)");
+static_assert(kEngMaxC * kEngCap <= kEngThreads, "one thread per (rank, member) when pushing records");
 
 // predicted record of an active particle: (x_hi, y_hi, z_hi, index bits), (x_lo, y_lo, z_lo, 0), (vx, vy, vz, 0)
 struct __align__(16) IRec {
@@ -77,7 +80,9 @@ struct __align__(16) EngSmem {
     IRec ilist[kEngMaxS];                   // all members in block order (copied from the inbox)
     float2 part_in[kEngCap][kEngMaxC][8];   // [k][q]: rank q's partial sums (hi, lo) for this chunk's member k
     int2 qmap[kEngMaxS];                    // block position -> (owner rank, member index there)
+    IRec own_rec[kEngCap];                  // this chunk's members' predicted records
     int own_idx[kEngCap];                   // this chunk's members (particle indices, ascending)
+    int rank_base[kEngMaxC];                // block position of each rank's first member
     float2 red[kEngWarps][7];               // per-warp sums (blocks of up to 16)
     long long slot_min[kEngMaxC];           // written by rank q: the smallest key of its chunk after the step
     int slot_err[kEngMaxC];                 // written by rank q: its status bits of the step
@@ -113,7 +118,9 @@ __device__ __forceinline__ void push_part(cg::cluster_group &cluster, EngSmem *s
 
 // Partial sums of one member (predicted record ip, index gi) over pair records
 // [rb, re) of the chunk, lanes interleaved with stride TJ starting at lane tj.
-// MASK: the member lies in this chunk (its own pair is left out by index).
+// MASK: the member's own pair is left out by index (the engine always masks: one
+// instantiation per width keeps the kernel's code, and its instruction-cache
+// footprint, small).
 template <bool MASK, int TJ>
 __device__ __forceinline__ void sweep(const JPair *recs, int64_t j0, int rb, int re, int tj, const IPk &ip, int gi,
                                       float2 e2, Acc7 &hi, Acc7 &lo)
@@ -135,8 +142,8 @@ __device__ __forceinline__ void sweep(const JPair *recs, int64_t j0, int rb, int
     fold(hi, lo, p);
 }
 
-// Blocks of more than 16: TJ lanes per member, each CTA thread group takes
-// members in rounds; the group's lanes reduce with two-sums in a fixed order.
+// Blocks of more than 16: TJ lanes per member (TJ = 8), each CTA thread group
+// takes members in rounds; the group's lanes reduce with two-sums in a fixed order.
 template <int TJ>
 __device__ void force_groups(cg::cluster_group &cluster, EngSmem *sm, const JPair *recs, int64_t j0, int64_t j1,
                              int nrec, int s, float2 e2, int rank)
@@ -152,10 +159,7 @@ __device__ void force_groups(cg::cluster_group &cluster, EngSmem *sm, const JPai
         Acc7 hi, lo;
         zero(hi);
         zero(lo);
-        if (gi >= j0 && gi < j1)
-            sweep<true, TJ>(recs, j0, 0, nrec, tj, ip, gi, e2, hi, lo);
-        else
-            sweep<false, TJ>(recs, j0, 0, nrec, tj, ip, gi, e2, hi, lo);
+        sweep<true, TJ>(recs, j0, 0, nrec, tj, ip, gi, e2, hi, lo);
         ds_group_reduce7<TJ>(hi, lo);
         if (tj == 0 && q < s) push_part(cluster, sm, q, rank, hi, lo);
     }
@@ -167,10 +171,10 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
     EngSmem *sm = reinterpret_cast<EngSmem *>(smem_raw);
     JPair *recs = reinterpret_cast<JPair *>(smem_raw + sizeof(EngSmem));
     const int64_t ch = E.chunk;
-    // this chunk's double-single state [3][ch], times, keys and masses
+    // this chunk's double-single state [3][ch] and times, keys and masses
     float2 *cx = reinterpret_cast<float2 *>(recs + ch / 2);
     float2 *cv = cx + 3 * ch, *ca = cv + 3 * ch, *ck = ca + 3 * ch;
-    double *ct = reinterpret_cast<double *>(ck + 3 * ch);
+    float2 *ct = ck + 3 * ch;
     long long *ckey = reinterpret_cast<long long *>(ct + ch);
     float *cm = reinterpret_cast<float *>(ckey + ch);
     cg::cluster_group cluster = cg::this_cluster();
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             ca[c * ch + li] = real ? A.a2[c * np + i] : make_float2(0.f, 0.f);
             ck[c * ch + li] = real ? A.k2[c * np + i] : make_float2(0.f, 0.f);
         }
-        ct[li] = real ? A.t[i] : 0.0;
+        ct[li] = real ? rn_ds_pack(A.t[i]) : make_float2(0.f, 0.f);
         ckey[li] = real ? key[i] : kInfBits;
         cm[li] = real ? (float)A.m[i] : 0.f;
     }
@@ -219,6 +223,8 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
     bool waited = false;
     for (;;) {
         const double tbd = __longlong_as_double(tb);
+        const float2 tb2 = rn_ds_pack(tbd);   // the block time as a double-single
+        const DS tbs{tb2.x, tb2.y};
         if (!clean || steps >= budget || !(tb < kInfBits) || (E.check_end && !(tbd <= t_end))) break;
 
         // ---- 1. this chunk's members (keys == block time), ascending, and the smallest other key
@@ -250,26 +256,23 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         }
         const int hk = hits < kEngCap ? hits : kEngCap;
 
-        // ---- 2. predict the chunk into pair records from the shared-memory state,
-        // then push the members' records to every CTA
-        for (int64_t i = j0 + tid; i < j1; i += kEngThreads) {
+        // ---- 2. predict this chunk's members (the chunk itself only once the block is
+        // known to be taken) and push their records to every CTA
+        for (int q = tid; q < hk; q += kEngThreads) {
+            const int i = sm->own_idx[q];
             const int64_t li = i - j0;
-            if (i < n) {
-                float2 X[3], V[3], Ac[3], K[3];
+            float2 X[3], V[3], Ac[3], K[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    X[c] = cx[c * ch + li];
-                    V[c] = cv[c * ch + li];
-                    Ac[c] = ca[c * ch + li];
-                    K[c] = ck[c * ch + li];
-                }
-                float4 h, l, w;
-                ds_predict_vals(X, V, Ac, K, tbd - ct[li], h, l, w, cm[li]);
-                jrec_store(recs, li, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
-            } else {
-                const float far = (float)kPadPos;
-                jrec_store(recs, li, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < 3; ++c) {
+                X[c] = cx[c * ch + li];
+                V[c] = cv[c * ch + li];
+                Ac[c] = ca[c * ch + li];
+                K[c] = ck[c * ch + li];
             }
+            float4 h, l, w;
+            ds_predict_ds(X, V, Ac, K, ds_sub(tbs, DS{ct[li].x, ct[li].y}), h, l, w, cm[li]);
+            sm->own_rec[q] = IRec{make_float4(h.x, h.y, h.z, __int_as_float(i)), make_float4(l.x, l.y, l.z, 0.f),
+                                  make_float4(w.x, w.y, w.z, 0.f)};
         }
         // the corrector's FP64 state of this thread's member (four lanes per member),
         // in flight during the force phase; a quad past the members works on member 0
@@ -288,11 +291,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         if (tid < C) *cluster.map_shared_rank(&sm->slot_cnt[rank], tid) = hits;
         if (tid < hk * C) {
             const int k = tid / C, dst = tid % C;
-            const int i = sm->own_idx[k];
-            const IPart P = jrec_load(recs, i - j0);
-            *cluster.map_shared_rank(&sm->inbox[rank][k], dst) =
-                IRec{make_float4(P.xh, P.yh, P.zh, __int_as_float(i)), make_float4(P.xl, P.yl, P.zl, 0.f),
-                     make_float4(P.vx, P.vy, P.vz, 0.f)};
+            *cluster.map_shared_rank(&sm->inbox[rank][k], dst) = sm->own_rec[k];
         }
         cluster.sync();
 
@@ -311,18 +310,45 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
         }
         if (s < 1 || s > E.s_max || mx > kEngCap) break;
 
-        // ---- 3. the members in block order (rank by rank), then the partial sums
-        // over this chunk, pushed to each member's owner
-        for (int q = tid; q < s; q += kEngThreads) {
-            int r = 0, base = 0;
-            while (r < C - 1) {
-                const int cr = sm->slot_cnt[r];
-                if (q < base + cr) break;
-                base += cr;
-                ++r;
+        // ---- 3. the chunk's pair records; the members in block order (rank by rank);
+        // then the partial sums over this chunk, pushed to each member's owner
+        if (warp == 0) {
+            const int cq = lane < C ? sm->slot_cnt[lane] : 0;
+            int incl = cq;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += y;
             }
-            sm->ilist[q] = sm->inbox[r][q - base];
-            sm->qmap[q] = make_int2(r, q - base);
+            if (lane < C) sm->rank_base[lane] = incl - cq;
+        }
+        for (int64_t i = j0 + tid; i < j1; i += kEngThreads) {
+            const int64_t li = i - j0;
+            if (i < n) {
+                float2 X[3], V[3], Ac[3], K[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X[c] = cx[c * ch + li];
+                    V[c] = cv[c * ch + li];
+                    Ac[c] = ca[c * ch + li];
+                    K[c] = ck[c * ch + li];
+                }
+                float4 h, l, w;
+                ds_predict_ds(X, V, Ac, K, ds_sub(tbs, DS{ct[li].x, ct[li].y}), h, l, w, cm[li]);
+                jrec_store(recs, li, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
+            } else {
+                const float far = (float)kPadPos;
+                jrec_store(recs, li, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (tid < C * kEngCap) {
+            const int r = tid / kEngCap, k = tid % kEngCap;
+            if (r < C && k < sm->slot_cnt[r]) {
+                const int q = sm->rank_base[r] + k;
+                sm->ilist[q] = sm->inbox[r][k];
+                sm->qmap[q] = make_int2(r, k);
+            }
         }
         __syncthreads();
         if (s <= 16) {
@@ -339,10 +365,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
                 Acc7 hi, lo;
                 zero(hi);
                 zero(lo);
-                if (gi >= j0 && gi < j1)
-                    sweep<true, 32>(recs, j0, rb, re, lane, ip, gi, e2, hi, lo);
-                else
-                    sweep<false, 32>(recs, j0, rb, re, lane, ip, gi, e2, hi, lo);
+                sweep<true, 32>(recs, j0, rb, re, lane, ip, gi, e2, hi, lo);
                 ds_group_reduce7<32>(hi, lo);
                 if (lane == 0) {
 #pragma unroll
@@ -350,22 +373,23 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
                 }
             }
             __syncthreads();
-            if (tid < s * 7) {
-                const int qq = tid / 7, c = tid % 7;
-                float h = 0.f, l = 0.f;
-                for (int p = 0; p < G; ++p) {
-                    const float2 v = sm->red[qq * G + p][c];
-                    ds_add(h, l, v.x, v.y);
+            // warp c adds component c of each member's G warp sums by a butterfly over
+            // groups of G lanes (lane l holds warp l's sum; lanes past the members add zeros)
+            if (warp < 7) {
+                const int c = warp;
+                const bool has = lane < kEngWarps && lane / G < s;
+                float h = has ? sm->red[lane][c].x : 0.f, l = has ? sm->red[lane][c].y : 0.f;
+                for (int off = G / 2; off >= 1; off >>= 1) {
+                    const float h2 = __shfl_xor_sync(full, h, off), l2 = __shfl_xor_sync(full, l, off);
+                    ds_add(h, l, h2, l2);
                 }
-                const int2 o = sm->qmap[qq];
-                *cluster.map_shared_rank(&sm->part_in[o.y][rank][c], o.x) = make_float2(h, l);
+                if (has && lane % G == 0) {
+                    const int2 o = sm->qmap[lane / G];
+                    *cluster.map_shared_rank(&sm->part_in[o.y][rank][c], o.x) = make_float2(h, l);
+                }
             }
-        } else if (s <= 32) {
-            force_groups<16>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
-        } else if (s <= 64) {
-            force_groups<8>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
         } else {
-            force_groups<4>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
+            force_groups<8>(cluster, sm, recs, j0, j1, nrec, s, e2, rank);
         }
         cluster.sync();
 
@@ -402,16 +426,6 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             sm->wflags[warp] = flags;
         }
         __syncthreads();
-        if (warp == 0) {
-            long long mm = lane < kEngWarps ? sm->wmin[lane] : kInfBits;
-            int ff = lane < kEngWarps ? sm->wflags[lane] : 0;
-            mm = warp_min(mm);
-            ff = (int)__reduce_or_sync(full, (unsigned)ff);
-            if (lane < C) {
-                *cluster.map_shared_rank(&sm->slot_min[rank], lane) = mm;
-                *cluster.map_shared_rank(&sm->slot_err[rank], lane) = ff;
-            }
-        }
         if (rank == 0 && tid == 0) {
             A.counters[0] += 1;
             A.counters[1] += s;
@@ -421,7 +435,26 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
             *A.interactions += (double)s * (double)n;
         }
         ++steps;
-        cluster.sync();
+        // The last warp (which holds no member: kEngCap members take warps 0 and 1)
+        // publishes this chunk's smallest key and status bits to every CTA and
+        // arrives with release semantics; the other warps arrive relaxed, so the
+        // barrier does not wait for the corrector's global stores (nothing in this
+        // cluster reads them before the next kernel; this CTA's own next reads of
+        // them follow a CTA barrier).
+        if (warp == kEngWarps - 1) {
+            long long mm = lane < kEngWarps ? sm->wmin[lane] : kInfBits;
+            int ff = lane < kEngWarps ? sm->wflags[lane] : 0;
+            mm = warp_min(mm);
+            ff = (int)__reduce_or_sync(full, (unsigned)ff);
+            if (lane < C) {
+                *cluster.map_shared_rank(&sm->slot_min[rank], lane) = mm;
+                *cluster.map_shared_rank(&sm->slot_err[rank], lane) = ff;
+            }
+            asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        } else {
+            asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+        }
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 
         // ---- the next block time: the smallest key of all chunks
         long long nxt = lane < C ? sm->slot_min[lane] : kInfBits;
@@ -450,7 +483,7 @@ __global__ void __launch_bounds__(kEngThreads, 1) engine_kernel(EngineArgs E)
 size_t engine_smem_bytes(int64_t chunk)
 {
     return sizeof(EngSmem) + (size_t)(chunk / 2) * sizeof(JPair) +
-           (size_t)chunk * (12 * sizeof(float2) + sizeof(double) + sizeof(long long) + sizeof(float));
+           (size_t)chunk * (12 * sizeof(float2) + sizeof(float2) + sizeof(long long) + sizeof(float));
 }
 
 // Cluster size of the engine for this device (16 if co-schedulable with the

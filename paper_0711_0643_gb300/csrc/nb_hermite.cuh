@@ -149,7 +149,7 @@ __device__ __forceinline__ double pow2_of(int e) { return dfrom((long long)(1023
 // particles' copy in shared memory): element (c, i) at c * np + (i - base).
 struct DsMirror {
     float2 *x2, *v2, *a2, *k2;
-    double *t;
+    float2 *t;            // times as double-single (hi, lo)
     long long *key;
     int64_t np, base;
 };
@@ -293,7 +293,7 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, const G
             H.tn[i] = key;
             if (key_out) *key_out = dbits(key);
             if (mir) {
-                mir->t[i - mir->base] = tn;
+                mir->t[i - mir->base] = rn_ds_pack(tn);
                 mir->key[i - mir->base] = dbits(key);
             }
         }

@@ -135,7 +135,8 @@ struct StepArgs {
     double *t_form;
     const double *fin;                    // final force sums [s][8]
     int32_t *status;
-    int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps
+    int64_t *counters;                    // [0] block steps, [1] particle steps, [2] max block steps,
+                                          // [3 + b] block-size histogram, [3 + NB_SIZE_BUCKETS] loop slots run
     double *interactions;                 // sum s*n
 };
 

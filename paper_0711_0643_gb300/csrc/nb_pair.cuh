@@ -132,16 +132,30 @@ __device__ __forceinline__ void ds_group_reduce(float &hi, float &lo)
     }
 }
 
+// All seven components through the same butterfly, level by level: the shuffles
+// of a level are independent and issue together (each component sees exactly the
+// operations of ds_group_reduce<G>, so the results are the same bits).
 template <int G>
 __device__ __forceinline__ void ds_group_reduce7(Acc7 &hi, Acc7 &lo)
 {
-    ds_group_reduce<G>(hi.ax, lo.ax);
-    ds_group_reduce<G>(hi.ay, lo.ay);
-    ds_group_reduce<G>(hi.az, lo.az);
-    ds_group_reduce<G>(hi.kx, lo.kx);
-    ds_group_reduce<G>(hi.ky, lo.ky);
-    ds_group_reduce<G>(hi.kz, lo.kz);
-    ds_group_reduce<G>(hi.ph, lo.ph);
+#pragma unroll
+    for (int off = G / 2; off >= 1; off >>= 1) {
+        float h[7], l[7];
+        h[0] = __shfl_xor_sync(0xffffffffu, hi.ax, off); l[0] = __shfl_xor_sync(0xffffffffu, lo.ax, off);
+        h[1] = __shfl_xor_sync(0xffffffffu, hi.ay, off); l[1] = __shfl_xor_sync(0xffffffffu, lo.ay, off);
+        h[2] = __shfl_xor_sync(0xffffffffu, hi.az, off); l[2] = __shfl_xor_sync(0xffffffffu, lo.az, off);
+        h[3] = __shfl_xor_sync(0xffffffffu, hi.kx, off); l[3] = __shfl_xor_sync(0xffffffffu, lo.kx, off);
+        h[4] = __shfl_xor_sync(0xffffffffu, hi.ky, off); l[4] = __shfl_xor_sync(0xffffffffu, lo.ky, off);
+        h[5] = __shfl_xor_sync(0xffffffffu, hi.kz, off); l[5] = __shfl_xor_sync(0xffffffffu, lo.kz, off);
+        h[6] = __shfl_xor_sync(0xffffffffu, hi.ph, off); l[6] = __shfl_xor_sync(0xffffffffu, lo.ph, off);
+        ds_add(hi.ax, lo.ax, h[0], l[0]);
+        ds_add(hi.ay, lo.ay, h[1], l[1]);
+        ds_add(hi.az, lo.az, h[2], l[2]);
+        ds_add(hi.kx, lo.kx, h[3], l[3]);
+        ds_add(hi.ky, lo.ky, h[4], l[4]);
+        ds_add(hi.kz, lo.kz, h[5], l[5]);
+        ds_add(hi.ph, lo.ph, h[6], l[6]);
+    }
 }
 
 __device__ __forceinline__ float acc_get(const Acc7 &q, int c)

@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(T) select_known_kernel(StepArgs A, cudaGraphCo
         if (!resident) out += wtot;
     }
     if (lead) {
+        A.counters[3 + NB_SIZE_BUCKETS] += 1;   // one more step slot of the nb_run loop has run
         const int64_t s = (int64_t)total;
         const double tmin = __longlong_as_double(kmin);
         const bool due = tmin <= t_end;

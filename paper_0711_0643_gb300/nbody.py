@@ -43,7 +43,13 @@ class nb_config(C.Structure):
 
 class nb_counters(C.Structure):
     _fields_ = [("block_steps", C.c_int64), ("particle_steps", C.c_int64), ("interactions", C.c_double),
-                ("t_now", C.c_double), ("size_hist", C.c_int64 * 32)]
+                ("t_now", C.c_double), ("size_hist", C.c_int64 * 32), ("loop_slots", C.c_int64)]
+
+
+class nb_timing(C.Structure):
+    _fields_ = [("force_ms", C.c_double), ("phase_ms", C.c_double * 5), ("force_launches", C.c_int64),
+                ("engine_steps", C.c_int64), ("force_interactions", C.c_double),
+                ("engine_interactions", C.c_double)]
 
 
 class nb_state_view(C.Structure):
@@ -75,7 +81,7 @@ _SIGS = [
     ("nb_correct_forces_dev", C.c_int, [_P, _D, _P, _P]),
     ("nb_step", C.c_int, [_P]),
     ("nb_run", C.c_int, [_P, _D]),
-    ("nb_run_timed", C.c_int, [_P, _D, _P, _P, _P, _P]),
+    ("nb_run_timed", C.c_int, [_P, _D, _I32, _P]),
     ("nb_set_engine", C.c_int, [_P, _I32]),
     ("nb_get_engine", C.c_int, [_P, _P, _P]),
     ("nb_energy", C.c_int, [_P, _P, _P, _P]),
@@ -262,14 +268,14 @@ PHASES = ("select", "predict", "force", "correct", "engine")
 
 
 def nb_run_timed(ctx, t_end, phases=False):
-    """Returns (force_ms, launches, engine_steps), plus a dict of summed phase times in ms
-    (select, predict, force, correct, engine) when phases is true."""
-    ms = C.c_double(); nl = C.c_int64(); ne = C.c_int64()
-    ph = (C.c_double * 5)() if phases else None
-    _check(ctx, load().nb_run_timed(ctx, float(t_end), C.byref(ms), C.byref(nl), ph, C.byref(ne)))
-    if phases:
-        return ms.value, nl.value, ne.value, dict(zip(PHASES, list(ph)))
-    return ms.value, nl.value, ne.value
+    """Runs like nb_run, host-driven with CUDA events; returns a dict: force_ms, force_launches,
+    engine_steps, force_interactions, engine_interactions and phase_ms (select, predict, force,
+    correct, engine; the first, second and fourth only with phases=True)."""
+    t = nb_timing()
+    _check(ctx, load().nb_run_timed(ctx, float(t_end), 1 if phases else 0, C.byref(t)))
+    return {"force_ms": t.force_ms, "force_launches": t.force_launches, "engine_steps": t.engine_steps,
+            "force_interactions": t.force_interactions, "engine_interactions": t.engine_interactions,
+            "phase_ms": dict(zip(PHASES, list(t.phase_ms)))}
 
 
 def nb_set_engine(ctx, s_max):
@@ -311,7 +317,8 @@ def nb_stats(ctx) -> dict:
     c = nb_counters()
     _check(ctx, load().nb_stats(ctx, C.byref(c)))
     return {"block_steps": c.block_steps, "particle_steps": c.particle_steps,
-            "interactions": c.interactions, "t_now": c.t_now, "size_hist": list(c.size_hist)}
+            "interactions": c.interactions, "t_now": c.t_now, "size_hist": list(c.size_hist),
+            "loop_slots": c.loop_slots}
 
 
 def nb_sync(ctx):

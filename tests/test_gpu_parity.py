@@ -364,15 +364,18 @@ def test_run_step_and_timed_paths_agree(nb, engine):
             if mode == "run":
                 nb.nb_run(c.ctx, 1.0 / 16)
             elif mode == "timed":
-                ms, nl, ne = nb.nb_run_timed(c.ctx, 1.0 / 16)
-                assert nl > 0 and ms > 0
-                assert (ne > 0) == (engine is None), ne
+                t = nb.nb_run_timed(c.ctx, 1.0 / 16)
+                assert t["force_launches"] > 0 and t["force_ms"] > 0
+                assert (t["engine_steps"] > 0) == (engine is None), t
+                assert t["force_interactions"] + t["engine_interactions"] == nb.nb_stats(c.ctx)["interactions"]
             elif mode == "phases":
-                ms, nl, ne, ph = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
-                assert nl > 0 and ph["force"] == ms
+                t = nb.nb_run_timed(c.ctx, 1.0 / 16, phases=True)
+                ph = t["phase_ms"]
+                assert t["force_launches"] > 0 and ph["force"] == t["force_ms"]
                 assert min(ph[k] for k in ("select", "predict", "force", "correct")) > 0
-                assert (ph["engine"] > 0) == (ne > 0)
-                print(f"engine {engine}: {nl} four-kernel steps, {ne} engine steps; phases (ms) {ph}")
+                assert (ph["engine"] > 0) == (t["engine_steps"] > 0)
+                print(f"engine {engine}: {t['force_launches']} four-kernel steps, {t['engine_steps']} engine "
+                      f"steps; phases (ms) {ph}")
             else:
                 while True:
                     tn, s = nb.nb_next_block(c.ctx)
