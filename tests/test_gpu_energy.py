@@ -63,8 +63,9 @@ def _crc(snap):
     return crc
 
 
-def _run(nb, snap, prec, t_end):
+def _run(nb, snap, prec, t_end, engine=-1):
     with nb.Context(precision=prec) as c:
+        nb.nb_set_engine(c.ctx, engine)
         c.init(snap)
         nb.nb_autotune(c.ctx)
         c.init(snap)
@@ -91,8 +92,9 @@ def _oracle_dE(orc, snap, t_end):
     return _LIVE[key]
 
 
-@pytest.mark.parametrize("cfg,prec", [(2, 0), (2, 1), (3, 0)])
-def test_energy_error_within_2x_oracle(nb, orc, cfg, prec):
+@pytest.mark.parametrize("cfg,prec,engine", [(2, 0, -1), (2, 0, 32), (2, 1, 0), (3, 0, -1)])
+def test_energy_error_within_2x_oracle(nb, orc, cfg, prec, engine):
+    """engine: the small-block engine's largest block (-1: the default for the workload)."""
     gold = _golden(cfg)
     snap = ics.config(cfg)
     assert snap.n == gold["n"]
@@ -104,7 +106,7 @@ def test_energy_error_within_2x_oracle(nb, orc, cfg, prec):
             how = "oracle rerun on this host's inputs"
         else:
             how = "stored, inputs differing in the last bits"
-    dE, cnt = _run(nb, snap, prec, gold["t_end"])
-    print(f"config {cfg}, precision {prec}: |dE/E| gpu {dE:.4e} oracle {ref:.4e} ({how}; stored "
+    dE, cnt = _run(nb, snap, prec, gold["t_end"], engine)
+    print(f"config {cfg}, precision {prec}, engine {engine}: |dE/E| gpu {dE:.4e} oracle {ref:.4e} ({how}; stored "
           f"{gold['abs_dE_over_E']:.4e}); block steps gpu {cnt['block_steps']} oracle {ref_steps}")
     assert dE <= 2.0 * ref + FLOOR, (dE, ref)

@@ -20,9 +20,9 @@ The oracle integrating its own state (free running) is run beside it; the step a
 block schedule first differs from the GPU's is printed.
 
 Two drivers: "explicit" calls nb_next_block, nb_predict, nb_force_jerk and nb_correct (the
-four-kernel step); "step" calls nb_step, which runs small blocks inside the small-block
-engine (its new forces are read back from the corrected state, where the corrector stores
-them; its potential is not compared).
+four-kernel step); "step" calls nb_step with the small-block engine taking blocks of up to
+32 particles (its new forces are read back from the corrected state, where the corrector
+stores them; its potential is not compared).
 """
 import numpy as np
 import pytest
@@ -68,7 +68,11 @@ def test_block_schedule_mixed_lockstep(nb, orc, cfg, driver):
     in_window = 0
     windows = []
     with nb.Context(precision=0) as c:
+        if driver == "step":
+            nb.nb_set_engine(c.ctx, 32)
         c.init(snap)
+        if driver == "step":
+            assert nb.nb_get_engine(c.ctx)[0] == 32
         g = c.state()
         # start steps: dt0 = 2^floor(log2(eta |a| / |k|)) on the forces of the initial state
         ar, kr, pr = orc.force(snap.m, snap.x, snap.v, snap.eps2, None, nthreads=nth)
