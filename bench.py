@@ -672,7 +672,8 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
     size s in {1, 64, 1024, 16384, N} (active = first s of a seeded permutation, ascending),
     split factor autotuned; interactions/s and FP32 roofline fraction per s. Each point is
     the median of single nb_force_jerk_dev calls (active list in, a/k/phi out, all on the
-    device), each timed with L2 flushed before it."""
+    device), each timed with L2 flushed before it and the launch queued behind a short spin
+    (the events bracket the device work, not the host's launch latency)."""
     import ics
     snap = ics.config(5, n=n_override)
     n = snap.n
@@ -688,7 +689,8 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
     perm = np.argsort(ics.SplitMix64(ics.BASE_SEED + 5).uniform(n))
     out = {"workload": f"king W0=6 N={n} eps=1e-3, single evaluation", "points": [],
            "precision": "fp64" if prec == nb.NB_PREC_FP64 else "mixed",
-           "l2": "flushed (256 MB write) before every timed call; median of single calls"}
+           "l2": "flushed (256 MB write) before every timed call; median of single calls, each queued "
+                 "behind a short spin so the events bracket device work"}
     stream = torch.cuda.current_stream(dev)
     assert stream.cuda_stream == sptr
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
@@ -709,6 +711,10 @@ def force_sweep(nb, torch, dev, sptr, num_sms, sm_mhz, n_override=None, s_list=N
         for _ in range(nrep):
             l2_flush.zero_()
             torch.cuda.synchronize(dev)
+            # a short spin on the stream first: the call is queued behind it before the
+            # start event is processed, so the events bracket the device work and not the
+            # host's launch latency
+            torch.cuda._sleep(100000)
             e0.record(stream)
             nb.nb_force_jerk_dev(c.ctx, idx_d.data_ptr(), s, a_d.data_ptr(), k_d.data_ptr(), p_d.data_ptr())
             e1.record(stream)

@@ -43,8 +43,11 @@ namespace cg = cooperative_groups;
 namespace nb {
 namespace {
 
-constexpr int kEnsThreads = 256;
-constexpr int kEnsTile = 256;
+#ifndef NB_ENS_THREADS
+#define NB_ENS_THREADS 256
+#endif
+constexpr int kEnsThreads = NB_ENS_THREADS;   // threads per CTA (and particles per j-tile)
+constexpr int kEnsTile = kEnsThreads;
 // j-split (every CTA takes all active i) when s <= this; on the 256-system
 // workload with 8-CTA clusters: 2048 2.42 s, 1024 2.45 s, 512 2.46 s
 constexpr int kEnsSplitMax = 2048;
@@ -286,7 +289,7 @@ __global__ void ens_soa_to_aos(const double *src, double *dst, int64_t n)
 
 __device__ __forceinline__ long long min_ll(long long a, long long b) { return a < b ? a : b; }
 
-__global__ void __launch_bounds__(kEnsThreads, 2) ensemble_kernel(EnsArgs E)
+__global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kernel(EnsArgs E)
 {
     __shared__ EnsSmem smem;
     EnsSmem *sm = &smem;

@@ -96,11 +96,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_
 constexpr int kMaxRC = 2 * 7;   // R * components, largest R over variants
 
 constexpr int kPT = kJT / 2;    // pair records per tile
+constexpr int kRing = 6;        // tiles in flight in the TMA streaming variant
 
 struct __align__(128) Smem {
-    JPair tile[kStages][kPT];
+    union {
+        JPair tile[kStages][kPT];   // tile variants
+        JPair ring[kRing][kPT];     // TMA streaming variant
+    };
     float2 red[kThreads / 32][kMaxRC];
-    uint64_t bar[kStages];
+    uint64_t bar[kRing];
     uint64_t inject_bar;
     int64_t s;                 // active count of this launch
     Tuning tune;               // the device tuning table, read once per CTA
@@ -223,20 +227,76 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
                 put_final(A, ii, c, (double)h + (double)l);
             }
         } else {
-            // many splits: one warp per (particle, component); lanes stride over the
-            // splits and a fixed butterfly of two-sums combines them
+            // many splits: a warp per (particle, component) sum; lane l adds splits l, l + 32,
+            // ... in ascending order (their loads issued together, kFinUnroll per round),
+            // then a fixed butterfly of two-sums combines the lanes. The order of every
+            // addition is the split order per lane, so the batching of the loads does not
+            // change the result.
+            constexpr int kFinUnroll = 4;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            for (int q = warp; q < cnt; q += kThreads / 32) {
-                const int64_t ii = ib0 + q / 7;
-                const int c = q % 7;
-                const float2 *src = reinterpret_cast<const float2 *>(A.part) + ii * S * kPartStride + c;
-                float h = 0.f, l = 0.f;
-                for (int sp = lane; sp < S; sp += 32) {
-                    const float2 v = __ldcg(src + sp * kPartStride);
-                    ds_add(h, l, v.x, v.y);
+            const float2 *base = reinterpret_cast<const float2 *>(A.part);
+            if (cnt <= kThreads / 32) {
+                // one sum per warp
+                if (warp < cnt) {
+                    const float2 *src = base + (ib0 + warp / 7) * S * kPartStride + warp % 7;
+                    float h = 0.f, l = 0.f;
+                    for (int sp0 = lane; sp0 < S; sp0 += 32 * kFinUnroll) {
+                        float2 v[kFinUnroll];
+#pragma unroll
+                        for (int u = 0; u < kFinUnroll; ++u)
+                            v[u] = sp0 + 32 * u < S ? __ldcg(src + (sp0 + 32 * u) * kPartStride) : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < kFinUnroll; ++u)
+                            if (sp0 + 32 * u < S) ds_add(h, l, v[u].x, v[u].y);
+                    }
+                    ds_group_reduce<32>(h, l);
+                    if (lane == 0) put_final(A, ib0 + warp / 7, warp % 7, (double)h + (double)l);
                 }
-                ds_group_reduce<32>(h, l);
-                if (lane == 0) put_final(A, ii, c, (double)h + (double)l);
+            } else {
+                // four sums in flight per warp, their butterflies interleaved level by level
+                constexpr int kFinTasks = 4;
+                for (int q0 = warp * kFinTasks; q0 < cnt; q0 += (kThreads / 32) * kFinTasks) {
+                    float h[kFinTasks], l[kFinTasks];
+                    const float2 *src[kFinTasks];
+#pragma unroll
+                    for (int t = 0; t < kFinTasks; ++t) {
+                        h[t] = 0.f;
+                        l[t] = 0.f;
+                        const int q = q0 + t < cnt ? q0 + t : cnt - 1;
+                        src[t] = base + (ib0 + q / 7) * S * kPartStride + q % 7;
+                    }
+                    for (int sp0 = lane; sp0 < S; sp0 += 32 * kFinUnroll) {
+                        float2 v[kFinTasks][kFinUnroll];
+#pragma unroll
+                        for (int t = 0; t < kFinTasks; ++t)
+#pragma unroll
+                            for (int u = 0; u < kFinUnroll; ++u) {
+                                const int sp = sp0 + 32 * u;
+                                v[t][u] = sp < S ? __ldcg(src[t] + sp * kPartStride) : make_float2(0.f, 0.f);
+                            }
+#pragma unroll
+                        for (int t = 0; t < kFinTasks; ++t)
+#pragma unroll
+                            for (int u = 0; u < kFinUnroll; ++u)
+                                if (sp0 + 32 * u < S) ds_add(h[t], l[t], v[t][u].x, v[t][u].y);
+                    }
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        float h2[kFinTasks], l2[kFinTasks];
+#pragma unroll
+                        for (int t = 0; t < kFinTasks; ++t) {
+                            h2[t] = __shfl_xor_sync(0xffffffffu, h[t], off);
+                            l2[t] = __shfl_xor_sync(0xffffffffu, l[t], off);
+                        }
+#pragma unroll
+                        for (int t = 0; t < kFinTasks; ++t) ds_add(h[t], l[t], h2[t], l2[t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kFinTasks; ++t) {
+                        const int q = q0 + t;
+                        if (lane == 0 && q < cnt) put_final(A, ib0 + q / 7, q % 7, (double)h[t] + (double)l[t]);
+                    }
+                }
             }
         }
         if (threadIdx.x == 0) A.tickets[bx] = 0;
@@ -322,6 +382,96 @@ __device__ void work_stream(const ForceArgs &A, int64_t s, int64_t bx, int by, i
         int r = tid / 7, c = tid % 7;
         int64_t ii = bx * R + r;
         if (ii < s) part2(A, ii, by, S)[c] = make_float2(h, l);
+    }
+    __syncthreads();
+}
+
+// --------------------------------------------------- TMA streaming variant
+// TI = 1: all threads share one i-particle; the item's j-tiles stream through a
+// ring of kRing shared-memory stages filled by the TMA bulk engine, so that
+// kRing x 10 KB per CTA are in flight without holding registers (for blocks of
+// one or two particles the evaluation is bound by reading the j-records). The
+// two halves of the CTA take consecutive tiles, a thread one pair record of its
+// half's tile.
+__device__ __forceinline__ void issue_ring(const ForceArgs &A, Smem *sm, int64_t tile, int st)
+{
+    constexpr uint32_t bytes = kPT * sizeof(JPair);
+    mbar_arrive_expect_tx(&sm->bar[st], bytes);
+    bulk_g2s(sm->ring[st], A.j.p + tile * kPT, bytes, &sm->bar[st]);
+}
+
+__device__ void work_stream_tma(const ForceArgs &A, int64_t s, int64_t bx, int by, int S, Smem *sm, uint32_t &git)
+{
+    static_assert(kThreads == 2 * kPT, "each half of the CTA takes one tile");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t tper = qdiv(A.tile_hi - A.tile_lo + S - 1, S);
+    const int64_t t0 = A.tile_lo + (int64_t)by * tper;
+    const int64_t t1 = t0 + tper < A.tile_hi ? t0 + tper : A.tile_hi;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    if (tid == 0) {
+        const int64_t pro = nt < kRing ? nt : kRing;
+        for (int64_t q = 0; q < pro; ++q) issue_ring(A, sm, t0 + q, (int)((git + q) % kRing));
+    }
+    const int32_t gi = idx_at(A, sm, bx < s ? bx : s - 1);
+    const IPk ip = ipk_of(jrec_load(A.j.p, gi));
+    const float2 e2 = make_float2(A.eps2f, A.eps2f);
+    const int half = tid / kPT, r = tid % kPT;
+    AccPk p;
+    Acc7 hi, lo;
+    zero(p);
+    zero(hi);
+    zero(lo);
+    int cnt = 0;
+    for (int64_t q = 0; q < nt; q += 2) {
+        const int64_t qh = q + half;
+        if (qh < nt) {
+            const uint32_t g = git + (uint32_t)qh;
+            const int st = (int)(g % kRing);
+            if (!mbar_wait(&sm->bar[st], (g / kRing) & 1u, A.spin_limit)) {
+                sm->abort = 1;
+            } else {
+                const float4 *Q = sm->ring[st][r].q;
+                const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
+                const int64_t ja = (t0 + qh) * kJT + 2 * r;
+                pair_packed<true>(q0, q1, q2, q3, q4, ip, e2, p, ja == gi, ja + 1 == gi);
+                if (++cnt == kFoldPairs / 2) {
+                    cnt = 0;
+                    fold(hi, lo, p);
+                }
+            }
+        }
+        __syncthreads();   // both tiles read: their stages may be refilled
+        if (sm->abort) {
+            // a wait ran out: drain what this CTA still has in flight (bounded), then stop
+            // (tiles q .. q + kRing - 1 were issued; each wait is bounded)
+            if (tid == 0) {
+                for (int64_t qq = q; qq < nt && qq < q + kRing; ++qq) {
+                    const uint32_t gg = git + (uint32_t)qq;
+                    (void)mbar_wait(&sm->bar[gg % kRing], (gg / kRing) & 1u, A.spin_limit);
+                }
+            }
+            git += (uint32_t)nt;
+            return;
+        }
+        if (tid == 0) {
+            for (int64_t qq = q + kRing; qq < q + kRing + 2 && qq < nt; ++qq)
+                issue_ring(A, sm, t0 + qq, (int)((git + qq) % kRing));
+        }
+    }
+    git += (uint32_t)nt;
+    fold(hi, lo, p);
+    // fixed-order reduction: lanes (xor tree of two-sums), then warps in ascending order
+    ds_group_reduce7<32>(hi, lo);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) sm->red[warp][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+    }
+    __syncthreads();
+    if (tid < 7) {
+        float h = sm->red[0][tid].x, l = sm->red[0][tid].y;
+#pragma unroll
+        for (int wv = 1; wv < kThreads / 32; ++wv) ds_add(h, l, sm->red[wv][tid].x, sm->red[wv][tid].y);
+        if (bx < s) part2(A, bx, by, S)[tid] = make_float2(h, l);
     }
     __syncthreads();
 }
@@ -444,7 +594,8 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 // -------------------------------------------------------------- variants
 
 // 0: stream R=1 (I=1)      1: stream R=2 (I=2)      2: tile R=1 TJ=32 (I=8)
-// 3: tile R=1 TJ=8 (I=32)  4: tile R=1 TJ=1 (I=256)
+// 3: tile R=1 TJ=8 (I=32)  4: tile R=1 TJ=1 (I=256) 5: TMA stream R=1 (I=1)
+constexpr int kMixedFallback = 4;   // the variant of an out-of-range table entry
 __host__ __device__ __forceinline__ int mixed_I(int v)
 {
     switch (v) {
@@ -452,6 +603,7 @@ __host__ __device__ __forceinline__ int mixed_I(int v)
     case 1: return 2;
     case 2: return 8;
     case 3: return 32;
+    case 5: return 1;
     default: return 256;
     }
 }
@@ -468,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     // read ahead of s: entries past s are stale and never used (idx_cap >= s)
     const int32_t ipre = tid < A.idx_cap ? A.idx[tid] : 0;
     if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&sm->bar[st], 1);
+        for (int st = 0; st < kRing; ++st) mbar_init(&sm->bar[st], 1);
         mbar_init(&sm->inject_bar, 1);
         fence_mbar_init();
         sm->abort = 0;
@@ -499,10 +651,10 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     } else {
         const int b = bucket_of(s);
         variant = sm->tune.variant[b];
-        if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
+        if (variant < 0 || variant >= kMixedVariants) variant = kMixedFallback;
         S = table_split(sm->tune.split[b], b, s, A.n, mixed_I(variant));
     }
-    if (variant < 0 || variant >= kMixedVariants) variant = kMixedVariants - 1;
+    if (variant < 0 || variant >= kMixedVariants) variant = kMixedFallback;
     S = clamp_split(S, A.tile_hi - A.tile_lo, s, A.part_cap);
     if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
     const int64_t I = mixed_I(variant);
@@ -517,6 +669,7 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         case 1: work_stream<2>(A, s, bx, by, S, sm); break;
         case 2: work_tile<1, 32>(A, s, bx, by, S, sm, git); break;
         case 3: work_tile<1, 8>(A, s, bx, by, S, sm, git); break;
+        case 5: work_stream_tma(A, s, bx, by, S, sm, git); break;
         default: work_tile<1, 1>(A, s, bx, by, S, sm, git); break;
         }
         if (sm->abort) {
@@ -629,8 +782,17 @@ __device__ void finish_item_f64(const ForceArgs &A, int64_t s, int64_t bx, int S
         for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
             const int64_t ii = ib0 + q / 7;
             const int c = (int)(q % 7);
+            const double *src = A.part + ii * S * kPartStride + c;
             double x = 0.0;
-            for (int sp = 0; sp < S; ++sp) x += __ldcg(A.part + (ii * S + sp) * kPartStride + c);
+            // eight loads in flight, added in split order
+            for (int sp0 = 0; sp0 < S; sp0 += 8) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = sp0 + u < S ? __ldcg(src + (sp0 + u) * kPartStride) : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (sp0 + u < S) x += v[u];
+            }
             put_final(A, ii, c, x);
         }
         if (threadIdx.x == 0) A.tickets[bx] = 0;
@@ -698,6 +860,7 @@ const char *mixed_variant_name(int v)
     case 2: return "tile R=1 TJ=32";
     case 3: return "tile R=1 TJ=8";
     case 4: return "tile R=1 TJ=1";
+    case 5: return "TMA stream R=1";
     default: return "?";
     }
 }

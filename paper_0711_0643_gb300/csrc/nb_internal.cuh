@@ -89,7 +89,7 @@ struct ForceArgs {
 };
 
 // Variant catalogue. Mixed: 0..kMixedVariants-1; FP64: 0..kF64Variants-1.
-constexpr int kMixedVariants = 5;
+constexpr int kMixedVariants = 6;
 constexpr int kF64Variants = 2;
 int mixed_variant_I(int v);           // i-particles per work item
 const char *mixed_variant_name(int v);
