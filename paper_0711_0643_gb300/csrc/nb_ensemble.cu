@@ -46,6 +46,9 @@ namespace {
 #ifndef NB_ENS_THREADS
 #define NB_ENS_THREADS 256
 #endif
+#ifndef NB_ENS_MIN_BLOCKS
+#define NB_ENS_MIN_BLOCKS (512 / NB_ENS_THREADS)
+#endif
 constexpr int kEnsThreads = NB_ENS_THREADS;   // threads per CTA (and particles per j-tile)
 constexpr int kEnsTile = kEnsThreads;
 // j-split (every CTA takes all active i) when s <= this; on the 256-system
@@ -63,8 +66,11 @@ struct EnsArgs {
     int64_t np;              // stride of the SoA vectors (total particles)
     double *m, *x, *v, *a, *k, *t, *dt, *tn;
     float2 *x2, *v2, *a2, *k2;   // double-single copies of x, v, a, k
+    float2 *t2;              // double-single copy of t (the predictor's time differences on the FP32 pipe)
+    float *m32;              // FP32 masses (the j-records' mass)
     float4 *jh, *jl, *jv;    // predicted records
-    int32_t *idx;            // active lists, member segments
+    int32_t *idx;            // per-rank candidate segments of the active list, member segments
+    int32_t *idx2;           // the active list in rank order (block steps with many active particles)
     float2 *part;            // j-split partials, per cluster
     int32_t *queue;          // next member to take
     int32_t *ready;          // [nc] 1 once forces and first steps exist
@@ -78,15 +84,57 @@ struct EnsArgs {
 
 struct EnsSmem {
     JPair tile[kEnsTile / 2];   // a j-tile as pair records (two particles' fields per float4)
-    float2 red[kEnsThreads / 32][14];
+    int32_t list[kEnsSplitMax];  // the active list of a block step with s <= kEnsSplitMax
     double dred[kEnsThreads / 32][2];
-    long long kmin;
+    long long kmin;              // this CTA's smallest key and how many of its particles have it
     int cnt;
     int err;
     int member;
     int wcnt[kEnsThreads / 32];
     long long wmin[kEnsThreads / 32];
+    int seg_off[16], seg_start[16];   // rank q's segment: list positions from seg_off[q], act from seg_start[q]
 };
+
+// ------------------------------------------------------------- prediction
+
+// Particle i (global index) predicted to the block time tb (double-single) as
+// its j-record. The time difference is formed in double-single from the
+// double-single copy of t_i (all times are multiples of the smallest step, so
+// the difference is exact), keeping the O(N) prediction off the FP64 pipe (a
+// narrow pipe on this part).
+__device__ __forceinline__ void predict_one(const EnsArgs &E, int64_t i, DS tb, float4 &h, float4 &l, float4 &w)
+{
+    float2 X[3], V[3], A[3], K[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        X[c] = E.x2[c * E.np + i];
+        V[c] = E.v2[c * E.np + i];
+        A[c] = E.a2[c * E.np + i];
+        K[c] = E.k2[c * E.np + i];
+    }
+    const float2 ti = E.t2[i];
+    ds_predict_ds(X, V, A, K, ds_sub(tb, DS{ti.x, ti.y}), h, l, w, E.m32[i]);
+}
+
+__device__ __forceinline__ DS ds_of_time(double t)
+{
+    const float2 p = rn_ds_pack(t);
+    return DS{p.x, p.y};
+}
+
+// Particles [c0, c1) of a member to the block time.
+__device__ __forceinline__ void predict_chunk(const EnsArgs &E, int64_t base, int64_t c0, int64_t c1, double tblock)
+{
+    const DS tb = ds_of_time(tblock);
+    for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
+        const int64_t i = base + q;
+        float4 h, l, w;
+        predict_one(E, i, tb, h, l, w);
+        E.jh[i] = h;
+        E.jl[i] = l;
+        E.jv[i] = w;
+    }
+}
 
 // ------------------------------------------------------------- force (CTA)
 
@@ -106,11 +154,14 @@ __device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_
 }
 
 // Forces on the active positions [p0, p1) of list act (member-relative particle
-// indices, ascending) from the member's j in [j0, j1), as (hi, lo) float pairs
-// into part: position pp goes to slot slot0 + pp - p0 (7 values of kPartStride).
-template <int R, int TJ>
+// indices, ascending; global or shared memory) from the member's j in [j0, j1),
+// as (hi, lo) float pairs into part: position pp goes to slot slot0 + pp - p0 (7
+// values of kPartStride). The i-particles' predicted records are read from
+// jh/jl/jv, or with PRED predicted here to tb (when other CTAs' predictions are
+// not synchronised with this one).
+template <int R, int TJ, bool PRED>
 __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1, int64_t j0,
-                          int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm)
+                          int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm, DS tb)
 {
     constexpr int TI = kEnsThreads / TJ;
     constexpr int I = TI * R;
@@ -128,7 +179,14 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
         for (int r = 0; r < R; ++r) {
             const int64_t p = pb + (int64_t)r * TI + ti;
             gi[r] = act[p < pe ? p : pe - 1];
-            const float4 h = E.jh[base + gi[r]], l = E.jl[base + gi[r]], w = E.jv[base + gi[r]];
+            float4 h, l, w;
+            if (PRED) {
+                predict_one(E, base + gi[r], tb, h, l, w);
+            } else {
+                h = E.jh[base + gi[r]];
+                l = E.jl[base + gi[r]];
+                w = E.jv[base + gi[r]];
+            }
             ip[r] = ipk_of(IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z});
         }
         const int64_t imin = act[pb], imax = act[pe - 1];
@@ -197,57 +255,88 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
 }
 
 // Size-adapted dispatch of cta_force.
-__device__ __noinline__ void cta_force_any(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1, int64_t j0,
-                              int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm)
+template <bool PRED>
+__device__ __noinline__ void cta_force_any(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
+                                           int64_t j0, int64_t j1, float eps2f, float2 *part, int64_t slot0,
+                                           EnsSmem *sm, DS tb = DS{0.f, 0.f})
 {
     const int64_t ni = p1 - p0;
     if (ni <= 0) return;
     // one i-particle per thread group (R = 1; two would not fit the registers of
     // the packed form); TJ threads share it
     if (ni <= 8)
-        cta_force<1, 32>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+        cta_force<1, 32, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
     else if (ni <= 32)
-        cta_force<1, 8>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+        cta_force<1, 8, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
     else if (ni <= 64)
-        cta_force<1, 4>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+        cta_force<1, 4, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
     else if (ni <= 128)
-        cta_force<1, 2>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+        cta_force<1, 2, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
     else
-        cta_force<1, 1>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm);
+        cta_force<1, 1, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+}
+
+// Component cq of a and k of list position p: the C ranks' partials summed in
+// rank order, all loads issued before the first addition.
+__device__ __forceinline__ void sum_partials(const float2 *part, int64_t s, int64_t p, int cq, int C, double &an,
+                                             double &kn)
+{
+    float ha = 0.f, la = 0.f, hk = 0.f, lk = 0.f;
+    for (int q0 = 0; q0 < C; q0 += 8) {
+        float2 va[8], vk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q0 + u < C) {
+                const float2 *src = part + ((int64_t)(q0 + u) * s + p) * kPartStride;
+                va[u] = __ldcg(src + cq);
+                vk[u] = __ldcg(src + 3 + cq);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (q0 + u < C) {
+                ds_add(ha, la, va[u].x, va[u].y);
+                ds_add(hk, lk, vk[u].x, vk[u].y);
+            }
+        }
+    }
+    an = (double)ha + (double)la;
+    kn = (double)hk + (double)lk;
 }
 
 // ---------------------------------------------------------------- phases
 
-__device__ __forceinline__ void predict_chunk(const EnsArgs &E, int64_t base, int64_t c0, int64_t c1, double tblock)
-{
-    for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
-        const int64_t i = base + q;
-        float4 h, l, w;
-        ds_predict(E.x2, E.v2, E.a2, E.k2, E.np, i, tblock - E.t[i], h, l, w, (float)E.m[i]);
-        E.jh[i] = h;
-        E.jl[i] = l;
-        E.jv[i] = w;
-    }
-}
-
 // K and W (softened, FP64) of the member's particles [c0, c1) summed by the CTA.
+// Every pair once: particle q takes the (N - 1) / 2 particles after it on the
+// ring of the member's indices, and for even N the opposite particle with
+// weight 1/2 (that pair is reached from both ends), so each thread does the
+// same work.
 __device__ void energy_chunk(const EnsArgs &E, int64_t base, int64_t N, int64_t c0, int64_t c1, double eps2,
                              EnsSmem *sm, double &K, double &W)
 {
     double ek = 0.0, ew = 0.0;
+    const int64_t half = (N - 1) / 2;
     for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
         const int64_t i = base + q;
         const double xi = E.x[i], yi = E.x[E.np + i], zi = E.x[2 * E.np + i];
         double phi = 0.0;
-        for (int64_t jj = 0; jj < N; ++jj) {
+        int64_t jj = q;
+        for (int64_t d = 1; d <= half; ++d) {
+            jj = jj + 1 < N ? jj + 1 : 0;
             const int64_t j = base + jj;
             const double dx = E.x[j] - xi, dy = E.x[E.np + j] - yi, dz = E.x[2 * E.np + j] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-            phi -= (jj == q) ? 0.0 : E.m[j] * rsqrt(r2);
+            phi -= E.m[j] * rsqrt(r2);
+        }
+        if ((N & 1) == 0) {
+            const int64_t j = base + (q + N / 2 < N ? q + N / 2 : q - N / 2);
+            const double dx = E.x[j] - xi, dy = E.x[E.np + j] - yi, dz = E.x[2 * E.np + j] - zi;
+            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            phi -= 0.5 * (E.m[j] * rsqrt(r2));
         }
         const double vx = E.v[i], vy = E.v[E.np + i], vz = E.v[2 * E.np + i];
         ek += 0.5 * E.m[i] * (vx * vx + vy * vy + vz * vz);
-        ew += 0.5 * E.m[i] * phi;
+        ew += E.m[i] * phi;
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
@@ -281,6 +370,12 @@ __global__ void ens_to_ds(const double *src, float2 *dst, int64_t count)
         dst[q] = ds_pack(src[q]);
 }
 
+__global__ void ens_to_f32(const double *src, float *dst, int64_t count)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = (float)src[q];
+}
+
 __global__ void ens_soa_to_aos(const double *src, double *dst, int64_t n)
 {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 3 * n; q += (int64_t)gridDim.x * blockDim.x)
@@ -289,7 +384,7 @@ __global__ void ens_soa_to_aos(const double *src, double *dst, int64_t n)
 
 __device__ __forceinline__ long long min_ll(long long a, long long b) { return a < b ? a : b; }
 
-__global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kernel(EnsArgs E)
+__global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kernel(EnsArgs E)
 {
     __shared__ EnsSmem smem;
     EnsSmem *sm = &smem;
@@ -315,7 +410,10 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
         const int64_t N = E.off[mem + 1] - base;
         const double eps2 = E.eps2[mem];
         const float eps2f = (float)eps2;
-        const int64_t chunk = (N + C - 1) / C;
+        // particles [c0, c1) belong to this CTA: it predicts them, holds the j-share
+        // of the small-s force, corrects them and scans their keys; an even share
+        // (pair records stay whole), 32-bit division (N < 2^19)
+        const int64_t chunk = (int64_t)((((uint32_t)N + (uint32_t)C - 1u) / (uint32_t)C + 1u) / 2u * 2u);
         const int64_t c0 = (int64_t)rank * chunk < N ? (int64_t)rank * chunk : N;
         const int64_t c1 = c0 + chunk < N ? c0 + chunk : N;
         int32_t *act = E.idx + base;
@@ -332,7 +430,7 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
             for (int64_t r0 = c0; r0 < c1; r0 += kEnsSlots) {
                 const int64_t r1 = r0 + kEnsSlots < c1 ? r0 + kEnsSlots : c1;
                 const int64_t slot0 = (int64_t)rank * kEnsSlots;
-                cta_force_any(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
+                cta_force_any<false>(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
                 __syncthreads();
                 for (int64_t pp = r0 + tid; pp < r1; pp += kEnsThreads) {
                     const float2 *src = part + (slot0 + pp - r0) * kPartStride;
@@ -370,72 +468,104 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
         }
 
         int64_t nsteps = 0;
+        const unsigned full = 0xffffffffu;
+        const long long kInf = 0x7ff0000000000000LL;
+        const int cq = (tid & 3) < 3 ? (tid & 3) : 2;   // four lanes per particle in the corrector
         for (;;) {
-            // ---- select: cluster-wide minimum of t + dt, ordered active list
+            // ---- select. Each thread's smallest key over its slice of this CTA's
+            // particles and how many have it, reduced to the CTA's (smallest key,
+            // count); the particles holding the CTA's smallest key are written, in
+            // index order, to this CTA's segment of act. One cluster barrier then
+            // exchanges the CTAs' pairs and error flags: the block time is the
+            // smallest key, the active list the segments of the CTAs holding it,
+            // in rank order.
             const long long *key = reinterpret_cast<const long long *>(E.tn) + base;
-            long long mloc = 0x7ff0000000000000LL;
             const int64_t sub = (c1 - c0 + kEnsThreads - 1) / kEnsThreads;
             const int64_t s0 = c0 + tid * sub < c1 ? c0 + tid * sub : c1;
             const int64_t s1 = s0 + sub < c1 ? s0 + sub : c1;
+            long long mloc = kInf;
+            int cloc = 0;
             for (int64_t q = s0; q < s1; q += 4) {   // four loads in flight
                 long long kv[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) kv[u] = q + u < s1 ? key[q + u] : 0x7ff0000000000000LL;
+                for (int u = 0; u < 4; ++u) kv[u] = q + u < s1 ? key[q + u] : kInf;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) mloc = min_ll(mloc, kv[u]);
+                for (int u = 0; u < 4; ++u) {
+                    if (q + u < s1) {
+                        if (kv[u] < mloc) {
+                            mloc = kv[u];
+                            cloc = 1;
+                        } else if (kv[u] == mloc) {
+                            ++cloc;
+                        }
+                    }
+                }
             }
+            long long wm = mloc;
+            int wc = cloc;
 #pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) mloc = min_ll(mloc, __shfl_xor_sync(0xffffffffu, mloc, off));
-            if (lane == 0) sm->wmin[warp] = mloc;
-            __syncthreads();
-            if (tid == 0) {
-                long long mm = sm->wmin[0];
-                for (int wv = 1; wv < kEnsThreads / 32; ++wv) mm = min_ll(mm, sm->wmin[wv]);
-                sm->kmin = mm;
+            for (int off = 16; off >= 1; off >>= 1) {
+                const long long om = __shfl_xor_sync(full, wm, off);
+                const int oc = __shfl_xor_sync(full, wc, off);
+                const long long nm = min_ll(wm, om);
+                wc = (wm == nm ? wc : 0) + (om == nm ? oc : 0);
+                wm = nm;
+            }
+            if (lane == 0) {
+                sm->wmin[warp] = wm;
+                sm->wcnt[warp] = wc;
             }
             // error flags of the previous step, OR-ed over the CTA
             if (flags) atomicOr(&sm->err, flags);
             flags = 0;
-            cluster.sync();
-            // lane q reads rank q's minimum and flags (C <= 32): one round of
-            // distributed shared-memory loads, then warp reductions
-            long long kmin = lane < C ? *cluster.map_shared_rank(&sm->kmin, lane) : 0x7ff0000000000000LL;
-            int err = lane < C ? *cluster.map_shared_rank(&sm->err, lane) : 0;
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                kmin = min_ll(kmin, __shfl_xor_sync(0xffffffffu, kmin, off));
-                err |= __shfl_xor_sync(0xffffffffu, err, off);
+            __syncthreads();
+            long long mc = sm->wmin[0];
+            for (int wv = 1; wv < kEnsThreads / 32; ++wv) mc = min_ll(mc, sm->wmin[wv]);
+            int wbase = 0, cc = 0;
+            for (int wv = 0; wv < kEnsThreads / 32; ++wv) {
+                const int cw = sm->wmin[wv] == mc ? sm->wcnt[wv] : 0;
+                if (wv < warp) wbase += cw;
+                cc += cw;
             }
-            const double tblock = __longlong_as_double(kmin);
-            int cnt = 0;
-            for (int64_t q = s0; q < s1; ++q) cnt += (key[q] == kmin);
-            int incl = cnt;
+            const int ct = mloc == mc ? cloc : 0;
+            int incl = ct;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                const int y = __shfl_up_sync(full, incl, off);
                 if (lane >= off) incl += y;
             }
-            if (lane == 31) sm->wcnt[warp] = incl;
-            __syncthreads();
-            int wbase = 0, total = 0;
-            for (int wv = 0; wv < kEnsThreads / 32; ++wv) {
-                if (wv < warp) wbase += sm->wcnt[wv];
-                total += sm->wcnt[wv];
+            if (ct > 0) {
+                int pos = (int)c0 + wbase + incl - ct;
+                for (int64_t q = s0; q < s1; ++q)
+                    if (key[q] == mc) act[pos++] = (int32_t)q;
             }
-            if (tid == 0) sm->cnt = total;
+            if (tid == 0) {
+                sm->kmin = mc;
+                sm->cnt = cc;
+            }
             cluster.sync();
-            int64_t offset = 0, s = 0;
-            {
-                const int cq = lane < C ? *cluster.map_shared_rank(&sm->cnt, lane) : 0;
-                int lo = lane < rank ? cq : 0, all = cq;
+            // lane q reads rank q's pair and flags (C <= 16): one round of distributed
+            // shared-memory loads, then warp reductions and a scan over the ranks
+            const long long kq = lane < C ? *cluster.map_shared_rank(&sm->kmin, lane) : kInf;
+            int nq = lane < C ? *cluster.map_shared_rank(&sm->cnt, lane) : 0;
+            int err = lane < C ? *cluster.map_shared_rank(&sm->err, lane) : 0;
+            long long kmin = kq;
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) {
-                    lo += __shfl_xor_sync(0xffffffffu, lo, off);
-                    all += __shfl_xor_sync(0xffffffffu, all, off);
-                }
-                offset = lo;
-                s = all;
+            for (int off = 16; off >= 1; off >>= 1) {
+                kmin = min_ll(kmin, __shfl_xor_sync(full, kmin, off));
+                err |= __shfl_xor_sync(full, err, off);
             }
+            nq = kq == kmin ? nq : 0;
+            int oq = nq;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(full, oq, off);
+                if (lane >= off) oq += y;
+            }
+            const int64_t s = __shfl_sync(full, oq, 31);
+            oq -= nq;   // rank lane's first position in the list
+            const int my_off = __shfl_sync(full, oq, rank), my_cnt = __shfl_sync(full, nq, rank);
+            const double tblock = __longlong_as_double(kmin);
             const bool go = (tblock <= E.t_end) && s > 0 && err == 0 && nsteps < E.max_steps;
             if (!go) {
                 if (rank == 0 && tid == 0) {
@@ -444,27 +574,68 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
                 }
                 break;
             }
-            int pos = (int)offset + wbase + incl - cnt;
-            for (int64_t q = s0; q < s1; ++q)
-                if (key[q] == kmin) act[pos++] = (int32_t)q;
-            // ---- predict every particle of the member to the block time
-            predict_chunk(E, base, c0, c1, tblock);
-            __threadfence();
-            cluster.sync();
-            // ---- force and correction
-            if (s > kEnsSplitMax) {
-                // i-split: this CTA's share against every j, in rounds of kEnsSlots through
-                // its own slots, each round corrected by four-lane groups
+            if (warp == 0 && lane < C) {
+                sm->seg_off[lane] = oq;
+                sm->seg_start[lane] = lane * (int)chunk;
+            }
+            if (s <= kEnsSplitMax) {
+                // ---- few active particles: every CTA takes all of them against its own
+                // j-share (its chunk, predicted by itself), so the i-particles are
+                // predicted where they are used and no barrier separates prediction
+                // from force. The list is gathered into shared memory.
+                __syncthreads();
+                for (int p = tid; p < (int)s; p += kEnsThreads) {
+                    int q = 0;
+                    while (q + 1 < C && sm->seg_off[q + 1] <= p) ++q;
+                    sm->list[p] = act[sm->seg_start[q] + p - sm->seg_off[q]];
+                }
+                predict_chunk(E, base, c0, c1, tblock);
+                __syncthreads();
+                if (c1 > c0) {
+                    cta_force_any<true>(E, base, sm->list, 0, s, c0, c1, eps2f, part, (int64_t)rank * s, sm,
+                                        ds_of_time(tblock));
+                } else {
+                    for (int64_t q = tid; q < s * 7; q += kEnsThreads)
+                        part[((int64_t)rank * s + q / 7) * kPartStride + q % 7] = make_float2(0.f, 0.f);
+                }
+                cluster.sync();
+                if (tid == 0) sm->err = 0;
+                // each CTA corrects its own active particles (positions my_off ...
+                // my_off + my_cnt of the list), summing the ranks' partials in rank order
+                const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
+                for (int b0 = 0; b0 < my_cnt; b0 += kEnsThreads / 4) {
+                    const int kk = b0 + (tid >> 2);
+                    const bool live = kk < my_cnt;
+                    const int p = my_off + (live ? kk : 0);
+                    const int64_t i = base + sm->list[p];
+                    const GroupState g = load_group(H, i);
+                    double an, kn;
+                    sum_partials(part, s, p, cq, C, an, kn);
+                    flags |= correct_group(H, i, g, live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                    if (live && (tid & 3) == 3) E.t2[i] = rn_ds_pack(tblock);
+                }
+                // the keys and states just written belong to this CTA: a CTA barrier
+                // orders them before the next scan and prediction
+                __syncthreads();
+            } else {
+                // ---- many active particles: the list in rank order into idx2, all j
+                // predicted; each CTA takes an even share of the list against every j
+                // (no reduction) in rounds of kEnsSlots through its own slots, each
+                // round corrected by four-lane groups
+                int32_t *list = E.idx2 + base;
+                for (int k = tid; k < my_cnt; k += kEnsThreads) list[my_off + k] = act[c0 + k];
+                predict_chunk(E, base, c0, c1, tblock);
+                cluster.sync();
+                if (tid == 0) sm->err = 0;
                 const int64_t share = (s + C - 1) / C;
                 const int64_t p0 = (int64_t)rank * share < s ? (int64_t)rank * share : s;
                 const int64_t p1 = p0 + share < s ? p0 + share : s;
                 const int64_t slot0 = (int64_t)rank * kEnsSlots;
-                const int cq = (tid & 3) < 3 ? (tid & 3) : 2;
-                const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
                 for (int64_t r0 = p0; r0 < p1; r0 += kEnsSlots) {
                     const int64_t r1 = r0 + kEnsSlots < p1 ? r0 + kEnsSlots : p1;
-                    cta_force_any(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
+                    cta_force_any<false>(E, base, list, r0, r1, 0, N, eps2f, part, slot0, sm);
                     __syncthreads();
+                    const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
                     for (int64_t b0 = r0; b0 < r1; b0 += kEnsThreads / 4) {
                         const int64_t pp = b0 + (tid >> 2);
                         const bool live = pp < r1;
@@ -472,44 +643,15 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
                         const float2 *src = part + (slot0 + pps - r0) * kPartStride;
                         const float2 va = __ldcg(src + cq), vk = __ldcg(src + 3 + cq);
                         const double an = (double)va.x + (double)va.y, kn = (double)vk.x + (double)vk.y;
-                        flags |= correct_group(H, base + act[pps], live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                        const int64_t i = base + list[pps];
+                        flags |= correct_group(H, i, live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
+                        if (live && (tid & 3) == 3) E.t2[i] = rn_ds_pack(tblock);
                     }
                     __syncthreads();
                 }
-            } else {
-                // every CTA takes an even-aligned share of j (pair records stay whole);
-                // 32-bit division (N < 2^19)
-                const int64_t jcs = (int64_t)((((uint32_t)N + (uint32_t)C - 1u) / (uint32_t)C + 1u) / 2u * 2u);
-                const int64_t j0 = (int64_t)rank * jcs < N ? (int64_t)rank * jcs : N;
-                const int64_t j1 = j0 + jcs < N ? j0 + jcs : N;
-                if (j1 > j0) {
-                    cta_force_any(E, base, act, 0, s, j0, j1, eps2f, part, (int64_t)rank * s, sm);
-                } else {
-                    for (int64_t q = tid; q < s * 7; q += kEnsThreads)
-                        part[((int64_t)rank * s + q / 7) * kPartStride + q % 7] = make_float2(0.f, 0.f);
-                }
-                __threadfence();
+                // particles of every chunk were corrected: a cluster barrier before the
+                // next scan
                 cluster.sync();
-                // four lanes per particle (correct_group); lane q reduces component min(q, 2)
-                // of a and k over the ranks' partials in rank order
-                const int64_t groups = (int64_t)C * (kEnsThreads / 4);
-                const int64_t gid = (int64_t)rank * (kEnsThreads / 4) + (tid >> 2);
-                const int cq = (tid & 3) < 3 ? (tid & 3) : 2;
-                const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
-                for (int64_t b0 = 0; b0 < s; b0 += groups) {
-                    const int64_t pp = b0 + gid;
-                    const bool live = pp < s;
-                    const int64_t pps = live ? pp : 0;
-                    float ha = 0.f, la = 0.f, hk = 0.f, lk = 0.f;
-                    for (int q = 0; q < C; ++q) {
-                        const float2 *src = part + ((int64_t)q * s + pps) * kPartStride;
-                        const float2 va = __ldcg(src + cq), vk = __ldcg(src + 3 + cq);
-                        ds_add(ha, la, va.x, va.y);
-                        ds_add(hk, lk, vk.x, vk.y);
-                    }
-                    const double an = (double)ha + (double)la, kn = (double)hk + (double)lk;
-                    flags |= correct_group(H, base + act[pps], live, tblock, an, kn, E.eta, E.dt_max, E.dt_min);
-                }
             }
             if (rank == 0 && tid == 0) {
                 E.steps[2 * mem] += 1;
@@ -517,9 +659,6 @@ __global__ void __launch_bounds__(kEnsThreads, 512 / kEnsThreads) ensemble_kerne
                 E.inter[mem] += (double)s * (double)N;
             }
             ++nsteps;
-            __threadfence();
-            cluster.sync();
-            if (tid == 0) sm->err = 0;
         }
         // ---- energy at the end of this launch
         __threadfence();
@@ -551,9 +690,10 @@ struct nb_ensemble {
     int32_t *order = nullptr;
     double *m = nullptr, *x = nullptr, *v = nullptr, *a = nullptr, *k = nullptr, *t = nullptr, *dt = nullptr,
            *tn = nullptr;
-    float2 *x2 = nullptr, *v2 = nullptr, *a2 = nullptr, *k2 = nullptr;
+    float2 *x2 = nullptr, *v2 = nullptr, *a2 = nullptr, *k2 = nullptr, *t2 = nullptr;
+    float *m32 = nullptr;
     float4 *jh = nullptr, *jl = nullptr, *jv = nullptr;
-    int32_t *idx = nullptr;
+    int32_t *idx = nullptr, *idx2 = nullptr;
     float2 *part = nullptr;
     int32_t *queue = nullptr, *ready = nullptr, *status = nullptr;
     int64_t *steps = nullptr;
@@ -568,8 +708,8 @@ void ensemble_free(nb_ensemble *e)
 {
     if (!e) return;
     void *ptrs[] = {e->off, e->eps2, e->order, e->m, e->x, e->v, e->a, e->k, e->t, e->dt, e->tn, e->x2, e->v2,
-                    e->a2, e->k2, e->jh, e->jl, e->jv,
-                    e->idx, e->part, e->queue, e->ready, e->status, e->steps, e->inter, e->energy, e->stage};
+                    e->a2, e->k2, e->t2, e->m32, e->jh, e->jl, e->jv,
+                    e->idx, e->idx2, e->part, e->queue, e->ready, e->status, e->steps, e->inter, e->energy, e->stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete e;
@@ -645,8 +785,10 @@ cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_
     E.np = e->ntot;
     E.m = e->m; E.x = e->x; E.v = e->v; E.a = e->a; E.k = e->k; E.t = e->t; E.dt = e->dt; E.tn = e->tn;
     E.x2 = e->x2; E.v2 = e->v2; E.a2 = e->a2; E.k2 = e->k2;
+    E.t2 = e->t2; E.m32 = e->m32;
     E.jh = e->jh; E.jl = e->jl; E.jv = e->jv;
     E.idx = e->idx;
+    E.idx2 = e->idx2;
     E.part = e->part;
     E.queue = e->queue;
     E.ready = e->ready;
@@ -755,8 +897,11 @@ nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, cons
     for (double **p : {&e->x, &e->v, &e->a, &e->k}) ECK(ealloc(p, 3 * n));
     for (double **p : {&e->t, &e->dt, &e->tn}) ECK(ealloc(p, n));
     for (float2 **p : {&e->x2, &e->v2, &e->a2, &e->k2}) ECK(ealloc(p, 3 * n));
+    ECK(ealloc(&e->t2, n));
+    ECK(ealloc(&e->m32, n));
     for (float4 **p : {&e->jh, &e->jl, &e->jv}) ECK(ealloc(p, n));
     ECK(ealloc(&e->idx, n));
+    ECK(ealloc(&e->idx2, n));
     ECK(ealloc(&e->part, (size_t)e->nclusters * kEnsPartPerCluster * kPartStride));
     ECK(ealloc(&e->queue, 1));
     ECK(ealloc(&e->ready, nc));
@@ -789,6 +934,8 @@ nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, cons
     ECK(cudaMemsetAsync(e->a2, 0, 3 * n * sizeof(float2), st));
     ECK(cudaMemsetAsync(e->k2, 0, 3 * n * sizeof(float2), st));
     ECK(cudaMemsetAsync(e->t, 0, n * sizeof(double), st));
+    ECK(cudaMemsetAsync(e->t2, 0, n * sizeof(float2), st));
+    ens_to_f32<<<blocks, 256, 0, st>>>(e->m, e->m32, n);
     ECK(cudaMemsetAsync(e->ready, 0, nc * sizeof(int32_t), st));
     ECK(cudaMemsetAsync(e->status, 0, nc * sizeof(int32_t), st));
     ECK(cudaMemsetAsync(e->steps, 0, 2 * nc * sizeof(int64_t), st));
