@@ -57,6 +57,12 @@ constexpr int kEnsSplitMax = 2048;
 constexpr int kEnsPartPerCluster = 16 * kEnsSplitMax;   // C * s_max entries of 8 float2
 constexpr int kEnsSlots = kEnsPartPerCluster / 16;       // entries per CTA in the i-split and start-up rounds
 constexpr int64_t kEnsMaxN = int64_t(1) << 19;          // largest system one cluster takes
+// Dynamic shared memory: a CTA's whole j-share as pair records for the small-s
+// force (chunks of up to 2 kJBufPairs - 64 particles; larger chunks stream
+// j-tiles from global memory), its first kEnsTile / 2 records the j-tile of the
+// streamed force.
+constexpr int kJBufPairs = 1024;
+constexpr size_t kEnsDynSmem = kJBufPairs * sizeof(JPair);
 
 struct EnsArgs {
     int32_t nc;
@@ -83,7 +89,6 @@ struct EnsArgs {
 };
 
 struct EnsSmem {
-    JPair tile[kEnsTile / 2];   // a j-tile as pair records (two particles' fields per float4)
     int32_t list[kEnsSplitMax];  // the active list of a block step with s <= kEnsSplitMax
     double dred[kEnsThreads / 32][2];
     long long kmin;              // this CTA's smallest key and how many of its particles have it
@@ -140,16 +145,16 @@ __device__ __forceinline__ void predict_chunk(const EnsArgs &E, int64_t base, in
 
 // Records of j in [j0, j1) of one member into shared memory as pair records
 // (the layout of the packed pair arithmetic), far-away massless padding past j1.
-__device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_t jt, int64_t j1, EnsSmem *sm)
+__device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_t jt, int64_t j1, JPair *tile)
 {
     const int q = threadIdx.x;
     const int64_t j = jt + q;
     if (j < j1) {
         const float4 h = E.jh[base + j], l = E.jl[base + j], w = E.jv[base + j];
-        jrec_store(sm->tile, q, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
+        jrec_store(tile, q, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
     } else {
         const float far = (float)kPadPos;
-        jrec_store(sm->tile, q, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        jrec_store(tile, q, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -161,7 +166,7 @@ __device__ __forceinline__ void load_tile(const EnsArgs &E, int64_t base, int64_
 // not synchronised with this one).
 template <int R, int TJ, bool PRED>
 __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1, int64_t j0,
-                          int64_t j1, float eps2f, float2 *part, int64_t slot0, EnsSmem *sm, DS tb)
+                          int64_t j1, float eps2f, float2 *part, int64_t slot0, JPair *tile, DS tb)
 {
     constexpr int TI = kEnsThreads / TJ;
     constexpr int I = TI * R;
@@ -197,7 +202,7 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
         int fc = 0;
         for (int64_t jt = j0; jt < j1; jt += kEnsTile) {
             __syncthreads();
-            load_tile(E, base, jt, j1, sm);
+            load_tile(E, base, jt, j1, tile);
             __syncthreads();
             const bool masked = jt <= imax && jt + kEnsTile - 1 >= imin;
             // pair records holding real particles in this tile (the rest is padding)
@@ -208,7 +213,7 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
 #pragma unroll 4
                     for (int u = 0; u < CH; ++u) {
                         const int pp = tj + (c0 + u) * TJ;
-                        const float4 *Q = sm->tile[pp].q;
+                        const float4 *Q = tile[pp].q;
                         const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
                         const int64_t ja = jt + 2 * pp;
 #pragma unroll
@@ -219,7 +224,7 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
 #pragma unroll 4
                     for (int u = 0; u < CH; ++u) {
                         const int pp = tj + (c0 + u) * TJ;
-                        const float4 *Q = sm->tile[pp].q;
+                        const float4 *Q = tile[pp].q;
                         const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
 #pragma unroll
                         for (int r = 0; r < R; ++r) pair_packed<false>(q0, q1, q2, q3, q4, ip[r], e2, p[r], false, false);
@@ -258,22 +263,134 @@ __device__ void cta_force(const EnsArgs &E, int64_t base, const int32_t *act, in
 template <bool PRED>
 __device__ __noinline__ void cta_force_any(const EnsArgs &E, int64_t base, const int32_t *act, int64_t p0, int64_t p1,
                                            int64_t j0, int64_t j1, float eps2f, float2 *part, int64_t slot0,
-                                           EnsSmem *sm, DS tb = DS{0.f, 0.f})
+                                           JPair *tile, DS tb = DS{0.f, 0.f})
 {
     const int64_t ni = p1 - p0;
     if (ni <= 0) return;
     // one i-particle per thread group (R = 1; two would not fit the registers of
     // the packed form); TJ threads share it
     if (ni <= 8)
-        cta_force<1, 32, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+        cta_force<1, 32, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, tile, tb);
     else if (ni <= 32)
-        cta_force<1, 8, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+        cta_force<1, 8, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, tile, tb);
     else if (ni <= 64)
-        cta_force<1, 4, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+        cta_force<1, 4, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, tile, tb);
     else if (ni <= 128)
-        cta_force<1, 2, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+        cta_force<1, 2, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, tile, tb);
     else
-        cta_force<1, 1, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, sm, tb);
+        cta_force<1, 1, PRED>(E, base, act, p0, p1, j0, j1, eps2f, part, slot0, tile, tb);
+}
+
+// ------------------------------------------- small-s force on a resident j-share
+
+// Particles [c0, c1) of a member predicted to the block time straight into
+// shared memory as pair records (the CTA's j-share), padded with far-away
+// massless records to a whole number of 32 records (a padding record adds exact
+// zeros).
+__device__ __forceinline__ void predict_share(const EnsArgs &E, int64_t base, int64_t c0, int64_t c1, double tblock,
+                                              JPair *jb)
+{
+    const DS tb = ds_of_time(tblock);
+    const int nj = (int)(c1 - c0);
+    const int npad = (nj + 63) / 64 * 64;
+    const float far = (float)kPadPos;
+    for (int q = threadIdx.x; q < npad; q += kEnsThreads) {
+        if (q < nj) {
+            float4 h, l, w;
+            predict_one(E, base + c0 + q, tb, h, l, w);
+            jrec_store(jb, q, h.x, h.y, h.z, h.w, l.x, l.y, l.z, w.x, w.y, w.z);
+        } else {
+            jrec_store(jb, q, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// One pass of the small-s force: cnt <= kEnsThreads / TJ active particles from
+// list position p0, each shared by TJ threads that split the resident j-share
+// (thread tj takes records tj, tj + TJ, ...; the padding covers the last round),
+// FP32 partials folded into two-sum accumulators every kFoldPairs terms, then
+// summed over the group. The i-particles are predicted here.
+template <int TJ>
+__device__ __forceinline__ void share_pass(const EnsArgs &E, int64_t base, const int32_t *list, int p0, int cnt,
+                                           int64_t c0, int nj, const JPair *jb, float eps2f, float2 *part,
+                                           int64_t slot0, DS tb)
+{
+    constexpr int FP = kFoldPairs / 2;   // records per fold
+    const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+    const bool live = ti < cnt;
+    const int32_t gi = list[p0 + (live ? ti : cnt - 1)];
+    float4 h, l, w;
+    predict_one(E, base + gi, tb, h, l, w);
+    const IPk ip = ipk_of(IPart{h.x, h.y, h.z, l.x, l.y, l.z, w.x, w.y, w.z});
+    const float2 e2 = make_float2(eps2f, eps2f);
+    AccPk p;
+    Acc7 hi, lo;
+    zero(p);
+    zero(hi);
+    zero(lo);
+    const int nrec = ((nj + 1) / 2 + TJ - 1) / TJ;   // records per thread
+    const int64_t self = (int64_t)gi - c0;           // i's place in the share, if it is there
+    if (__any_sync(0xffffffffu, self >= 0 && self < nj)) {
+        for (int k0 = 0; k0 < nrec; k0 += FP) {
+            const int k1 = k0 + FP < nrec ? k0 + FP : nrec;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const int pp = tj + k * TJ;
+                const float4 *Q = jb[pp].q;
+                pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == self, 2 * pp + 1 == self);
+            }
+            fold(hi, lo, p);
+        }
+    } else {
+        for (int k0 = 0; k0 < nrec; k0 += FP) {
+            const int k1 = k0 + FP < nrec ? k0 + FP : nrec;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const float4 *Q = jb[tj + k * TJ].q;
+                pair_packed<false>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, false, false);
+            }
+            fold(hi, lo, p);
+        }
+    }
+    if (TJ > 1) ds_group_reduce7<TJ>(hi, lo);
+    if (tj == 0 && live) {
+        float2 *dst = part + (slot0 + p0 + ti) * kPartStride;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) dst[c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+    }
+}
+
+// All s active particles against the resident j-share of nj particles, in
+// passes whose group width TJ fits the remaining count (256 particles with TJ = 1,
+// then 128 with TJ = 2, ... down to 8 with TJ = 32), so few threads hold a
+// duplicate particle.
+__device__ __noinline__ void share_force(const EnsArgs &E, int64_t base, const int32_t *list, int s, int64_t c0,
+                                         int nj, const JPair *jb, float eps2f, float2 *part, int64_t slot0, DS tb)
+{
+    int done = 0;
+    while (done < s) {
+        const int r = s - done;
+        if (r >= 256) {
+            share_pass<1>(E, base, list, done, 256, c0, nj, jb, eps2f, part, slot0, tb);
+            done += 256;
+        } else if (r >= 128) {
+            share_pass<2>(E, base, list, done, 128, c0, nj, jb, eps2f, part, slot0, tb);
+            done += 128;
+        } else if (r >= 64) {
+            share_pass<4>(E, base, list, done, 64, c0, nj, jb, eps2f, part, slot0, tb);
+            done += 64;
+        } else if (r >= 32) {
+            share_pass<8>(E, base, list, done, 32, c0, nj, jb, eps2f, part, slot0, tb);
+            done += 32;
+        } else if (r > 8) {
+            const int cnt = r < 16 ? r : 16;
+            share_pass<16>(E, base, list, done, cnt, c0, nj, jb, eps2f, part, slot0, tb);
+            done += cnt;
+        } else {
+            share_pass<32>(E, base, list, done, r, c0, nj, jb, eps2f, part, slot0, tb);
+            done += r;
+        }
+    }
 }
 
 // Component cq of a and k of list position p: the C ranks' partials summed in
@@ -387,7 +504,9 @@ __device__ __forceinline__ long long min_ll(long long a, long long b) { return a
 __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kernel(EnsArgs E)
 {
     __shared__ EnsSmem smem;
+    extern __shared__ __align__(16) unsigned char ens_dyn[];
     EnsSmem *sm = &smem;
+    JPair *jbuf = reinterpret_cast<JPair *>(ens_dyn);
     cg::cluster_group cluster = cg::this_cluster();
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -430,7 +549,7 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
             for (int64_t r0 = c0; r0 < c1; r0 += kEnsSlots) {
                 const int64_t r1 = r0 + kEnsSlots < c1 ? r0 + kEnsSlots : c1;
                 const int64_t slot0 = (int64_t)rank * kEnsSlots;
-                cta_force_any<false>(E, base, act, r0, r1, 0, N, eps2f, part, slot0, sm);
+                cta_force_any<false>(E, base, act, r0, r1, 0, N, eps2f, part, slot0, jbuf);
                 __syncthreads();
                 for (int64_t pp = r0 + tid; pp < r1; pp += kEnsThreads) {
                     const float2 *src = part + (slot0 + pp - r0) * kPartStride;
@@ -582,18 +701,27 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 // ---- few active particles: every CTA takes all of them against its own
                 // j-share (its chunk, predicted by itself), so the i-particles are
                 // predicted where they are used and no barrier separates prediction
-                // from force. The list is gathered into shared memory.
+                // from force. The list is gathered into shared memory; the j-share
+                // too, for chunks of up to 2 kJBufPairs - 64 particles.
                 __syncthreads();
                 for (int p = tid; p < (int)s; p += kEnsThreads) {
                     int q = 0;
                     while (q + 1 < C && sm->seg_off[q + 1] <= p) ++q;
                     sm->list[p] = act[sm->seg_start[q] + p - sm->seg_off[q]];
                 }
-                predict_chunk(E, base, c0, c1, tblock);
+                const bool resident = chunk <= 2 * kJBufPairs - 64;
+                if (resident)
+                    predict_share(E, base, c0, c1, tblock, jbuf);
+                else
+                    predict_chunk(E, base, c0, c1, tblock);
                 __syncthreads();
                 if (c1 > c0) {
-                    cta_force_any<true>(E, base, sm->list, 0, s, c0, c1, eps2f, part, (int64_t)rank * s, sm,
-                                        ds_of_time(tblock));
+                    if (resident)
+                        share_force(E, base, sm->list, (int)s, c0, (int)(c1 - c0), jbuf, eps2f, part,
+                                    (int64_t)rank * s, ds_of_time(tblock));
+                    else
+                        cta_force_any<true>(E, base, sm->list, 0, s, c0, c1, eps2f, part, (int64_t)rank * s, jbuf,
+                                            ds_of_time(tblock));
                 } else {
                     for (int64_t q = tid; q < s * 7; q += kEnsThreads)
                         part[((int64_t)rank * s + q / 7) * kPartStride + q % 7] = make_float2(0.f, 0.f);
@@ -633,7 +761,7 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 const int64_t slot0 = (int64_t)rank * kEnsSlots;
                 for (int64_t r0 = p0; r0 < p1; r0 += kEnsSlots) {
                     const int64_t r1 = r0 + kEnsSlots < p1 ? r0 + kEnsSlots : p1;
-                    cta_force_any<false>(E, base, list, r0, r1, 0, N, eps2f, part, slot0, sm);
+                    cta_force_any<false>(E, base, list, r0, r1, 0, N, eps2f, part, slot0, jbuf);
                     __syncthreads();
                     const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
                     for (int64_t b0 = r0; b0 < r1; b0 += kEnsThreads / 4) {
@@ -731,10 +859,14 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
         return cudaSuccess;
     }
     cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsDynSmem) !=
+        cudaSuccess)
+        return cudaErrorInvalidConfiguration;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel, kEnsThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel, kEnsThreads, kEnsDynSmem) !=
+            cudaSuccess ||
         per_sm < 1)
         return cudaErrorInvalidConfiguration;
     const int slots = sms * per_sm;
@@ -748,7 +880,7 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(C * 64);
         cfg.blockDim = dim3(kEnsThreads);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = kEnsDynSmem;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nclu = 0;
@@ -813,7 +945,7 @@ cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(e->cluster * e->nclusters);
     cfg.blockDim = dim3(kEnsThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kEnsDynSmem;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
