@@ -553,10 +553,12 @@ def force_error_report(nb, oracle, nth, sptr, local):
     return out
 
 
-def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
+def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192, tune=True):
     """256 independent Plummer clusters, N_c = round(exp(U[ln 256, ln 8192])) (seeded),
     eps = 4/N_c, equal masses, each with its own block schedule, advanced to t = 1 by
-    one persistent launch of thread-block clusters (mixed precision)."""
+    one persistent launch of thread-block clusters (mixed precision). The launch shape
+    (cluster size, j-split cap) is autotuned on the same ensemble before the timed
+    region; the timed region is nb_ensemble_init + nb_ensemble_run."""
     import ics
     members = ics.ensemble(nc, ics.BASE_SEED + 4, n_lo=n_lo, n_hi=n_hi)
     off = np.zeros(nc + 1, dtype=np.int64)
@@ -569,12 +571,21 @@ def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
     # warm-up on a small ensemble (module load, cluster-occupancy query)
     nb.nb_ensemble_init(c.ctx, off[:3], m[:off[2]], x[:off[2]], v[:off[2]], e2[:2])
     nb.nb_ensemble_run(c.ctx, 1.0 / 64)
+    shape = None
+    if tune:
+        # launch shape (cluster size, j-split cap) tuned on this ensemble, untimed
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        nb.nb_ensemble_autotune(c.ctx, 1.0 / 16)
+        shape = nb.nb_ensemble_get_shape(c.ctx)
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e2v = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+    if shape:
+        nb.nb_ensemble_set_shape(c.ctx, shape[0], shape[2])
     e1.record(stream)
+    shape = nb.nb_ensemble_get_shape(c.ctx)
     E0 = nb.nb_ensemble_energy(c.ctx, nc)
     nb.nb_ensemble_run(c.ctx, T_END)
     e2v.record(stream)
@@ -592,7 +603,8 @@ def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192):
             "ips": _r(total_inter / (run_s + init_s)), "tflops": _r(60 * total_inter / (run_s + init_s) / 1e12, 3),
             "bsps": _r(float(bs.sum()) / run_s), "block_steps": int(bs.sum()),
             "worst_dE": _r(float(dE.max()), 5), "median_dE": _r(float(np.median(dE)), 3),
-            "worst_member": [int(np.argmax(dE)), int(np.diff(off)[int(np.argmax(dE))])]}
+            "worst_member": [int(np.argmax(dE)), int(np.diff(off)[int(np.argmax(dE))])],
+            "shape": {"cluster": shape[0], "clusters": shape[1], "split_cap": shape[2], "tuned": bool(tune)}}
 
 
 def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):

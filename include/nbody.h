@@ -332,6 +332,34 @@ nb_status nb_ensemble_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *particle
 /* Full concatenated state of all systems (view->n = offsets[nc]). */
 nb_status nb_ensemble_get_state(nb_ctx *ctx, nb_state_view *view);
 
+/* Launch shape for the loaded ensemble. cluster: CTAs per thread-block cluster,
+ * 2, 4, 8 or 16 (0: the default, the largest of 16, 8 and 4 whose co-resident
+ * clusters keep at least 90 % of the device's CTA slots busy). split_cap: the
+ * largest block (active count s) taken by the j-split, where every CTA of the
+ * cluster computes all active particles against its own share of j and the
+ * shares' partial forces are summed in rank order; larger blocks are dealt out
+ * by i, each CTA taking a share of them against all j (0: the default,
+ * min(largest system, 8192); capped at 8192). The partial-force buffer
+ * (clusters x cluster x split_cap slots of 64 bytes) grows as needed. Results
+ * depend on the shape through the order of the partial sums; one shape gives
+ * the same bits on every run. NB_ERR_ARG for a cluster size this device cannot
+ * keep resident. */
+nb_status nb_ensemble_set_shape(nb_ctx *ctx, int32_t cluster, int32_t split_cap);
+
+/* The current shape: cluster size, co-resident clusters, split cap (any may be NULL). */
+nb_status nb_ensemble_get_shape(nb_ctx *ctx, int32_t *cluster, int32_t *nclusters, int32_t *split_cap);
+
+/* Autotuner of the ensemble launch: advances the loaded ensemble by
+ * t_probe (<= 0: the configuration's dt_max) under every cluster size of {16,
+ * 8, 4} that the device keeps resident and every split cap of {min(largest
+ * system, 8192), 4096, 2048, 1024} not above the first, timing each probe with
+ * CUDA events and restoring the state after it; keeps the fastest shape (a
+ * probe that ends with a status error does not count). best_ms (may be NULL)
+ * receives the fastest probe's time. The ensemble's state afterwards is
+ * bitwise the state before the call; it allocates a device copy of that state
+ * (about 13 doubles and 13 float pairs per particle) for the duration. */
+nb_status nb_ensemble_autotune(nb_ctx *ctx, double t_probe, float *best_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,11 +15,14 @@
 // construction (every decision is taken from values that all CTAs read the
 // same way), so every CTA reaches every barrier; no software spin-wait exists.
 //
-// Force work per block step: with many active particles (s > kEnsSplitMax) each CTA
-// takes a share of them against all of the system's j (no reduction needed);
-// otherwise every CTA takes all of them against a 1/C share of the j, which
-// keeps every CTA's i-blocks full, and the partials are summed in rank order by
-// the CTA that owns each active particle.
+// Particles are dealt to the cluster's CTAs in even chunks; a CTA predicts,
+// corrects and scans the keys of its own chunk. Force work per block step: every
+// CTA takes all s active particles against its own chunk as j (the j-split,
+// j-share resident in shared memory for chunks of up to 1984 particles), and the
+// partials are summed in rank order by the CTA that owns each active particle;
+// blocks too large for the j-split's partial slots or shared-memory list (s >
+// kEnsSplitCap) are dealt out by i instead, each CTA taking a share of them
+// against all of the system's j (no reduction needed).
 //
 // This file is compiled with -fmad=false (the FP64 corrector must round like
 // the CPU oracle); the FP32 pair arithmetic uses explicit fused multiply-adds.
@@ -51,11 +54,14 @@ namespace {
 #endif
 constexpr int kEnsThreads = NB_ENS_THREADS;   // threads per CTA (and particles per j-tile)
 constexpr int kEnsTile = kEnsThreads;
-// j-split (every CTA takes all active i) when s <= this; on the 256-system
-// workload with 8-CTA clusters: 2048 2.42 s, 1024 2.45 s, 512 2.46 s
-constexpr int kEnsSplitMax = 2048;
-constexpr int kEnsPartPerCluster = 16 * kEnsSplitMax;   // C * s_max entries of 8 float2
-constexpr int kEnsSlots = kEnsPartPerCluster / 16;       // entries per CTA in the i-split and start-up rounds
+// Largest block (active count s) taken by the j-split: every CTA runs all active
+// particles against its own j-share and the partials are summed across the
+// cluster, which needs C * s partial slots per cluster (8 float2 each) and the
+// active list in shared memory. On the 256-system workload (8-CTA clusters),
+// with larger blocks left to the i-split: 1024 2.16 s, 2048 2.10 s, 4096 2.01 s,
+// 6144 1.98 s, 8192 (every block) 1.97 s. Members of up to this many particles
+// never take the i-split.
+constexpr int kEnsSplitCap = 8192;
 constexpr int64_t kEnsMaxN = int64_t(1) << 19;          // largest system one cluster takes
 // Dynamic shared memory: a CTA's whole j-share as pair records for the small-s
 // force (chunks of up to 2 kJBufPairs - 64 particles; larger chunks stream
@@ -86,10 +92,11 @@ struct EnsArgs {
     double *energy;          // [nc][16][2] K, W per cluster rank after the last launch
     double t_end, eta, dt_max, dt_min;
     int64_t max_steps;       // per member and launch
+    int64_t part_cap;        // partial slots per cluster (C * the j-split's largest s)
+    int32_t s_cap;           // the j-split's largest s (<= kEnsSplitCap)
 };
 
 struct EnsSmem {
-    int32_t list[kEnsSplitMax];  // the active list of a block step with s <= kEnsSplitMax
     double dred[kEnsThreads / 32][2];
     long long kmin;              // this CTA's smallest key and how many of its particles have it
     int cnt;
@@ -511,7 +518,8 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
     const int C = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float2 *part = E.part + (int64_t)(blockIdx.x / C) * kEnsPartPerCluster * kPartStride;
+    float2 *part = E.part + (int64_t)(blockIdx.x / C) * E.part_cap * kPartStride;
+    const int64_t slots = E.part_cap / C;   // partial slots per CTA (i-split and start-up rounds)
     if (tid == 0) {
         sm->err = 0;
         sm->cnt = 0;
@@ -544,11 +552,11 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
             predict_chunk(E, base, c0, c1, 0.0);
             __threadfence();
             cluster.sync();
-            // own particles in rounds of kEnsSlots: sums into this CTA's slots, then a, k,
+            // own particles in rounds of `slots`: sums into this CTA's slots, then a, k,
             // their double-single copies and the first step per particle
-            for (int64_t r0 = c0; r0 < c1; r0 += kEnsSlots) {
-                const int64_t r1 = r0 + kEnsSlots < c1 ? r0 + kEnsSlots : c1;
-                const int64_t slot0 = (int64_t)rank * kEnsSlots;
+            for (int64_t r0 = c0; r0 < c1; r0 += slots) {
+                const int64_t r1 = r0 + slots < c1 ? r0 + slots : c1;
+                const int64_t slot0 = (int64_t)rank * slots;
                 cta_force_any<false>(E, base, act, r0, r1, 0, N, eps2f, part, slot0, jbuf);
                 __syncthreads();
                 for (int64_t pp = r0 + tid; pp < r1; pp += kEnsThreads) {
@@ -697,7 +705,16 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 sm->seg_off[lane] = oq;
                 sm->seg_start[lane] = lane * (int)chunk;
             }
-            if (s <= kEnsSplitMax) {
+            // the j-split's active list sits in dynamic shared memory after the
+            // resident j-share (or after the streamed j-tile). Its place, and so the
+            // choice between j-split and i-split, follows from the chunk size alone,
+            // the same in every CTA of the cluster: a choice that differed between
+            // CTAs would pair up different cluster barriers.
+            const bool resident = chunk <= 2 * kJBufPairs - 64;
+            const int nj = (int)(c1 - c0);
+            const int list_rec = resident ? (int)((chunk + 63) / 64 * 32) : kEnsTile / 2;
+            int32_t *slist = reinterpret_cast<int32_t *>(jbuf + list_rec);
+            if (s <= E.s_cap && s * (int64_t)sizeof(int32_t) <= (int64_t)kEnsDynSmem - list_rec * (int64_t)sizeof(JPair)) {
                 // ---- few active particles: every CTA takes all of them against its own
                 // j-share (its chunk, predicted by itself), so the i-particles are
                 // predicted where they are used and no barrier separates prediction
@@ -707,9 +724,8 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 for (int p = tid; p < (int)s; p += kEnsThreads) {
                     int q = 0;
                     while (q + 1 < C && sm->seg_off[q + 1] <= p) ++q;
-                    sm->list[p] = act[sm->seg_start[q] + p - sm->seg_off[q]];
+                    slist[p] = act[sm->seg_start[q] + p - sm->seg_off[q]];
                 }
-                const bool resident = chunk <= 2 * kJBufPairs - 64;
                 if (resident)
                     predict_share(E, base, c0, c1, tblock, jbuf);
                 else
@@ -717,10 +733,10 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 __syncthreads();
                 if (c1 > c0) {
                     if (resident)
-                        share_force(E, base, sm->list, (int)s, c0, (int)(c1 - c0), jbuf, eps2f, part,
+                        share_force(E, base, slist, (int)s, c0, nj, jbuf, eps2f, part,
                                     (int64_t)rank * s, ds_of_time(tblock));
                     else
-                        cta_force_any<true>(E, base, sm->list, 0, s, c0, c1, eps2f, part, (int64_t)rank * s, jbuf,
+                        cta_force_any<true>(E, base, slist, 0, s, c0, c1, eps2f, part, (int64_t)rank * s, jbuf,
                                             ds_of_time(tblock));
                 } else {
                     for (int64_t q = tid; q < s * 7; q += kEnsThreads)
@@ -735,7 +751,7 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                     const int kk = b0 + (tid >> 2);
                     const bool live = kk < my_cnt;
                     const int p = my_off + (live ? kk : 0);
-                    const int64_t i = base + sm->list[p];
+                    const int64_t i = base + slist[p];
                     const GroupState g = load_group(H, i);
                     double an, kn;
                     sum_partials(part, s, p, cq, C, an, kn);
@@ -748,7 +764,7 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
             } else {
                 // ---- many active particles: the list in rank order into idx2, all j
                 // predicted; each CTA takes an even share of the list against every j
-                // (no reduction) in rounds of kEnsSlots through its own slots, each
+                // (no reduction) in rounds of `slots` through its own slots, each
                 // round corrected by four-lane groups
                 int32_t *list = E.idx2 + base;
                 for (int k = tid; k < my_cnt; k += kEnsThreads) list[my_off + k] = act[c0 + k];
@@ -758,9 +774,9 @@ __global__ void __launch_bounds__(kEnsThreads, NB_ENS_MIN_BLOCKS) ensemble_kerne
                 const int64_t share = (s + C - 1) / C;
                 const int64_t p0 = (int64_t)rank * share < s ? (int64_t)rank * share : s;
                 const int64_t p1 = p0 + share < s ? p0 + share : s;
-                const int64_t slot0 = (int64_t)rank * kEnsSlots;
-                for (int64_t r0 = p0; r0 < p1; r0 += kEnsSlots) {
-                    const int64_t r1 = r0 + kEnsSlots < p1 ? r0 + kEnsSlots : p1;
+                const int64_t slot0 = (int64_t)rank * slots;
+                for (int64_t r0 = p0; r0 < p1; r0 += slots) {
+                    const int64_t r1 = r0 + slots < p1 ? r0 + slots : p1;
                     cta_force_any<false>(E, base, list, r0, r1, 0, N, eps2f, part, slot0, jbuf);
                     __syncthreads();
                     const HState H{E.x, E.v, E.a, E.k, E.t, E.dt, E.tn, E.x2, E.v2, E.a2, E.k2, E.np};
@@ -813,6 +829,10 @@ struct nb_ensemble {
     int32_t nc = 0;
     int64_t ntot = 0;
     int cluster = 0, nclusters = 0;
+    int32_t s_cap = 0;      // the j-split's largest block: min(largest member, kEnsSplitCap) by default
+    int64_t nmax = 0;       // largest member
+    size_t part_alloc = 0;  // float2 entries allocated in part
+    double t_now = 0.0;     // time every member is at
     int64_t *off = nullptr;
     double *eps2 = nullptr;
     int32_t *order = nullptr;
@@ -850,6 +870,41 @@ void ensemble_free(nb_ensemble *e)
 // (14 clusters, 224 of 304 CTAs) where 8-CTA clusters fill 288: measured on the
 // 256-cluster workload, 4.37 s with 16 against 2.46 s with 8 (3.4 s with 4,
 // 6.2 s with 2: smaller clusters lengthen every system's block step).
+static cudaError_t ensemble_attrs()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t err = cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsDynSmem);
+    if (err != cudaSuccess) return err;
+    done = true;
+    return cudaSuccess;
+}
+
+// Clusters of C CTAs the device keeps resident at once (0: C does not run).
+static int ensemble_clusters(int C)
+{
+    if (ensemble_attrs() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * 64);
+    cfg.blockDim = dim3(kEnsThreads);
+    cfg.dynamicSmemBytes = kEnsDynSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclu = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclu, ensemble_kernel, &cfg) != cudaSuccess || nclu < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nclu;
+}
+
 static cudaError_t ensemble_shape(int *cluster, int *nclusters)
 {
     static int c_cached = 0, n_cached = 0;
@@ -858,10 +913,8 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
         *nclusters = n_cached;
         return cudaSuccess;
     }
-    cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (cudaFuncSetAttribute(ensemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEnsDynSmem) !=
-        cudaSuccess)
-        return cudaErrorInvalidConfiguration;
+    cudaError_t err = ensemble_attrs();
+    if (err != cudaSuccess) return err;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -872,22 +925,8 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
     const int slots = sms * per_sm;
     int best_c = 0, best_n = 0;
     for (int C : {16, 8, 4}) {
-        cudaLaunchConfig_t cfg{};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(C * 64);
-        cfg.blockDim = dim3(kEnsThreads);
-        cfg.dynamicSmemBytes = kEnsDynSmem;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclu = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclu, ensemble_kernel, &cfg) != cudaSuccess || nclu < 1) {
-            cudaGetLastError();
-            continue;
-        }
+        const int nclu = ensemble_clusters(C);
+        if (nclu < 1) continue;
         if (!best_c) {   // fallback: the largest size that runs at all
             best_c = C;
             best_n = nclu;
@@ -898,7 +937,6 @@ static cudaError_t ensemble_shape(int *cluster, int *nclusters)
             break;
         }
     }
-    cudaGetLastError();
     if (!best_c) return cudaErrorInvalidConfiguration;
     c_cached = best_c;
     n_cached = best_n;
@@ -922,6 +960,8 @@ cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_
     E.idx = e->idx;
     E.idx2 = e->idx2;
     E.part = e->part;
+    E.s_cap = e->s_cap;
+    E.part_cap = (int64_t)e->cluster * e->s_cap;
     E.queue = e->queue;
     E.ready = e->ready;
     E.status = e->status;
@@ -978,6 +1018,20 @@ cudaError_t ealloc(T **p, size_t count)
         }                                                                                             \
     } while (0)
 
+// Partial slots for the current shape: nclusters * cluster * s_cap entries of
+// kPartStride (grown, never shrunk).
+nb_status ens_part_reserve(nb_ctx *ctx, nb_ensemble *e)
+{
+    const size_t need = (size_t)e->nclusters * e->cluster * e->s_cap * kPartStride;
+    if (need <= e->part_alloc) return NB_OK;
+    if (e->part) cudaFree(e->part);
+    e->part = nullptr;
+    e->part_alloc = 0;
+    ECK(ealloc(&e->part, need));
+    e->part_alloc = need;
+    return NB_OK;
+}
+
 nb_status ens_sync(nb_ctx *ctx, nb_ensemble *e)
 {
     cudaStream_t st = nb_ctx_stream(ctx);
@@ -992,6 +1046,51 @@ nb_status ens_sync(nb_ctx *ctx, nb_ensemble *e)
     if (any & kStUnderflow) return nb_ctx_fail(ctx, NB_ERR_DT_UNDERFLOW, "ensemble: time step below dt_min");
     if (any & kStSteps) return nb_ctx_fail(ctx, NB_ERR_STATE, "ensemble: block-step cap reached");
     return nb_ctx_fail(ctx, NB_ERR_CUDA, "ensemble: device error");
+}
+
+// Device copies of the state a run changes (for the tuner's probes).
+struct EnsBackup {
+    double *d = nullptr;
+    float2 *f = nullptr;
+    int32_t *i = nullptr;
+    int64_t *l = nullptr;
+    ~EnsBackup()
+    {
+        for (void *p : {(void *)d, (void *)f, (void *)i, (void *)l})
+            if (p) cudaFree(p);
+    }
+};
+
+static void ens_copy_state(nb_ensemble *e, EnsBackup &b, bool save, cudaStream_t st)
+{
+    const int64_t n = e->ntot, nc = e->nc;
+    auto cp = [&](void *live, void *keep, size_t bytes) {
+        if (save)
+            cudaMemcpyAsync(keep, live, bytes, cudaMemcpyDeviceToDevice, st);
+        else
+            cudaMemcpyAsync(live, keep, bytes, cudaMemcpyDeviceToDevice, st);
+    };
+    double *dd = b.d;
+    for (double *p : {e->x, e->v, e->a, e->k}) {
+        cp(p, dd, 3 * n * sizeof(double));
+        dd += 3 * n;
+    }
+    for (double *p : {e->t, e->dt, e->tn}) {
+        cp(p, dd, n * sizeof(double));
+        dd += n;
+    }
+    cp(e->inter, dd, nc * sizeof(double));
+    dd += nc;
+    cp(e->energy, dd, 32 * nc * sizeof(double));
+    float2 *ff = b.f;
+    for (float2 *p : {e->x2, e->v2, e->a2, e->k2}) {
+        cp(p, ff, 3 * n * sizeof(float2));
+        ff += 3 * n;
+    }
+    cp(e->t2, ff, n * sizeof(float2));
+    cp(e->ready, b.i, nc * sizeof(int32_t));
+    cp(e->status, b.i + nc, nc * sizeof(int32_t));
+    cp(e->steps, b.l, 2 * nc * sizeof(int64_t));
 }
 
 }  // namespace nb_ens_host
@@ -1034,7 +1133,12 @@ nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, cons
     for (float4 **p : {&e->jh, &e->jl, &e->jv}) ECK(ealloc(p, n));
     ECK(ealloc(&e->idx, n));
     ECK(ealloc(&e->idx2, n));
-    ECK(ealloc(&e->part, (size_t)e->nclusters * kEnsPartPerCluster * kPartStride));
+    for (int32_t c = 0; c < nc; ++c) e->nmax = std::max<int64_t>(e->nmax, offsets[c + 1] - offsets[c]);
+    e->s_cap = (int32_t)std::min<int64_t>(e->nmax, kEnsSplitCap);
+    {
+        const nb_status ps = ens_part_reserve(ctx, e);
+        if (ps != NB_OK) return ps;
+    }
     ECK(ealloc(&e->queue, 1));
     ECK(ealloc(&e->ready, nc));
     ECK(ealloc(&e->status, nc));
@@ -1086,7 +1190,9 @@ nb_status nb_ensemble_run(nb_ctx *ctx, double t_end)
     if (!std::isfinite(t_end)) return nb_ctx_fail(ctx, NB_ERR_ARG, "t_end must be finite");
     const nb_config *cfg = nb_ctx_config(ctx);
     ECK(ensemble_launch(e, t_end, cfg->eta, cfg->dt_max, cfg->dt_min, nb_ctx_stream(ctx)));
-    return ens_sync(ctx, e);
+    const nb_status st = ens_sync(ctx, e);
+    if (st == NB_OK) e->t_now = t_end;
+    return st;
 }
 
 nb_status nb_ensemble_energy(nb_ctx *ctx, double *E)
@@ -1123,6 +1229,118 @@ nb_status nb_ensemble_stats(nb_ctx *ctx, int64_t *block_steps, int64_t *particle
     }
     if (interactions) ECK(cudaMemcpy(interactions, e->inter, e->nc * sizeof(double), cudaMemcpyDeviceToHost));
     return NB_OK;
+}
+
+nb_status nb_ensemble_set_shape(nb_ctx *ctx, int32_t cluster, int32_t split_cap)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    if (cluster != 0 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16)
+        return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: cluster must be 0, 2, 4, 8 or 16");
+    if (split_cap < 0) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: split_cap must be >= 0");
+    int C = 0, ncl = 0;
+    if (cluster == 0) {
+        ECK(ensemble_shape(&C, &ncl));
+    } else {
+        C = cluster;
+        ncl = ensemble_clusters(C);
+        if (ncl < 1) return nb_ctx_fail(ctx, NB_ERR_ARG, "ensemble: that cluster size does not run on this device");
+    }
+    const int64_t cap = split_cap == 0 ? std::min<int64_t>(e->nmax, kEnsSplitCap)
+                                       : std::min<int64_t>(std::min<int64_t>(split_cap, e->nmax), kEnsSplitCap);
+    ECK(cudaStreamSynchronize(nb_ctx_stream(ctx)));
+    e->cluster = C;
+    e->nclusters = ncl;
+    e->s_cap = (int32_t)std::max<int64_t>(cap, 1);
+    return ens_part_reserve(ctx, e);
+}
+
+nb_status nb_ensemble_get_shape(nb_ctx *ctx, int32_t *cluster, int32_t *nclusters, int32_t *split_cap)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    if (cluster) *cluster = e->cluster;
+    if (nclusters) *nclusters = e->nclusters;
+    if (split_cap) *split_cap = e->s_cap;
+    return NB_OK;
+}
+
+nb_status nb_ensemble_autotune(nb_ctx *ctx, double t_probe, float *best_ms)
+{
+    if (!ctx) return NB_ERR_ARG;
+    nb_ensemble *e = nb_ctx_ensemble(ctx);
+    if (!e) return nb_ctx_fail(ctx, NB_ERR_STATE, "no ensemble loaded (call nb_ensemble_init)");
+    const nb_config *cfg = nb_ctx_config(ctx);
+    if (!(t_probe > 0.0)) t_probe = cfg->dt_max;
+    if (!std::isfinite(t_probe)) return nb_ctx_fail(ctx, NB_ERR_ARG, "t_probe must be finite");
+    cudaStream_t st = nb_ctx_stream(ctx);
+    const int64_t n = e->ntot, nc = e->nc;
+    EnsBackup b;
+    ECK(ealloc(&b.d, 15 * n + 33 * nc));
+    ECK(ealloc(&b.f, 13 * n));
+    ECK(ealloc(&b.i, 2 * nc));
+    ECK(ealloc(&b.l, 2 * nc));
+    ens_copy_state(e, b, true, st);
+    ECK(cudaGetLastError());
+    const int C0 = e->cluster, N0 = e->nclusters;
+    const int32_t S0 = e->s_cap;
+    const int64_t top = std::min<int64_t>(e->nmax, kEnsSplitCap);
+    std::vector<int64_t> caps{top};
+    for (int64_t c : {4096, 2048, 1024})
+        if (c < top) caps.push_back(c);
+    cudaEvent_t ev0, ev1;
+    ECK(cudaEventCreate(&ev0));
+    ECK(cudaEventCreate(&ev1));
+    float best = -1.f;
+    int bc = C0, bn = N0;
+    int32_t bs = S0;
+    nb_status rc = NB_OK;
+    for (int C : {16, 8, 4}) {
+        const int ncl = ensemble_clusters(C);
+        if (ncl < 1) continue;
+        for (int64_t cap : caps) {
+            e->cluster = C;
+            e->nclusters = ncl;
+            e->s_cap = (int32_t)cap;
+            rc = ens_part_reserve(ctx, e);
+            if (rc != NB_OK) break;
+            cudaEventRecord(ev0, st);
+            cudaError_t err = ensemble_launch(e, e->t_now + t_probe, cfg->eta, cfg->dt_max, cfg->dt_min, st);
+            cudaEventRecord(ev1, st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(ev1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ev0, ev1);
+            std::vector<int32_t> status(nc);
+            if (err == cudaSuccess)
+                err = cudaMemcpy(status.data(), e->status, nc * sizeof(int32_t), cudaMemcpyDeviceToHost);
+            ens_copy_state(e, b, false, st);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+            if (err != cudaSuccess) {
+                rc = nb_ctx_fail(ctx, NB_ERR_CUDA, cudaGetErrorString(err));
+                break;
+            }
+            bool ok = true;
+            for (int32_t v : status) ok = ok && v == 0;
+            if (ok && (best < 0.f || ms < best)) {
+                best = ms;
+                bc = C;
+                bn = ncl;
+                bs = (int32_t)cap;
+            }
+        }
+        if (rc != NB_OK) break;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    e->cluster = bc;
+    e->nclusters = bn;
+    e->s_cap = bs;
+    if (rc != NB_OK) return rc;
+    if (best < 0.f) return nb_ctx_fail(ctx, NB_ERR_STATE, "ensemble: no probe ran cleanly");
+    if (best_ms) *best_ms = best;
+    return ens_part_reserve(ctx, e);
 }
 
 nb_status nb_ensemble_get_state(nb_ctx *ctx, nb_state_view *view)

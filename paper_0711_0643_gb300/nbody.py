@@ -100,6 +100,9 @@ _SIGS = [
     ("nb_ensemble_energy", C.c_int, [_P, _P]),
     ("nb_ensemble_stats", C.c_int, [_P, _P, _P, _P]),
     ("nb_ensemble_get_state", C.c_int, [_P, _P]),
+    ("nb_ensemble_set_shape", C.c_int, [_P, _I32, _I32]),
+    ("nb_ensemble_get_shape", C.c_int, [_P, _P, _P, _P]),
+    ("nb_ensemble_autotune", C.c_int, [_P, _D, _P]),
 ]
 EXPORTED = [s[0] for s in _SIGS]
 
@@ -391,6 +394,24 @@ def nb_ensemble_get_state(ctx, N):
     view = nb_state_view(N, *[_ptr(arr[key]) for key in ("m", "x", "v", "a", "k", "t", "dt")])
     _check(ctx, load().nb_ensemble_get_state(ctx, C.byref(view)))
     return arr
+
+
+def nb_ensemble_set_shape(ctx, cluster=0, split_cap=0):
+    return _check(ctx, load().nb_ensemble_set_shape(ctx, int(cluster), int(split_cap)))
+
+
+def nb_ensemble_get_shape(ctx):
+    """(cluster, nclusters, split_cap) of the loaded ensemble's launch."""
+    c = C.c_int32(0); n = C.c_int32(0); s = C.c_int32(0)
+    _check(ctx, load().nb_ensemble_get_shape(ctx, C.byref(c), C.byref(n), C.byref(s)))
+    return c.value, n.value, s.value
+
+
+def nb_ensemble_autotune(ctx, t_probe=0.0):
+    """Probes the launch shapes on the loaded ensemble, keeps the fastest; returns its time in ms."""
+    ms = C.c_float(0.0)
+    _check(ctx, load().nb_ensemble_autotune(ctx, float(t_probe), C.byref(ms)))
+    return ms.value
 
 
 # ----------------------------------------------------------------- convenience

@@ -63,12 +63,27 @@ def test_ensemble_initial_state(nb, orc):
         assert abs(E[q] - (Kr + Wr)) < 1e-12 * abs(Kr + Wr), q
 
 
-def test_ensemble_run_conserves_energy_and_lands(nb, orc):
-    mem = _members()
+_ORACLE = {}
+
+
+def _oracle_run(orc, s, t_end):
+    """The oracle's |dE/E| and block steps for member s to t_end (cached)."""
+    key = (s.n, float(s.eps2), float(s.x[0, 0]), t_end)
+    if key not in _ORACLE:
+        sysr = orc.System(s.m, s.x, s.v, s.eps2, nthreads=orc.default_threads())
+        Er0 = sysr.energy()
+        assert sysr.run(t_end) == 0
+        _ORACLE[key] = (abs(sysr.energy() - Er0) / abs(Er0), sysr.counters["block_steps"])
+    return _ORACLE[key]
+
+
+def _run_and_check(nb, orc, mem, t_end, cluster=0, split_cap=0):
     off, m, x, v, e2 = _pack(mem)
-    t_end = 0.25
     with nb.Context() as c:
         nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        if cluster or split_cap:
+            nb.nb_ensemble_set_shape(c.ctx, cluster, split_cap)
+        shape = nb.nb_ensemble_get_shape(c.ctx)
         E0 = nb.nb_ensemble_energy(c.ctx, len(mem))
         nb.nb_ensemble_run(c.ctx, t_end)
         E1 = nb.nb_ensemble_energy(c.ctx, len(mem))
@@ -78,14 +93,75 @@ def test_ensemble_run_conserves_energy_and_lands(nb, orc):
     assert np.all(bs > 0) and np.all(ps >= bs)
     np.testing.assert_allclose(inter, ps * np.diff(off), rtol=0)
     for q, s in enumerate(mem):
-        sysr = orc.System(s.m, s.x, s.v, s.eps2, nthreads=orc.default_threads())
-        Er0 = sysr.energy()
-        assert sysr.run(t_end) == 0
-        dEr = abs(sysr.energy() - Er0) / abs(Er0)
+        dEr, steps_r = _oracle_run(orc, s, t_end)
         dE = abs(E1[q] - E0[q]) / abs(E0[q])
-        print(f"member {q} N={s.n}: |dE/E| {dE:.3e} oracle {dEr:.3e}; steps {bs[q]} oracle "
-              f"{sysr.counters['block_steps']}")
+        print(f"shape {shape} member {q} N={s.n}: |dE/E| {dE:.3e} oracle {dEr:.3e}; steps {bs[q]} oracle {steps_r}")
         assert dE <= 2 * dEr + 1e-9, (q, dE, dEr)
+    return st, shape
+
+
+def test_ensemble_run_conserves_energy_and_lands(nb, orc):
+    _run_and_check(nb, orc, _members(), 0.25)
+
+
+def test_ensemble_i_split_and_cluster_shapes(nb, orc):
+    """A split cap of 16 sends every block of more than 16 active particles through the
+    i-split (each CTA a share of the active particles against all j); clusters of 4 and
+    16 CTAs change the j-shares. Each shape conserves energy like the oracle and gives
+    the same bits on a rerun."""
+    mem = _members()
+    for cluster, cap in ((0, 16), (4, 0), (16, 64)):
+        st, shape = _run_and_check(nb, orc, mem, 0.25, cluster, cap)
+        if cluster:
+            assert shape[0] == cluster
+        if cap:
+            assert shape[2] == cap
+        st2, _ = _run_and_check(nb, orc, mem, 0.25, cluster, cap)
+        for key in ("x", "v", "a", "k", "dt"):
+            np.testing.assert_array_equal(st[key], st2[key])
+
+
+def test_ensemble_autotune_keeps_state(nb, orc):
+    """The tuner's probes leave the state bitwise as it was; the chosen shape is one of
+    the candidates, and the run continues from the restored state."""
+    mem = _members()
+    off, m, x, v, e2 = _pack(mem)
+    nmax = int(np.diff(off).max())
+    with nb.Context() as c:
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        nb.nb_ensemble_run(c.ctx, 0.0625)
+        before = nb.nb_ensemble_get_state(c.ctx, off[-1])
+        E_before = nb.nb_ensemble_energy(c.ctx, len(mem))
+        bs_before = nb.nb_ensemble_stats(c.ctx, len(mem))[0]
+        ms = nb.nb_ensemble_autotune(c.ctx, 1.0 / 64)
+        after = nb.nb_ensemble_get_state(c.ctx, off[-1])
+        cluster, ncl, cap = nb.nb_ensemble_get_shape(c.ctx)
+        np.testing.assert_array_equal(nb.nb_ensemble_energy(c.ctx, len(mem)), E_before)
+        np.testing.assert_array_equal(nb.nb_ensemble_stats(c.ctx, len(mem))[0], bs_before)
+        nb.nb_ensemble_run(c.ctx, 0.125)
+        st = nb.nb_ensemble_get_state(c.ctx, off[-1])
+    print(f"tuned shape: cluster {cluster} x {ncl}, split cap {cap}, probe {ms:.2f} ms")
+    for key in ("x", "v", "a", "k", "t", "dt"):
+        np.testing.assert_array_equal(before[key], after[key])
+    assert cluster in (4, 8, 16) and ncl >= 1 and ms > 0
+    assert cap in [min(nmax, 8192)] + [q for q in (4096, 2048, 1024) if q < min(nmax, 8192)]
+    np.testing.assert_array_equal(st["t"], 0.125)
+
+
+def test_ensemble_shape_arguments(nb):
+    mem = _members()
+    off, m, x, v, e2 = _pack(mem)
+    with nb.Context() as c:
+        with pytest.raises(nb.NbError) as e:
+            nb.nb_ensemble_set_shape(c.ctx, 8, 0)
+        assert e.value.status == nb.NB_ERR_STATE
+        nb.nb_ensemble_init(c.ctx, off, m, x, v, e2)
+        for bad in ((3, 0), (32, 0), (8, -1)):
+            with pytest.raises(nb.NbError) as e:
+                nb.nb_ensemble_set_shape(c.ctx, *bad)
+            assert e.value.status == nb.NB_ERR_ARG
+        nb.nb_ensemble_set_shape(c.ctx, 0, 100000)
+        assert nb.nb_ensemble_get_shape(c.ctx)[2] == int(np.diff(off).max())
 
 
 def test_ensemble_deterministic_and_independent(nb):
