@@ -233,6 +233,46 @@ __host__ __device__ __forceinline__ double recip_pow2(double p) { return dfrom((
 // Bits of the largest power of two <= cand for cand > 0 finite and normal,
 // +inf for +inf, 0 for subnormal cand (frexp/ldexp's answer is then below any
 // normal step bound, which is all the quantisation rule looks at).
+// RN32(x), ties to even, on the integer pipe, for |x| < 2^60; values whose
+// float would be subnormal give 0 (as a flush-to-zero FP32 unit would). False
+// for |x| >= 2^60, infinities and NaN.
+__host__ __device__ __forceinline__ bool rn32_int(double x, float &f)
+{
+    const long long xb = dbits(x);
+    const int E = (int)((xb >> 52) & 0x7ff);
+    if (E >= 1023 + 60) return false;
+    if (E < 1023 - 126) {
+        f = 0.f;
+        return true;
+    }
+    const unsigned sign = (unsigned)((unsigned long long)xb >> 63) << 31;
+    const unsigned long long M = (unsigned long long)xb & ((1ull << 52) - 1);
+    unsigned mh = (unsigned)(M >> 29);
+    const unsigned rem = (unsigned)(M & ((1u << 29) - 1));
+    const bool up = rem > (1u << 28) || (rem == (1u << 28) && (mh & 1u));
+    int Eh = E;
+    if (up && ++mh == (1u << 23)) {
+        mh = 0;
+        ++Eh;
+    }
+    f = ffrom(sign | ((unsigned)(Eh - 896) << 23) | mh);
+    return true;
+}
+
+// f^2 in FP32, flushed to 0 below 2^-126 (a flush-to-zero unit's result). The
+// corrector's step estimate sums three of these in the oracle's order (x^2 +
+// y^2) + z^2 from RN32 copies of FP64 components; the sum counts as in range in
+// [2^-100, 2^120], where a flushed square changes it by under 2^-26 relative.
+__host__ __device__ __forceinline__ float sq_ftz(float f)
+{
+    const float q = f * f;
+    return q < 1.17549435e-38f ? 0.f : q;
+}
+__host__ __device__ __forceinline__ bool norm2_f32_in_range(float S)
+{
+    return S >= 7.88860905e-31f && S <= 1.32922800e+36f;   // 2^-100, 2^120
+}
+
 __host__ __device__ __forceinline__ long long pow2_floor_bits(double cand)
 {
     return dbits(cand) & (long long)0xFFF0000000000000ull;

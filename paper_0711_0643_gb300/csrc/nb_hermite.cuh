@@ -224,32 +224,50 @@ __device__ __forceinline__ int correct_group(const HState &H, int64_t i, const G
     }
     const double a2p = __dadd_rn(a2, scale2(a3, e, dt));
 
-    // lane q gathers the three component squares of vector q (a, k, a2p, a3) by
-    // rotating shuffles and sums them in component order, as dot3 does
-    const double s0 = __dmul_rn(an, an), s1 = __dmul_rn(kn, kn), s2 = __dmul_rn(a2p, a2p), s3 = __dmul_rn(a3, a3);
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    // The step's power of two from the FP32 estimate. Lane q gathers the three
+    // component squares of vector q (a, k, a2p, a3) by rotating shuffles and sums
+    // them in component order, as dot3 does, in FP32 from RN32 copies of the FP64
+    // components made on the integer pipe (the estimate's error stays far inside
+    // its 2^-14 decision window). The FP64 norms are formed only where the
+    // estimate does not decide.
+    float c0f, c1f, c2f, c3f;
+    const bool ok32 = rn32_int(an, c0f) & rn32_int(kn, c1f) & rn32_int(a2p, c2f) & rn32_int(a3, c3f);
+    const float t0 = sq_ftz(c0f), t1 = sq_ftz(c1f), t2 = sq_ftz(c2f), t3 = sq_ftz(c3f);
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const double mine = pick4(s0, s1, s2, s3, (q - r) & 3);   // lane src supplies vector (src - r) & 3
+        const int w = (q - r) & 3;   // lane src supplies vector (src - r) & 3
+        const float mine = w == 0 ? t0 : (w == 1 ? t1 : (w == 2 ? t2 : t3));
         const int src = (q + r) & 3;
-        const double got = __shfl_sync(full, mine, g0 + src);
-        if (src == 0) p0 = got;
-        if (src == 1) p1 = got;
-        if (src == 2) p2 = got;
+        const float got = __shfl_sync(full, mine, g0 + src);
+        if (src == 0) f0 = got;
+        if (src == 1) f1 = got;
+        if (src == 2) f2 = got;
     }
-    const double S = __dadd_rn(__dadd_rn(p0, p1), p2);
-
-    const float fS = __double2float_rn(S);
+    const float fS = (f0 + f1) + f2;
     const float rS = __fsqrt_rn(fS);
     const float rA = __shfl_sync(full, rS, g0), rK = __shfl_sync(full, rS, g0 + 1);
     const float rP = __shfl_sync(full, rS, g0 + 2), rQ = __shfl_sync(full, rS, g0 + 3);
     const float fK = __shfl_sync(full, fS, g0 + 1), fP = __shfl_sync(full, fS, g0 + 2);
-    const unsigned okb = __ballot_sync(full, norm2_in_range(S));
+    const unsigned okb = __ballot_sync(full, ok32 && norm2_f32_in_range(fS));
     long long qb = 0;
     bool pos = true;
     bool decided = aarseth_estimate(rA, rK, rP, rQ, fK, fP, __double2float_rn(eta), qb);
     decided = decided && ((okb >> g0) & 0xFu) == 0xFu;
     if (__any_sync(full, live && !decided)) {
+        const double s0 = __dmul_rn(an, an), s1 = __dmul_rn(kn, kn), s2 = __dmul_rn(a2p, a2p),
+                     s3 = __dmul_rn(a3, a3);
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double mine = pick4(s0, s1, s2, s3, (q - r) & 3);
+            const int src = (q + r) & 3;
+            const double got = __shfl_sync(full, mine, g0 + src);
+            if (src == 0) p0 = got;
+            if (src == 1) p1 = got;
+            if (src == 2) p2 = got;
+        }
+        const double S = __dadd_rn(__dadd_rn(p0, p1), p2);
         const double mag = __dsqrt_rn(S);   // the four magnitudes, one per lane
         const double mA = __shfl_sync(full, mag, g0), mK = __shfl_sync(full, mag, g0 + 1);
         const double mP = __shfl_sync(full, mag, g0 + 2), mQ = __shfl_sync(full, mag, g0 + 3);

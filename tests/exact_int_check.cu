@@ -75,10 +75,63 @@ static int aarseth_mode()
     return 0;
 }
 
+// The corrector's FP32 norms: records of the four vectors' FP64 components (a, k,
+// a2p, a3; 12 values) and eta; RN32 copies on the integer pipe, squares flushed
+// below 2^-126, (x^2 + y^2) + z^2, then the estimate. Writes (decided, power of two).
+static int aarseth32_mode()
+{
+    long long n = 0;
+    if (std::fread(&n, 8, 1, stdin) != 1 || n < 0) return 2;
+    for (long long q = 0; q < n; ++q) {
+        double r[13];
+        if (std::fread(r, 8, 13, stdin) != 13) return 2;
+        float S[4];
+        bool ok = true;
+        for (int v = 0; v < 4; ++v) {
+            float c[3];
+            for (int k = 0; k < 3; ++k) ok = rn32_int(r[3 * v + k], c[k]) && ok;
+            S[v] = (sq_ftz(c[0]) + sq_ftz(c[1])) + sq_ftz(c[2]);
+            ok = ok && norm2_f32_in_range(S[v]);
+        }
+        long long qb = 0;
+        bool decided = ok && aarseth_estimate(std::sqrt(S[0]), std::sqrt(S[1]), std::sqrt(S[2]), std::sqrt(S[3]),
+                                              S[1], S[2], (float)r[12], qb);
+        const double out[2] = {decided ? 1.0 : 0.0, dfrom(qb)};
+        if (std::fwrite(out, 8, 2, stdout) != 2) return 2;
+    }
+    return 0;
+}
+
+// rn32_int against the host's double-to-float conversion (subnormal floats
+// flushed) on random doubles of every exponent below 2^60.
+static long long rn32_check(long long cases)
+{
+    long long bad = 0;
+    for (long long n = 0; n < cases; ++n) {
+        const unsigned long long r = splitmix();
+        const int E = (int)(splitmix() % (1023 + 60));
+        const double y = dfrom((long long)((r & (1ull << 63)) | ((unsigned long long)E << 52) | (r & ((1ull << 52) - 1))));
+        float f = 1.f;
+        const bool ok = rn32_int(y, f);
+        float ref = (float)y;
+        if (std::fabs(ref) < 1.17549435e-38f) ref = 0.f;
+        if (!ok || (f != ref) || (f == 0.f && ref != 0.f)) {
+            if (bad < 5) std::printf("MISMATCH rn32 y=%a got=%a ref=%a\n", y, (double)f, (double)ref);
+            ++bad;
+        }
+    }
+    for (double big : {0x1p60, -0x1p61, 1.0 / 0.0}) {
+        float f;
+        if (rn32_int(big, f)) ++bad;
+    }
+    return bad;
+}
+
 int main(int argc, char **argv)
 {
     if (argc > 1 && std::string(argv[1]) == "quantise") return quantise_mode();
     if (argc > 1 && std::string(argv[1]) == "aarseth") return aarseth_mode();
+    if (argc > 1 && std::string(argv[1]) == "aarseth32") return aarseth32_mode();
     const long long cases = argc > 1 ? std::atoll(argv[1]) : 4000000;
     const unsigned long long edges[] = {0ull, 1ull, 2ull, (1ull << 52) - 1, (1ull << 52) - 2, (1ull << 51),
                                         (1ull << 51) - 1, (1ull << 51) + 1, (1ull << 50), (1ull << 49),
@@ -123,6 +176,7 @@ int main(int argc, char **argv)
             }
         }
     }
+    fails += (int)rn32_check(cases / 4);
     std::printf("cases %lld (div3 accepted %lld, declined %lld), mismatches %d\n", cases, accepted, declined, fails);
     return fails ? 1 : 0;
 }

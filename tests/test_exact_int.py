@@ -114,3 +114,48 @@ def test_fp32_aarseth_estimate_decides_like_the_fp64_step(orc):
     # 2^-14 above and 2^-13 below a power of two); near them it must also decide
     # some (the exact path is not taken for all of them)
     assert decided[0] > 0.99 * len(cases) / 2 and decided[1] > 0.05 * len(cases) / 2, decided
+
+
+def test_fp32_norm_estimate_decides_like_the_fp64_step(orc):
+    """The corrector forms the squared norms of the step estimate in FP32 from RN32 copies
+    of the FP64 components (integer pipe), each square flushed below 2^-126, summed in
+    the oracle's order, and decides only when every norm lies in [2^-100, 2^120]. Wherever
+    it decides, the power of two must be the one below the oracle's FP64 step, also for
+    steps within 10^-4 or 10^-6 of a power of two, vectors with components of very
+    different sizes and cancelling a2p."""
+    import math
+
+    import numpy as np
+    rng = np.random.default_rng(20071108)
+
+    def vec(scale):
+        u = rng.normal(size=3)
+        if rng.uniform() < 0.2:   # one component much smaller than the others
+            u[int(rng.integers(0, 3))] *= 10.0 ** rng.uniform(-12, -3)
+        return u / np.linalg.norm(u) * scale
+
+    cases = []
+    for q in range(20000):
+        a, k, a2p, a3 = (vec(10.0 ** rng.uniform(-8, 8)) for _ in range(4))
+        eta = 0.01
+        if q % 2:
+            c0 = orc.aarseth_dt(a, k, a2p, a3, eta)
+            spread = 1e-4 if q % 4 == 1 else 1e-6
+            target = 2.0 ** round(math.log2(c0)) * (1.0 + rng.uniform(-spread, spread))
+            eta = eta * (target / c0) ** 2
+        cases.append((a, k, a2p, a3, eta))
+    rows = np.array([np.concatenate([a, k, a2p, a3, [eta]]) for a, k, a2p, a3, eta in cases], dtype=np.float64)
+    with tempfile.TemporaryDirectory() as d:
+        exe = _build(d)
+        payload = np.array([len(rows)], dtype=np.int64).tobytes() + rows.tobytes()
+        out = subprocess.run([exe, "aarseth32"], input=payload, capture_output=True, check=True)
+    res = np.frombuffer(out.stdout, dtype=np.float64).reshape(-1, 2)
+    decided = [0, 0]
+    for q, ((a, k, a2p, a3, eta), (dec, qb)) in enumerate(zip(cases, res)):
+        if dec == 0.0:
+            continue
+        decided[q % 2] += 1
+        cand = orc.aarseth_dt(a, k, a2p, a3, eta)
+        m, e = math.frexp(cand)
+        assert qb == math.ldexp(0.5, e), (q, cand, qb)
+    assert decided[0] > 0.99 * len(cases) / 2 and decided[1] > 0.05 * len(cases) / 2, decided
