@@ -195,8 +195,7 @@ ForceArgs force_args(nb_ctx *c, int variant = -1, int split = 0)
 
 int force_grid(nb_ctx *c)
 {
-    const int occ = c->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
-    return c->num_sms * occ;
+    return c->cfg.precision == NB_PREC_FP64 ? c->num_sms * force_f64_ctas_per_sm() : force_mixed_grid(c->num_sms, c->n_tiles);
 }
 
 cudaError_t launch_force(nb_ctx *c, const ForceArgs &F)
@@ -339,12 +338,11 @@ nb_status alloc_system(nb_ctx *ctx, int64_t n)
 
 void fill_default_tuning(nb_ctx *c)
 {
-    const int occ = c->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
     for (int b = 0; b < kBuckets; ++b) {
         int64_t s = int64_t(1) << b;
         if (s > c->n) s = c->n;
         int v, S;
-        default_tuning(c->cfg.precision, c->n, s, c->num_sms, occ, &v, &S);
+        default_tuning(c->cfg.precision, c->n, s, force_grid(c), 1, &v, &S);
         c->tune.variant[b] = v;
         c->tune.split[b] = S;
     }
@@ -1212,10 +1210,9 @@ nb_status nb_set_tuning(nb_ctx *ctx, int32_t bucket, int32_t variant, int32_t sp
     if (bucket < 0 || bucket >= kBuckets) return fail(ctx, NB_ERR_ARG, "bucket out of range");
     if (variant >= nb_num_variants(ctx)) return fail(ctx, NB_ERR_ARG, "variant out of range");
     if (variant < 0) {
-        const int occ = ctx->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
         int64_t s = std::min<int64_t>(int64_t(1) << bucket, ctx->n);
         int vv, SS;
-        default_tuning(ctx->cfg.precision, ctx->n, s, ctx->num_sms, occ, &vv, &SS);
+        default_tuning(ctx->cfg.precision, ctx->n, s, force_grid(ctx), 1, &vv, &SS);
         variant = vv;
         split = SS;
     }
@@ -1268,7 +1265,7 @@ nb_status nb_autotune(nb_ctx *ctx)
     nb_status st = check_ctx(ctx, true);
     if (st != NB_OK) return st;
     const int nv = nb_num_variants(ctx);
-    const int occ = ctx->cfg.precision == NB_PREC_FP64 ? force_f64_ctas_per_sm() : force_mixed_ctas_per_sm();
+    const bool mixed = ctx->cfg.precision != NB_PREC_FP64;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1281,11 +1278,13 @@ nb_status nb_autotune(nb_ctx *ctx)
         float best = 1e30f;
         int bv = ctx->tune.variant[b], bs = ctx->tune.split[b];
         for (int v = 0; v < nv; ++v) {
+            const bool share = mixed && v == kShareVariantId;
+            if (share && !mixed_share_fits(ctx->n_tiles)) continue;
             const int64_t I = ctx->cfg.precision == NB_PREC_FP64 ? f64_variant_I(v) : mixed_variant_I(v);
             if (I > 4 * s && v > 0) continue;        // i-blocks mostly empty
-            if ((s + I - 1) / I > 4096 && v < nv - 1) continue;   // far too many small work items
+            if (!share && (s + I - 1) / I > 4096 && v != kMixedFallbackId) continue;   // far too many small work items
             const int64_t nib = (s + I - 1) / I;
-            const int64_t R = (int64_t)ctx->num_sms * occ;
+            const int64_t R = force_grid(ctx);
             // wave-aligned splits (W = nib * S just below k full waves), the default's
             // choice, a few coarse ones and 1..4; more than 16 waves of items only
             // for splits up to 4
@@ -1297,6 +1296,7 @@ nb_status nb_autotune(nb_ctx *ctx)
                 if (nib * S > 16 * R && S > 4) continue;
                 if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
             }
+            if (share) cands.assign(1, 1);   // the resident-share variant has no split factor
             for (int64_t S : cands) {
                 if (S * s * kPartStride > ctx->part_cap) continue;
                 ForceArgs F = force_args(ctx, v, (int)S);

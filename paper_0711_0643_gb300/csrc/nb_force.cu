@@ -25,8 +25,12 @@
 // pairs are folded into (hi, lo) two-sum accumulators, and the cross-thread
 // reductions combine (hi, lo) pairs with two-sums too (FP64 is a narrow pipe on
 // this part; only the final per-split partial is converted to double).
+#include <cooperative_groups.h>
+
 #include "nb_internal.cuh"
 #include "nb_pair.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nb {
 
@@ -98,10 +102,21 @@ constexpr int kMaxRC = 2 * 7;   // R * components, largest R over variants
 constexpr int kPT = kJT / 2;    // pair records per tile
 constexpr int kRing = 6;        // tiles in flight in the TMA streaming variant
 
+// Resident-share variant: clusters of kShareC CTAs, CTA r holding up to
+// kShareRec pair records of the j range in shared memory, the active list dealt
+// out to the clusters in chunks of up to kShareSlots particles.
+constexpr int kShareC = 8;
+constexpr int kShareRec = 1024;
+constexpr int kShareSlots = 256;
+
 struct __align__(128) Smem {
     union {
         JPair tile[kStages][kPT];   // tile variants
         JPair ring[kRing][kPT];     // TMA streaming variant
+        struct {
+            JPair rec[kShareRec];            // this CTA's share of the j-records
+            float2 slot[kShareSlots][7];     // (hi, lo) partials of the chunk's particles
+        } share;                            // resident-share variant
     };
     float2 red[kThreads / 32][kMaxRC];
     uint64_t bar[kRing];
@@ -595,7 +610,9 @@ __device__ void work_tile(const ForceArgs &A, int64_t s, int64_t bx, int by, int
 
 // 0: stream R=1 (I=1)      1: stream R=2 (I=2)      2: tile R=1 TJ=32 (I=8)
 // 3: tile R=1 TJ=8 (I=32)  4: tile R=1 TJ=1 (I=256) 5: TMA stream R=1 (I=1)
-constexpr int kMixedFallback = 4;   // the variant of an out-of-range table entry
+// 6: resident share (cluster launch; the split factor is unused)
+constexpr int kMixedFallback = kMixedFallbackId;   // the variant of an out-of-range table entry
+constexpr int kShareVariant = kShareVariantId;
 __host__ __device__ __forceinline__ int mixed_I(int v)
 {
     switch (v) {
@@ -604,8 +621,226 @@ __host__ __device__ __forceinline__ int mixed_I(int v)
     case 2: return 8;
     case 3: return 32;
     case 5: return 1;
+    case 6: return 1;
     default: return 256;
     }
+}
+
+// ------------------------------------------------- resident-share variant
+// For j ranges of up to kShareC * kShareRec pair records. The launch runs as
+// clusters of kShareC CTAs; CTA r of a cluster copies records [r * rper, (r + 1)
+// * rper) of the range into shared memory once (bulk copies on one mbarrier),
+// padded with far-away massless records to whole rounds of 32. The clusters deal
+// out the active list in chunks (chunk k to cluster k mod clusters); every CTA of
+// the cluster runs the whole chunk against its share in passes whose group
+// width TJ fits the remaining count, leaving (hi, lo) partials in its shared
+// memory. After a cluster barrier, CTA r sums positions r, r + kShareC, ... of
+// the chunk over the kShareC CTAs in rank order through distributed shared
+// memory and writes the FP64 results; a second barrier frees the slots. No
+// global partial slots, tickets or fences; the same bits on every run.
+
+// rper: records per CTA, a multiple of 32 (0 when the range does not fit)
+__device__ __forceinline__ int64_t share_rper(const ForceArgs &A)
+{
+    const int64_t nrec = (A.tile_hi - A.tile_lo) * kPT;
+    const int64_t rper = ((nrec + kShareC - 1) / kShareC + 31) / 32 * 32;
+    return rper <= kShareRec ? rper : 0;
+}
+
+// One pass: cnt particles from list position p0 into slots slot0 ..., TJ threads
+// per particle taking records tj, tj + TJ, ... of the share (nr rounds).
+template <int TJ>
+__device__ __forceinline__ void share_pass(const ForceArgs &A, Smem *sm, int64_t p0, int cnt, int slot0,
+                                           int64_t rec0, int nrec, int nr)
+{
+    constexpr int FP = kFoldPairs / 2;   // records per fold
+    const int tid = threadIdx.x, tj = tid % TJ, ti = tid / TJ;
+    const bool live = ti < cnt;
+    const int32_t gi = idx_at(A, sm, p0 + (live ? ti : cnt - 1));
+    const IPk ip = ipk_of(jrec_load(A.j.p, gi));
+    const float2 e2 = make_float2(A.eps2f, A.eps2f);
+    AccPk p;
+    Acc7 hi, lo;
+    zero(p);
+    zero(hi);
+    zero(lo);
+    const int64_t self = (int64_t)gi - 2 * rec0;   // i's place in the share, if it is there
+    const JPair *R = sm->share.rec;
+    if (__any_sync(0xffffffffu, self >= 0 && self < 2 * (int64_t)nrec)) {
+        for (int k0 = 0; k0 < nr; k0 += FP) {
+            const int k1 = k0 + FP < nr ? k0 + FP : nr;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const int pp = tj + k * TJ;
+                const float4 *Q = R[pp].q;
+                pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == self, 2 * pp + 1 == self);
+            }
+            fold(hi, lo, p);
+        }
+    } else {
+        for (int k0 = 0; k0 < nr; k0 += FP) {
+            const int k1 = k0 + FP < nr ? k0 + FP : nr;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) {
+                const float4 *Q = R[tj + k * TJ].q;
+                pair_packed<false>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, false, false);
+            }
+            fold(hi, lo, p);
+        }
+    }
+    if (TJ > 1) ds_group_reduce7<TJ>(hi, lo);
+    if (tj == 0 && live) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) sm->share.slot[slot0 + ti][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+    }
+}
+
+// A pass for cnt <= 4 particles with 256 / cnt threads each (whole warps): lanes
+// then warps of a particle summed in ascending order.
+__device__ __forceinline__ void share_pass_wide(const ForceArgs &A, Smem *sm, int64_t p0, int cnt, int slot0,
+                                                int64_t rec0, int nrec, int nrec32)
+{
+    constexpr int FP = kFoldPairs / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = cnt == 1 ? 8 : (cnt == 2 ? 4 : 2);   // warps per particle
+    const int TW = 32 * W;                            // threads per particle
+    const int ti = tid / TW, tj = tid % TW;
+    const bool live = ti < cnt;
+    const int32_t gi = idx_at(A, sm, p0 + (live ? ti : cnt - 1));
+    const IPk ip = ipk_of(jrec_load(A.j.p, gi));
+    const float2 e2 = make_float2(A.eps2f, A.eps2f);
+    AccPk p;
+    Acc7 hi, lo;
+    zero(p);
+    zero(hi);
+    zero(lo);
+    const int64_t self = (int64_t)gi - 2 * rec0;
+    const JPair *R = sm->share.rec;
+    const int nr = (nrec32 + TW - 1) / TW;
+    const bool mine = self >= 0 && self < 2 * (int64_t)nrec;
+    int f = 0;
+    for (int k = 0; k < nr; ++k) {
+        const int pp = tj + k * TW;
+        if (pp < nrec32) {
+            const float4 *Q = R[pp].q;
+            if (mine)
+                pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == self, 2 * pp + 1 == self);
+            else
+                pair_packed<false>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, false, false);
+        }
+        if (++f == FP) {
+            f = 0;
+            fold(hi, lo, p);
+        }
+    }
+    fold(hi, lo, p);
+    ds_group_reduce7<32>(hi, lo);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) sm->red[warp][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+    }
+    __syncthreads();
+    if (tid < cnt * 7) {
+        const int t = tid / 7, c = tid % 7;
+        float h = sm->red[t * W][c].x, l = sm->red[t * W][c].y;
+        for (int wv = 1; wv < W; ++wv) ds_add(h, l, sm->red[t * W + wv][c].x, sm->red[t * W + wv][c].y);
+        sm->share.slot[slot0 + t][c] = make_float2(h, l);
+    }
+    __syncthreads();
+}
+
+// The whole launch of the resident-share variant for this CTA.
+__device__ __noinline__ void share_force(const ForceArgs &A, int64_t s, Smem *sm, int64_t rper)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int q = blockIdx.x / kShareC, ncl = gridDim.x / kShareC;
+    const int tid = threadIdx.x;
+    const int64_t rtot = (A.tile_hi - A.tile_lo) * kPT;
+    const int64_t rec0 = A.tile_lo * kPT + (int64_t)rank * rper;
+    const int64_t rlim = A.tile_lo * kPT + rtot;
+    const int nrec = (int)(rec0 < rlim ? (rlim - rec0 < rper ? rlim - rec0 : rper) : 0);
+    const int nrec32 = (nrec + 31) / 32 * 32;
+    // chunks: ceil(s / clusters) particles each (at most kShareSlots)
+    int64_t csz = (s + ncl - 1) / ncl;
+    if (csz > kShareSlots) csz = kShareSlots;
+    const int64_t nchunk = (s + csz - 1) / csz;
+    if (q >= nchunk) return;   // the whole cluster has nothing to do (uniform over it)
+    // the share: bulk copies of at most 16 KB on one mbarrier, padding by the threads
+    bool ok = true;
+    if (nrec > 0) {
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)nrec * (uint32_t)sizeof(JPair);
+            mbar_arrive_expect_tx(&sm->bar[0], bytes);
+            constexpr int kPiece = 200;   // records per copy (16000 bytes)
+            for (int r0 = 0; r0 < nrec; r0 += kPiece) {
+                const int nr = nrec - r0 < kPiece ? nrec - r0 : kPiece;
+                bulk_g2s(sm->share.rec + r0, A.j.p + rec0 + r0, (uint32_t)nr * (uint32_t)sizeof(JPair), &sm->bar[0]);
+            }
+        }
+    }
+    {
+        const float far = (float)kPadPos;
+        for (int qq = 2 * nrec + tid; qq < 2 * nrec32; qq += kThreads)
+            jrec_store(sm->share.rec, qq, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+    }
+    if (nrec > 0 && !mbar_wait(&sm->bar[0], 0, A.spin_limit)) {
+        ok = false;
+        if (tid == 0) atomicOr(A.status, kStTimeout);
+    }
+    __syncthreads();
+    for (int64_t k = q; k < nchunk; k += ncl) {
+        const int64_t c0 = k * csz;
+        const int cnt = (int)(c0 + csz < s ? csz : s - c0);
+        if (ok) {
+            int done = 0;
+            while (done < cnt) {
+                const int r = cnt - done;
+                if (r >= 256) {
+                    share_pass<1>(A, sm, c0 + done, 256, done, rec0, nrec, nrec32);
+                    done += 256;
+                } else if (r >= 128) {
+                    share_pass<2>(A, sm, c0 + done, 128, done, rec0, nrec, nrec32 / 2);
+                    done += 128;
+                } else if (r >= 64) {
+                    share_pass<4>(A, sm, c0 + done, 64, done, rec0, nrec, nrec32 / 4);
+                    done += 64;
+                } else if (r >= 32) {
+                    share_pass<8>(A, sm, c0 + done, 32, done, rec0, nrec, nrec32 / 8);
+                    done += 32;
+                } else if (r > 8) {
+                    const int n16 = r < 16 ? r : 16;
+                    share_pass<16>(A, sm, c0 + done, n16, done, rec0, nrec, nrec32 / 16);
+                    done += n16;
+                } else if (r > 4) {
+                    share_pass<32>(A, sm, c0 + done, r, done, rec0, nrec, nrec32 / 32);
+                    done += r;
+                } else {
+                    share_pass_wide(A, sm, c0 + done, r, done, rec0, nrec, nrec32);
+                    done += r;
+                }
+            }
+        } else {
+            for (int qq = tid; qq < cnt * 7; qq += kThreads)
+                sm->share.slot[qq / 7][qq % 7] = make_float2(0.f, 0.f);
+        }
+        cl.sync();
+        // rank r sums positions r, r + kShareC, ...: one (position, component) per thread
+        for (int t = tid; t < ((cnt + kShareC - 1) / kShareC) * 7; t += kThreads) {
+            const int pl = rank + kShareC * (t / 7), c = t % 7;
+            if (pl < cnt) {
+                float2 v[kShareC];
+#pragma unroll
+                for (int u = 0; u < kShareC; ++u) v[u] = *cl.map_shared_rank(&sm->share.slot[pl][c], u);
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int u = 0; u < kShareC; ++u) ds_add(h, l, v[u].x, v[u].y);
+                put_final(A, c0 + pl, c, (double)h + (double)l);
+            }
+        }
+        cl.sync();
+    }
+    if (!ok && nrec > 0 && tid == 0) (void)mbar_wait(&sm->bar[0], 0, A.spin_limit);   // drain before exit
 }
 
 __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
@@ -655,6 +890,19 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
         S = table_split(sm->tune.split[b], b, s, A.n, mixed_I(variant));
     }
     if (variant < 0 || variant >= kMixedVariants) variant = kMixedFallback;
+    if (variant == kShareVariant) {
+        // needs the cluster launch and a j range that fits the shares (the same
+        // answer in every CTA of a cluster)
+        const int64_t rper = share_rper(A);
+        if (cg::this_cluster().num_blocks() == kShareC && rper > 0) {
+            if (blockIdx.x == 0 && tid == 0) *A.split_used = kShareC;
+            share_force(A, s, sm, rper);
+            return;
+        }
+        variant = kMixedFallback;
+        const int64_t nib4 = qdiv(s + mixed_I(variant) - 1, mixed_I(variant));
+        S = (int)(gridDim.x / nib4 > 1 ? gridDim.x / nib4 : 1);
+    }
     S = clamp_split(S, A.tile_hi - A.tile_lo, s, A.part_cap);
     if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
     const int64_t I = mixed_I(variant);
@@ -861,6 +1109,7 @@ const char *mixed_variant_name(int v)
     case 3: return "tile R=1 TJ=8";
     case 4: return "tile R=1 TJ=1";
     case 5: return "TMA stream R=1";
+    case 6: return "resident share (8-CTA clusters)";
     default: return "?";
     }
 }
@@ -871,7 +1120,7 @@ const char *f64_variant_name(int v) { return v == 0 ? "f64 stream" : "f64 i-loop
 
 size_t force_mixed_smem_bytes() { return sizeof(Smem); }
 
-static int g_mixed_occ = -1, g_f64_occ = -1;
+static int g_mixed_occ = -1, g_f64_occ = -1, g_mixed_grid = -1;
 
 int force_mixed_ctas_per_sm()
 {
@@ -886,6 +1135,49 @@ int force_mixed_ctas_per_sm()
         g_mixed_occ = occ;
     }
     return g_mixed_occ;
+}
+
+// For particle counts whose j-records fit the resident shares of one cluster,
+// the mixed kernel runs as clusters of kShareC CTAs (the resident-share variant
+// needs them; the others ignore them). Its persistent grid is then the number of
+// clusters the device keeps resident at once times kShareC, so that no CTA of
+// the grid waits for another to finish (a CTA of a late cluster would hold its
+// work items until then); 0 when cluster launches are not available. Larger
+// particle counts (and that case) launch SMs x resident CTAs without clusters.
+static int mixed_cluster_grid()
+{
+    if (g_mixed_grid < 0) {
+        (void)force_mixed_ctas_per_sm();
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kShareC;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(kShareC * 64);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, force_mixed_kernel, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            ncl = 0;
+        }
+        g_mixed_grid = ncl * kShareC;
+    }
+    return g_mixed_grid;
+}
+
+bool mixed_share_fits(int64_t n_tiles)
+{
+    const int64_t rper = ((n_tiles * kPT + kShareC - 1) / kShareC + 31) / 32 * 32;
+    return rper <= kShareRec && mixed_cluster_grid() > 0;
+}
+
+int force_mixed_grid(int num_sms, int64_t n_tiles)
+{
+    return mixed_share_fits(n_tiles) ? mixed_cluster_grid() : num_sms * force_mixed_ctas_per_sm();
 }
 
 int force_f64_ctas_per_sm()
@@ -903,6 +1195,21 @@ int force_f64_ctas_per_sm()
 cudaError_t launch_force_mixed(const ForceArgs &a, int grid, cudaStream_t st)
 {
     (void)force_mixed_ctas_per_sm();   // sets the dynamic shared-memory attribute once
+    if (mixed_share_fits(a.n_tiles) && grid % kShareC == 0) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kShareC;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, force_mixed_kernel, a);
+    }
     force_mixed_kernel<<<grid, kThreads, sizeof(Smem), st>>>(a);
     return cudaGetLastError();
 }
@@ -945,6 +1252,9 @@ void default_tuning(int precision, int64_t n, int64_t s, int num_sms, int ctas_p
     int v;
     if (precision == NB_PREC_FP64) {
         v = s <= 64 ? 0 : 1;
+    } else if (mixed_share_fits(n_tiles) && s > 16 && s <= 8192) {
+        // the j-records fit the resident shares of a cluster: no split partials in L2
+        v = kShareVariant;
     } else if (n <= 65536) {
         // j-records stay in L2 and are cheap to re-read: stream variants (every
         // thread of a CTA on the same 1 or 2 i-particles) win while blocks are small

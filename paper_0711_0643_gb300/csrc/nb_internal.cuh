@@ -89,7 +89,9 @@ struct ForceArgs {
 };
 
 // Variant catalogue. Mixed: 0..kMixedVariants-1; FP64: 0..kF64Variants-1.
-constexpr int kMixedVariants = 6;
+constexpr int kMixedVariants = 7;
+constexpr int kMixedFallbackId = 4;   // tiled, one particle per thread: takes any size
+constexpr int kShareVariantId = 6;    // resident j-share in 8-CTA clusters
 constexpr int kF64Variants = 2;
 int mixed_variant_I(int v);           // i-particles per work item
 const char *mixed_variant_name(int v);
@@ -100,6 +102,12 @@ const char *f64_variant_name(int v);
 cudaError_t launch_force_mixed(const ForceArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_force_f64(const ForceArgs &a, int grid, cudaStream_t st);
 int force_mixed_ctas_per_sm();
+// Persistent grid of the mixed force kernel for n_tiles tiles of j-records (the
+// resident cluster grid where the resident-share variant can run): pass it to
+// launch_force_mixed, which launches clusters in that case.
+int force_mixed_grid(int num_sms, int64_t n_tiles);
+// Whether the resident-share variant (6) can take a j range of n_tiles tiles.
+bool mixed_share_fits(int64_t n_tiles);
 int force_f64_ctas_per_sm();
 size_t force_mixed_smem_bytes();
 

@@ -97,10 +97,10 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     }
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NB_ERR_CUDA;
-    const int occ = force_mixed_ctas_per_sm();
     const int64_t n_tiles = (n + kJT - 1) / kJT;
+    const int grid = force_mixed_grid(num_sms, n_tiles);
     int variant = 0, split = 1;
-    default_tuning(NB_PREC_MIXED, n, s, num_sms, occ, &variant, &split);
+    default_tuning(NB_PREC_MIXED, n, s, grid, 1, &variant, &split);
     // the split partials must fit: s * split * 8 words
     const int64_t max_split = kStaticPartWords / (s * kPartStride);
     if (max_split < 1) return NB_ERR_ARG;
@@ -137,7 +137,7 @@ extern "C" nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const 
     F.status = reinterpret_cast<int32_t *>(base + kOffStatus);
     F.spin_limit = int64_t(1) << 24;
     F.inject = 0;
-    if (launch_force_mixed(F, num_sms * occ, st) != cudaSuccess) return NB_ERR_CUDA;
+    if (launch_force_mixed(F, grid, st) != cudaSuccess) return NB_ERR_CUDA;
     if (launch_reduce_out(F.fin, F.s, s, a_dev, k_dev, phi_dev, F.status, st) != cudaSuccess) return NB_ERR_CUDA;
     // the status word is read in stream order (no wait on other streams' work)
     int32_t status = 0;
