@@ -27,6 +27,8 @@
 // this part; only the final per-split partial is converted to double).
 #include <cooperative_groups.h>
 
+#include <cstddef>
+
 #include "nb_internal.cuh"
 #include "nb_pair.cuh"
 
@@ -109,15 +111,11 @@ constexpr int kShareC = 8;
 constexpr int kShareRec = 1024;
 constexpr int kShareSlots = 256;
 
+// The staging buffers come last, so that the resident-share variant's larger
+// buffer can take their place and run past the end of the struct: the kernel
+// instantiation without that variant is launched with sizeof(Smem) bytes, the
+// one with it with kSmemShare bytes.
 struct __align__(128) Smem {
-    union {
-        JPair tile[kStages][kPT];   // tile variants
-        JPair ring[kRing][kPT];     // TMA streaming variant
-        struct {
-            JPair rec[kShareRec];            // this CTA's share of the j-records
-            float2 slot[kShareSlots][7];     // (hi, lo) partials of the chunk's particles
-        } share;                            // resident-share variant
-    };
     float2 red[kThreads / 32][kMaxRC];
     uint64_t bar[kRing];
     uint64_t inject_bar;
@@ -126,7 +124,20 @@ struct __align__(128) Smem {
     int32_t idx_pre[kThreads]; // the first kThreads entries of the active list, read with s
     int abort;
     int last;
+    alignas(128) union {
+        JPair tile[kStages][kPT];   // tile variants
+        JPair ring[kRing][kPT];     // TMA streaming variant
+    };
 };
+
+struct ShareBuf {
+    JPair rec[kShareRec];            // this CTA's share of the j-records
+    float2 slot[kShareSlots][7];     // (hi, lo) partials of the chunk's particles
+};
+
+constexpr size_t kSmemShare = (offsetof(Smem, tile) + sizeof(ShareBuf) + 127) / 128 * 128;
+
+__device__ __forceinline__ ShareBuf *shb(Smem *sm) { return reinterpret_cast<ShareBuf *>(&sm->tile[0][0]); }
 
 __device__ __forceinline__ int bucket_of(int64_t s)
 {
@@ -664,34 +675,26 @@ __device__ __forceinline__ void share_pass(const ForceArgs &A, Smem *sm, int64_t
     zero(p);
     zero(hi);
     zero(lo);
-    const int64_t self = (int64_t)gi - 2 * rec0;   // i's place in the share, if it is there
-    const JPair *R = sm->share.rec;
-    if (__any_sync(0xffffffffu, self >= 0 && self < 2 * (int64_t)nrec)) {
-        for (int k0 = 0; k0 < nr; k0 += FP) {
-            const int k1 = k0 + FP < nr ? k0 + FP : nr;
-#pragma unroll 4
-            for (int k = k0; k < k1; ++k) {
-                const int pp = tj + k * TJ;
-                const float4 *Q = R[pp].q;
-                pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == self, 2 * pp + 1 == self);
-            }
-            fold(hi, lo, p);
+    // i's place in the share, if it is there (else a value no record matches);
+    // one loop with the self test in it keeps the code small: each launch runs
+    // its passes once, from a cold instruction cache
+    const int64_t self = (int64_t)gi - 2 * rec0;
+    const int selfi = self >= 0 && self < 2 * (int64_t)nrec ? (int)self : -2;
+    const JPair *R = shb(sm)->rec;
+    for (int k0 = 0; k0 < nr; k0 += FP) {
+        const int k1 = k0 + FP < nr ? k0 + FP : nr;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k) {
+            const int pp = tj + k * TJ;
+            const float4 *Q = R[pp].q;
+            pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == selfi, 2 * pp + 1 == selfi);
         }
-    } else {
-        for (int k0 = 0; k0 < nr; k0 += FP) {
-            const int k1 = k0 + FP < nr ? k0 + FP : nr;
-#pragma unroll 4
-            for (int k = k0; k < k1; ++k) {
-                const float4 *Q = R[tj + k * TJ].q;
-                pair_packed<false>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, false, false);
-            }
-            fold(hi, lo, p);
-        }
+        fold(hi, lo, p);
     }
     if (TJ > 1) ds_group_reduce7<TJ>(hi, lo);
     if (tj == 0 && live) {
 #pragma unroll
-        for (int c = 0; c < 7; ++c) sm->share.slot[slot0 + ti][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
+        for (int c = 0; c < 7; ++c) shb(sm)->slot[slot0 + ti][c] = make_float2(acc_get(hi, c), acc_get(lo, c));
     }
 }
 
@@ -715,18 +718,15 @@ __device__ __forceinline__ void share_pass_wide(const ForceArgs &A, Smem *sm, in
     zero(hi);
     zero(lo);
     const int64_t self = (int64_t)gi - 2 * rec0;
-    const JPair *R = sm->share.rec;
+    const int selfi = self >= 0 && self < 2 * (int64_t)nrec ? (int)self : -2;
+    const JPair *R = shb(sm)->rec;
     const int nr = (nrec32 + TW - 1) / TW;
-    const bool mine = self >= 0 && self < 2 * (int64_t)nrec;
     int f = 0;
     for (int k = 0; k < nr; ++k) {
         const int pp = tj + k * TW;
         if (pp < nrec32) {
             const float4 *Q = R[pp].q;
-            if (mine)
-                pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == self, 2 * pp + 1 == self);
-            else
-                pair_packed<false>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, false, false);
+            pair_packed<true>(Q[0], Q[1], Q[2], Q[3], Q[4], ip, e2, p, 2 * pp == selfi, 2 * pp + 1 == selfi);
         }
         if (++f == FP) {
             f = 0;
@@ -744,7 +744,7 @@ __device__ __forceinline__ void share_pass_wide(const ForceArgs &A, Smem *sm, in
         const int t = tid / 7, c = tid % 7;
         float h = sm->red[t * W][c].x, l = sm->red[t * W][c].y;
         for (int wv = 1; wv < W; ++wv) ds_add(h, l, sm->red[t * W + wv][c].x, sm->red[t * W + wv][c].y);
-        sm->share.slot[slot0 + t][c] = make_float2(h, l);
+        shb(sm)->slot[slot0 + t][c] = make_float2(h, l);
     }
     __syncthreads();
 }
@@ -775,14 +775,14 @@ __device__ __noinline__ void share_force(const ForceArgs &A, int64_t s, Smem *sm
             constexpr int kPiece = 200;   // records per copy (16000 bytes)
             for (int r0 = 0; r0 < nrec; r0 += kPiece) {
                 const int nr = nrec - r0 < kPiece ? nrec - r0 : kPiece;
-                bulk_g2s(sm->share.rec + r0, A.j.p + rec0 + r0, (uint32_t)nr * (uint32_t)sizeof(JPair), &sm->bar[0]);
+                bulk_g2s(shb(sm)->rec + r0, A.j.p + rec0 + r0, (uint32_t)nr * (uint32_t)sizeof(JPair), &sm->bar[0]);
             }
         }
     }
     {
         const float far = (float)kPadPos;
         for (int qq = 2 * nrec + tid; qq < 2 * nrec32; qq += kThreads)
-            jrec_store(sm->share.rec, qq, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+            jrec_store(shb(sm)->rec, qq, far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f);
     }
     if (nrec > 0 && !mbar_wait(&sm->bar[0], 0, A.spin_limit)) {
         ok = false;
@@ -822,7 +822,7 @@ __device__ __noinline__ void share_force(const ForceArgs &A, int64_t s, Smem *sm
             }
         } else {
             for (int qq = tid; qq < cnt * 7; qq += kThreads)
-                sm->share.slot[qq / 7][qq % 7] = make_float2(0.f, 0.f);
+                shb(sm)->slot[qq / 7][qq % 7] = make_float2(0.f, 0.f);
         }
         cl.sync();
         // rank r sums positions r, r + kShareC, ...: one (position, component) per thread
@@ -831,7 +831,7 @@ __device__ __noinline__ void share_force(const ForceArgs &A, int64_t s, Smem *sm
             if (pl < cnt) {
                 float2 v[kShareC];
 #pragma unroll
-                for (int u = 0; u < kShareC; ++u) v[u] = *cl.map_shared_rank(&sm->share.slot[pl][c], u);
+                for (int u = 0; u < kShareC; ++u) v[u] = *cl.map_shared_rank(&shb(sm)->slot[pl][c], u);
                 float h = 0.f, l = 0.f;
 #pragma unroll
                 for (int u = 0; u < kShareC; ++u) ds_add(h, l, v[u].x, v[u].y);
@@ -843,6 +843,10 @@ __device__ __noinline__ void share_force(const ForceArgs &A, int64_t s, Smem *sm
     if (!ok && nrec > 0 && tid == 0) (void)mbar_wait(&sm->bar[0], 0, A.spin_limit);   // drain before exit
 }
 
+// SHARE: the instantiation with the resident-share variant (launched as clusters
+// with kSmemShare bytes); without it the kernel has no cluster code and the
+// plain shared-memory size.
+template <bool SHARE>
 __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -893,15 +897,16 @@ __global__ void __launch_bounds__(kThreads, 2) force_mixed_kernel(ForceArgs A)
     if (variant == kShareVariant) {
         // needs the cluster launch and a j range that fits the shares (the same
         // answer in every CTA of a cluster)
-        const int64_t rper = share_rper(A);
-        if (cg::this_cluster().num_blocks() == kShareC && rper > 0) {
-            if (blockIdx.x == 0 && tid == 0) *A.split_used = kShareC;
-            share_force(A, s, sm, rper);
-            return;
+        if constexpr (SHARE) {
+            const int64_t rper = share_rper(A);
+            if (cg::this_cluster().num_blocks() == kShareC && rper > 0) {
+                if (blockIdx.x == 0 && tid == 0) *A.split_used = kShareC;
+                share_force(A, s, sm, rper);
+                return;
+            }
         }
-        variant = kMixedFallback;
-        const int64_t nib4 = qdiv(s + mixed_I(variant) - 1, mixed_I(variant));
-        S = (int)(gridDim.x / nib4 > 1 ? gridDim.x / nib4 : 1);
+        variant = kMixedFallback;   // (a launch without clusters: one split)
+        S = 1;
     }
     S = clamp_split(S, A.tile_hi - A.tile_lo, s, A.part_cap);
     if (blockIdx.x == 0 && tid == 0) *A.split_used = S;
@@ -1125,10 +1130,12 @@ static int g_mixed_occ = -1, g_f64_occ = -1, g_mixed_grid = -1;
 int force_mixed_ctas_per_sm()
 {
     if (g_mixed_occ < 0) {
-        cudaFuncSetAttribute(force_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(force_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(Smem));
+        cudaFuncSetAttribute(force_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemShare);
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_mixed_kernel, kThreads, sizeof(Smem)) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, force_mixed_kernel<false>, kThreads, sizeof(Smem)) !=
                 cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -1156,11 +1163,11 @@ static int mixed_cluster_grid()
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(kShareC * 64);
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.dynamicSmemBytes = kSmemShare;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int ncl = 0;
-        if (cudaOccupancyMaxActiveClusters(&ncl, force_mixed_kernel, &cfg) != cudaSuccess || ncl < 1) {
+        if (cudaOccupancyMaxActiveClusters(&ncl, force_mixed_kernel<true>, &cfg) != cudaSuccess || ncl < 1) {
             cudaGetLastError();
             ncl = 0;
         }
@@ -1204,13 +1211,13 @@ cudaError_t launch_force_mixed(const ForceArgs &a, int grid, cudaStream_t st)
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.dynamicSmemBytes = kSmemShare;
         cfg.stream = st;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, force_mixed_kernel, a);
+        return cudaLaunchKernelEx(&cfg, force_mixed_kernel<true>, a);
     }
-    force_mixed_kernel<<<grid, kThreads, sizeof(Smem), st>>>(a);
+    force_mixed_kernel<false><<<grid, kThreads, sizeof(Smem), st>>>(a);
     return cudaGetLastError();
 }
 
