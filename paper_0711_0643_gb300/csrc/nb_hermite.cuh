@@ -49,9 +49,16 @@ __host__ __device__ __forceinline__ bool norm2_in_range(double S)
 __host__ __device__ __forceinline__ bool aarseth_estimate(float rA, float rK, float rP, float rQ, float fK,
                                                           float fP, float eta_f, long long &qb)
 {
+    // separate roundings, whatever the including file's contraction setting
+#ifdef __CUDA_ARCH__
+    const float num = __fadd_rn(__fmul_rn(rA, rP), fK);
+    const float den = __fadd_rn(__fmul_rn(rK, rQ), fP);
+    const float ratio = __fdiv_rn(__fmul_rn(eta_f, num), den);
+#else
     const float num = rA * rP + fK;
     const float den = rK * rQ + fP;
     const float ratio = (eta_f * num) / den;
+#endif
     const int re = (fbits(ratio) >> 23) & 0xff;
     const float c32 = sqrtf(ratio);
     const int cb = fbits(c32);
