@@ -298,6 +298,46 @@ def ensemble(n_clusters: int, seed: int, n_lo: int = 256, n_hi: int = 8192,
     return out
 
 
+def plummer_binaries(n: int, n_bin: int, seed: int, eps: float, a_lo: float = 1e-4,
+                     a_hi: float = 1e-2) -> Snapshot:
+    """A Plummer model of n stars of which 2 n_bin are in primordial binaries (equal masses
+    1/n): a Plummer model of n - n_bin centres of mass (each binary centre twice the mass),
+    then the first n_bin centres (in the stream's order) split into two stars at a
+    separation d drawn log-uniformly in [a_lo, a_hi], isotropic orientation, on a circular
+    relative orbit (|v_rel|^2 = m_b / d) in a random plane. Member 1 of binary b keeps index
+    b, member 2 takes index n - n_bin + b. ``meta["pairs"]`` holds the [n_bin, 2] index pairs.
+    """
+    n_c = n - n_bin
+    assert 0 <= n_bin <= n_c
+    mc = np.full(n_c, 1.0 / n)
+    mc[:n_bin] *= 2.0
+    base = plummer(n_c, seed, eps=eps, masses=mc, name="plummer-binaries")
+    rng = SplitMix64(seed + 700_000)
+    d = np.exp(math.log(a_lo) + rng.uniform(n_bin) * (math.log(a_hi) - math.log(a_lo)))
+    nhat = _isotropic(rng, np.ones(n_bin))
+    # a unit vector perpendicular to nhat: nhat x w, w isotropic, normalised
+    w = _isotropic(rng, np.ones(n_bin))
+    perp = np.cross(nhat, w)
+    perp /= np.linalg.norm(perp, axis=1)[:, None]
+    m = np.full(n, 1.0 / n)
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    x[:n_c] = base.x
+    v[:n_c] = base.v
+    mb = 2.0 / n
+    vrel = np.sqrt(mb / d)
+    # equal members: each at +-d/2 from the centre, velocities +-v_rel/2
+    x[n_c:] = base.x[:n_bin] - 0.5 * d[:, None] * nhat
+    v[n_c:] = base.v[:n_bin] - 0.5 * vrel[:, None] * perp
+    x[:n_bin] = base.x[:n_bin] + 0.5 * d[:, None] * nhat
+    v[:n_bin] = base.v[:n_bin] + 0.5 * vrel[:, None] * perp
+    pairs = np.stack([np.arange(n_bin), n_c + np.arange(n_bin)], axis=1).astype(np.int32)
+    meta = dict(base.meta)
+    meta.update({"model": "plummer+binaries", "n_bin": n_bin, "pairs": pairs, "sep": d})
+    return Snapshot(m, np.ascontiguousarray(x), np.ascontiguousarray(v), float(eps) ** 2,
+                    f"plummer N={n} with {n_bin} binaries", meta)
+
+
 def random_state(n: int, seed: int, eps: float, spread: float = 1.0) -> Snapshot:
     """Small uniform-cube systems with unequal masses (for tiny parity cases)."""
     rng = SplitMix64(seed)

@@ -74,6 +74,7 @@ def _bind(lib):
     lib.orc_next_block.argtypes = [i64, p, p, p, p]
     lib.orc_next_block.restype = i64
     lib.orc_energy.argtypes = [i64, p, p, p, d, p, p, C.c_int]
+    lib.orc_perturbers.argtypes = [i64, p, p, C.c_int32, p, d, C.c_int32, i64, i64, p, p]
     lib.orc_init.argtypes = [p]
     lib.orc_init.restype = C.c_int
     lib.orc_step.argtypes = [p, p, p, p]
@@ -161,6 +162,20 @@ def next_block(t, dt):
     tn = C.c_double(0.0)
     s = lib.orc_next_block(n, _ptr(t), _ptr(dt), C.byref(tn), _ptr(idx))
     return tn.value, idx[:s].copy()
+
+
+def perturbers(m, x, pairs, gamma=1e-7, nmax=256, j_lo=0, j_hi=None):
+    """Perturber lists of the binaries pairs[b] = (i, k) over stars [j_lo, j_hi) (Sect. 3.1):
+    (lists [nbin][nmax] with -1 padding, counts [nbin]); see orc_perturbers."""
+    m = _f64(m); n = m.shape[0]
+    x = _f64(x, (n, 3))
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    nb = pairs.shape[0]
+    lists = np.full((nb, int(nmax)), -1, dtype=np.int32)
+    counts = np.zeros(nb, dtype=np.int32)
+    _load().orc_perturbers(n, _ptr(m), _ptr(x), nb, _ptr(pairs), float(gamma), int(nmax), int(j_lo),
+                           int(n if j_hi is None else j_hi), _ptr(lists), _ptr(counts))
+    return lists, counts
 
 
 def energy(m, x, v, eps2, nthreads: int = 1):

@@ -218,6 +218,54 @@ void orc_energy(int64_t n, const double *m, const double *x, const double *v, do
     free(a); free(k); free(phi); free(idx);
 }
 
+/* ------------------------------------------------------------- perturbers */
+
+/* Sect. 3.1: the perturber list of a binary holds the stars with the strongest
+ * effect on its internal motion, in the order the serial scan finds them, at most
+ * nmax of them (the paper's N_pert = 256). The paper states the threshold as a
+ * force of about 10^-7 relative to a mean force; read here as the tidal
+ * perturbation of the binary: star j at distance r_j from the binary's centre of
+ * mass accelerates the two members differently by about 2 m_j d / r_j^3 (d their
+ * separation), against the binary's internal acceleration m_b / d^2, and it is a
+ * perturber when the ratio 2 m_j d^3 / (m_b r_j^3) reaches gamma. The test is
+ * taken without roots, on the sixth powers of the distances:
+ *     (2 m_j)^2 d^6 >= (gamma m_b)^2 r_j^6. */
+static double dist2(const double *u, const double *w)
+{
+    double dx = u[0] - w[0], dy = u[1] - w[1], dz = u[2] - w[2];
+    return dx * dx + dy * dy + dz * dz;
+}
+
+void orc_perturbers(int64_t n, const double *m, const double *x, int32_t nbin, const int32_t *pairs,
+                    double gamma, int32_t nmax, int64_t j_lo, int64_t j_hi, int32_t *lists, int32_t *counts)
+{
+    if (j_lo < 0) j_lo = 0;
+    if (j_hi > n) j_hi = n;
+    for (int32_t b = 0; b < nbin; ++b) {
+        int32_t i = pairs[2 * b], k = pairs[2 * b + 1];
+        double mb = m[i] + m[k];
+        double cm[3];
+        for (int c = 0; c < 3; ++c) cm[c] = (m[i] * x[3 * i + c] + m[k] * x[3 * k + c]) / mb;
+        double d2 = dist2(x + 3 * i, x + 3 * k);
+        double d6 = d2 * d2 * d2;
+        double gm = gamma * mb;
+        double rhs_scale = gm * gm;
+        int32_t found = 0;
+        for (int32_t q = 0; q < nmax; ++q) lists[(int64_t)b * nmax + q] = -1;
+        for (int64_t j = j_lo; j < j_hi; ++j) {
+            if (j == i || j == k) continue;
+            double r2 = dist2(x + 3 * j, cm);
+            double r6 = r2 * r2 * r2;
+            double tm = 2.0 * m[j];
+            if (tm * tm * d6 >= rhs_scale * r6) {
+                if (found < nmax) lists[(int64_t)b * nmax + found] = (int32_t)j;
+                ++found;
+            }
+        }
+        counts[b] = found;
+    }
+}
+
 /* ------------------------------------------------------------- integrator */
 
 static int all_finite(const double *u, int64_t count)

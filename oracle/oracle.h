@@ -90,6 +90,17 @@ int64_t orc_next_block(int64_t n, const double *t, const double *dt, double *t_n
 void orc_energy(int64_t n, const double *m, const double *x, const double *v, double eps2,
                 double *K, double *W, int nthreads);
 
+/* Perturber lists of binaries (Sect. 3.1). Binary b = (pairs[2b], pairs[2b+1]).
+ * Star j (not a member) perturbs it when its tidal acceleration across the
+ * binary, relative to the binary's internal acceleration, reaches gamma:
+ *     2 m_j d^3 / (m_b r_j^3) >= gamma,
+ * d the members' separation, m_b their mass, r_j the distance from the binary's
+ * centre of mass. Stars j in [j_lo, j_hi) are scanned in ascending index; the
+ * first nmax perturbers go to lists[b][0..), in that order (unused entries -1);
+ * counts[b] is the number found (it may exceed nmax). */
+void orc_perturbers(int64_t n, const double *m, const double *x, int32_t nbin, const int32_t *pairs,
+                    double gamma, int32_t nmax, int64_t j_lo, int64_t j_hi, int32_t *lists, int32_t *counts);
+
 /* Integrator state. All arrays are caller-owned, length n ([n][3] for vectors). */
 typedef struct {
     int64_t n;

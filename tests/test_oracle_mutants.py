@@ -49,6 +49,13 @@ MUTANTS = [
     ("next_block: max for min", "if (ti < tmin) tmin = ti;\n    }\n    int64_t s", "if (ti > tmin) tmin = ti;\n    }\n    int64_t s"),
     # energy
     ("energy: W double-counted", "pot += 0.5 * m[i] * phi[i];", "pot += m[i] * phi[i];"),
+    # perturber lists (Sect. 3.1)
+    ("perturbers: factor 2 dropped", "double tm = 2.0 * m[j];", "double tm = m[j];"),
+    ("perturbers: d^4 for d^6", "double d6 = d2 * d2 * d2;", "double d6 = d2 * d2;"),
+    ("perturbers: distance from member 1", "double r2 = dist2(x + 3 * j, cm);", "double r2 = dist2(x + 3 * j, x + 3 * i);"),
+    ("perturbers: members not excluded", "if (j == i || j == k) continue;", "if (j == i) continue;"),
+    ("perturbers: last nmax kept", "if (found < nmax) lists[(int64_t)b * nmax + found] = (int32_t)j;", "lists[(int64_t)b * nmax + found % nmax] = (int32_t)j;"),
+    ("perturbers: m_b for gamma m_b", "double gm = gamma * mb;", "double gm = gamma;"),
 ]
 
 

@@ -367,3 +367,89 @@ def test_error_codes(orc):
     m, x, v, _ = _kepler()
     s = orc.System(m, x, v, 0.0, dt_min=2.0 ** -3)
     assert s.status == orc.ERR_DT_UNDERFLOW
+
+
+# ------------------------------------------------------------------ perturber lists
+
+def _binary_at_origin(d, m1, m2):
+    """Members on the x axis with their centre of mass at the origin."""
+    mb = m1 + m2
+    return np.array([[-m2 / mb * d, 0.0, 0.0], [m1 / mb * d, 0.0, 0.0]])
+
+
+def test_perturber_threshold_closed_form(orc):
+    """Sect. 3.1, tidal reading: star j perturbs the binary iff 2 m_j d^3 / (m_b r^3) >= gamma,
+    i.e. r <= r_c = d (2 m_j / (gamma m_b))^(1/3) from the centre of mass. Stars placed at
+    r_c (1 -+ 1e-6) on the y and z axes (and one along -x) fall on the predicted sides, for
+    several star masses and gammas."""
+    for gamma, d, mj in ((1e-7, 1e-3, 1e-3), (1e-4, 2.5e-2, 0.3), (1e-2, 0.5, 2.0)):
+        xb = _binary_at_origin(d, 0.5, 0.5)
+        rc = d * (2.0 * mj / gamma) ** (1.0 / 3.0)
+        stars = []
+        inside = []
+        for q, (f, axis) in enumerate(((1 - 1e-6, 1), (1 + 1e-6, 1), (1 - 1e-6, 2), (1 + 1e-6, 2),
+                                       (0.5, 2), (2.0, 1), (1 - 1e-6, 0))):
+            p = np.zeros(3)
+            p[axis] = rc * f * (-1.0 if axis == 0 else 1.0)
+            stars.append(p)
+            inside.append(f < 1.0)
+        x = np.vstack([xb, np.array(stars)])
+        m = np.concatenate([[0.5, 0.5], np.full(len(stars), mj)])
+        lists, counts = orc.perturbers(m, x, [[0, 1]], gamma=gamma, nmax=16)
+        want = [2 + q for q, ins in enumerate(inside) if ins]
+        assert counts[0] == len(want), (gamma, counts[0], want)
+        assert list(lists[0, :len(want)]) == want and np.all(lists[0, len(want):] == -1)
+
+
+def test_perturber_distance_from_centre_of_mass(orc):
+    """Unequal members (0.8, 0.2): distances count from the centre of mass, not from either
+    member. A star at 0.999 r_c on +x is 1.006 r_c from member 1; one at 1.001 r_c on -x is
+    0.994 r_c from member 1. Only the centre-of-mass reading lists the first and not the
+    second."""
+    gamma, d, mj = 1e-7, 1e-3, 1e-3
+    m1, m2 = 0.8, 0.2
+    xb = _binary_at_origin(d, m1, m2)
+    rc = d * (2.0 * mj / (gamma * (m1 + m2))) ** (1.0 / 3.0)
+    x = np.vstack([xb, [[0.999 * rc, 0.0, 0.0], [-1.001 * rc, 0.0, 0.0]]])
+    m = np.array([m1, m2, mj, mj])
+    lists, counts = orc.perturbers(m, x, [[0, 1]], gamma=gamma, nmax=4)
+    assert counts[0] == 1 and lists[0, 0] == 2
+
+
+def test_perturber_members_order_truncation(orc):
+    """The members never perturb their own binary; the list holds the first nmax perturbers
+    in ascending index (the serial scan's order), and the count all of them."""
+    gamma, d = 1e-3, 1e-2
+    rng = np.random.default_rng(5)
+    n = 40
+    x = rng.normal(size=(n, 3)) * 0.01   # everything well inside r_c
+    m = np.full(n, 1.0 / n)
+    x[7] = [0.0, 0.0, 0.0]
+    x[23] = [d, 0.0, 0.0]
+    lists, counts = orc.perturbers(m, x, [[23, 7]], gamma=gamma, nmax=5)
+    assert counts[0] == n - 2
+    assert list(lists[0]) == [0, 1, 2, 3, 4]
+    lists, counts = orc.perturbers(m, x, [[23, 7]], gamma=gamma, nmax=64)
+    assert list(lists[0, :n - 2]) == [j for j in range(n) if j not in (7, 23)]
+    assert np.all(lists[0, n - 2:] == -1)
+
+
+def test_perturber_ranges_merge_and_exact_scalings(orc):
+    """Lists over j-ranges, concatenated in range order and cut at nmax, are the full list
+    (the parallel code's merge, Sect. 3.1), with counts summed; scaling all positions or all
+    masses by a power of two leaves the lists unchanged (the criterion is scale free and such
+    scalings are exact)."""
+    snap = ics.plummer_binaries(600, 40, 31, 1e-3, a_lo=1e-3, a_hi=5e-2)
+    pairs = snap.meta["pairs"]
+    full, cfull = orc.perturbers(snap.m, snap.x, pairs, gamma=1e-7, nmax=32)
+    assert np.any(cfull > 32) and np.any((cfull > 0) & (cfull < 32))
+    parts = [orc.perturbers(snap.m, snap.x, pairs, gamma=1e-7, nmax=32, j_lo=lo, j_hi=hi)
+             for lo, hi in ((0, 137), (137, 400), (400, 600))]
+    for b in range(pairs.shape[0]):
+        cat = np.concatenate([p[0][b][p[0][b] >= 0] for p in parts])[:32]
+        assert list(cat) == list(full[b][full[b] >= 0])
+        assert sum(int(p[1][b]) for p in parts) == cfull[b]
+    l2, c2 = orc.perturbers(snap.m, snap.x * 4.0, pairs, gamma=1e-7, nmax=32)
+    l3, c3 = orc.perturbers(snap.m * 0.5, snap.x, pairs, gamma=1e-7, nmax=32)
+    assert np.array_equal(l2, full) and np.array_equal(c2, cfull)
+    assert np.array_equal(l3, full) and np.array_equal(c3, cfull)
