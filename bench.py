@@ -406,6 +406,7 @@ def main_gpu(args):
     ens = ensemble_bench(nb, torch, dev, sptr, stream) if (args.ensemble and rank == 0) else None
     salp = salpeter_bench(nb, torch, dev, sptr, stream) if (args.salpeter and rank == 0) else None
     king = king_bench(nb, torch, dev, sptr, stream) if (args.king and rank == 0) else None
+    pert, pert_out = perturbers_bench(nb, torch, dev, sptr, stream) if (args.perturbers and rank == 0) else (None, None)
 
     # ---- full-N force sweep (King W0 = 6, N = 2^20), mixed and FP64, one evaluation per s
     sweep = None
@@ -435,6 +436,11 @@ def main_gpu(args):
                                           f"t={args.ref_t_end} of the same N=16384 Plummer run "
                                           f"({r['seconds']:.1f} s); host {cpu_model()}"}
         ferr = force_error_report(nb, oracle, nth, sptr, local)
+        if pert_out is not None:
+            # the perturber lists against the oracle's on the same positions, bit for bit
+            pm, px, pp, pg, pn, pl, pc = pert_out
+            ol, oc = oracle.perturbers(pm, px, pp, gamma=pg, nmax=pn)
+            pert["oracle_equal"] = bool(np.array_equal(pl, ol) and np.array_equal(pc, oc))
 
     c.close()
     if rank == 0:
@@ -460,7 +466,7 @@ def main_gpu(args):
             "engine": engine,
             "king": king,
             "force_sweep": sweep,
-            "ensemble": ens, "salpeter": salp, "fp64_gpu": fp64, "timing_model": model,
+            "ensemble": ens, "salpeter": salp, "perturbers": pert, "fp64_gpu": fp64, "timing_model": model,
             "force_error": ferr,
         }
         print(json.dumps(line))
@@ -605,6 +611,46 @@ def ensemble_bench(nb, torch, dev, sptr, stream, nc=256, n_lo=256, n_hi=8192, tu
             "worst_dE": _r(float(dE.max()), 5), "median_dE": _r(float(np.median(dE)), 3),
             "worst_member": [int(np.argmax(dE)), int(np.diff(off)[int(np.argmax(dE))])],
             "shape": {"cluster": shape[0], "clusters": shape[1], "split_cap": shape[2], "tuned": bool(tune)}}
+
+
+def perturbers_bench(nb, torch, dev, sptr, stream, n=16384, nbin=1638, gamma=1e-7, nmax=256):
+    """Perturber lists of binaries (Sect. 3.1): Plummer N = 16384 of which 2 x 1638 stars in
+    primordial binaries (separations log-uniform in [1e-4, 1e-2]), gamma = 1e-7, N_pert = 256;
+    one nb_perturbers_dev call (device arrays, all binaries against all stars) timed with
+    events, median of 10 after 3 warm-up calls (the 0.4 MB of positions stay in L2). Returns
+    the summary and the lists and counts (compared with the oracle's in the CPU leg)."""
+    import ics
+    snap = ics.plummer_binaries(n, nbin, ics.BASE_SEED + 49, 1.0 / 1024)
+    pairs = snap.meta["pairs"]
+    c = nb.Context(precision=nb.NB_PREC_MIXED, device=0, stream=sptr)
+    c.init(snap)
+    p_d = torch.tensor(pairs, device=dev)
+    l_d = torch.empty((nbin, nmax), dtype=torch.int32, device=dev)
+    c_d = torch.empty(nbin, dtype=torch.int32, device=dev)
+
+    def call():
+        nb.nb_perturbers_dev(c.ctx, nbin, p_d.data_ptr(), gamma, nmax, 0, -1, l_d.data_ptr(), c_d.data_ptr())
+
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(10):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    lists, counts = l_d.cpu().numpy(), c_d.cpu().numpy()
+    c.close()
+    tests = float(nbin) * (n - 2)
+    summary = {"workload": f"plummer N={n} with {nbin} primordial binaries, gamma={gamma}, N_pert={nmax}",
+               "ms": _r(ms, 4), "tests_per_s": _r(tests / (ms / 1e3)),
+               "mean_count": _r(float(counts.mean()), 4), "lists_full": int((counts > nmax).sum()),
+               "oracle_equal": None}
+    return summary, (snap.m, snap.x, pairs, gamma, nmax, lists, counts)
 
 
 def salpeter_bench(nb, torch, dev, sptr, stream, t_end=0.5):
@@ -774,6 +820,10 @@ def main(argv=None):
     ap.add_argument("--model", action=argparse.BooleanOptionalAction, default=True,
                     help="refit the per-block-step timing model on this GPU (default on)")
     ap.add_argument("--model-only", action="store_true", help="run only the timing model and print it")
+    ap.add_argument("--perturbers", action=argparse.BooleanOptionalAction, default=True,
+                    help="time the perturber lists of a Plummer model with primordial binaries")
+    ap.add_argument("--perturbers-only", action="store_true",
+                    help="run only the perturber-list timing and print it")
     ap.add_argument("--salpeter-only", action="store_true",
                     help="run only the Salpeter workload and print it")
     ap.add_argument("--ensemble-only", action="store_true",
@@ -800,9 +850,26 @@ def main(argv=None):
         return main_ensemble(args)
     if args.salpeter_only:
         return main_salpeter(args)
+    if args.perturbers_only:
+        return main_perturbers(args)
     if args.model_only:
         return main_model(args)
     return main_gpu(args)
+
+
+def main_perturbers(args):
+    """Only the perturber-list timing, printed as one JSON line (not a bench line)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    import paper_0711_0643_gb300 as pkg
+    pkg.build()
+    from paper_0711_0643_gb300 import nbody as nb
+    nb.load()
+    print(json.dumps(perturbers_bench(nb, torch, dev, stream.cuda_stream, stream)[0]))
+    return 0
 
 
 def main_ensemble(args):

@@ -305,6 +305,32 @@ nb_status nb_force_jerk_static(int64_t n, const double *m_dev, const double *x_d
                                double eps2, const int32_t *idx_dev, int64_t s, double *a_dev, double *k_dev,
                                double *phi_dev, void *stream);
 
+/* Perturber lists of binaries (Sect. 3.1). Binary b is the particle pair
+ * (pairs[2b], pairs[2b+1]). Star j (not a member) perturbs it when its tidal
+ * acceleration across the binary, relative to the binary's internal
+ * acceleration, reaches gamma:
+ *     2 m_j d^3 / (m_b r_j^3) >= gamma
+ * (d the members' separation, m_b their mass, r_j the distance from the
+ * binary's centre of mass; the paper's 10^-7 is gamma = 1e-7), evaluated on the
+ * context's current positions as (2 m_j)^2 d^6 >= (gamma m_b)^2 r_j^6 in FP64
+ * with every operation rounded separately, in a fixed order (the CPU oracle's
+ * order: the same decisions bit for bit). Stars j in [j_lo, j_hi) (j_hi < 0:
+ * n) are scanned in ascending index and the first nmax perturbers go to
+ * lists[b][0..) in that order — the serial code's order, which the paper's
+ * parallel code restores by sorting — the rest of the row -1; counts[b] is the
+ * number found (it may exceed nmax). Lists of consecutive j-ranges (one per
+ * rank of the j-parallel step), concatenated in range order and cut at nmax,
+ * are the list of the whole range and their counts add up. nmax in [1,
+ * NB_PERT_MAX] (the paper's N_pert = 256). Host arrays: pairs[nbin][2],
+ * lists[nbin][nmax], counts[nbin]; synchronous; NB_ERR_ARG for an invalid pair.
+ * The _dev form takes device arrays, is asynchronous on the context's stream
+ * and marks an invalid pair with counts[b] = -1 and an empty row. */
+#define NB_PERT_MAX 4096
+nb_status nb_perturbers(nb_ctx *ctx, int32_t nbin, const int32_t *pairs, double gamma, int32_t nmax,
+                        int64_t j_lo, int64_t j_hi, int32_t *lists, int32_t *counts);
+nb_status nb_perturbers_dev(nb_ctx *ctx, int32_t nbin, const int32_t *pairs_dev, double gamma, int32_t nmax,
+                            int64_t j_lo, int64_t j_hi, int32_t *lists_dev, int32_t *counts_dev);
+
 /* Batched ensemble of nc independent systems (Sect. 2.1 applied to each):
  * offsets[nc+1] delimit each system's particles in the concatenated arrays
  * m[N], x[N][3], v[N][3] (host, N = offsets[nc]); eps2[nc] per system, each

@@ -28,6 +28,7 @@ SOURCES = [
     ("nb_ensemble.cu", ["-fmad=false", "-ftz=true"]),
     ("nb_static.cu", ["-ftz=true"]),
     ("nb_engine.cu", ["-fmad=false", "-ftz=true"]),
+    ("nb_perturb.cu", ["-fmad=false"]),
 ]
 
 

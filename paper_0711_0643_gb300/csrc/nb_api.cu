@@ -926,6 +926,84 @@ nb_status nb_correct_forces_dev(nb_ctx *ctx, double t_block, const double *a_dev
     return correct_with(ctx, t_block);
 }
 
+// Perturber lists (nb_perturb.cu): argument checks shared by both entry points.
+static nb_status perturbers_args(nb_ctx *ctx, int32_t nbin, const void *pairs, int32_t nmax, int64_t *j_lo,
+                                 int64_t *j_hi, const void *lists, const void *counts)
+{
+    nb_status st = check_ctx(ctx, true);
+    if (st != NB_OK) return st;
+    if (nbin < 0) return fail(ctx, NB_ERR_ARG, "nbin must be >= 0");
+    if (nbin > 0 && (!pairs || !lists || !counts)) return fail(ctx, NB_ERR_ARG, "null pairs, lists or counts");
+    if (nmax < 1 || nmax > NB_PERT_MAX) return fail(ctx, NB_ERR_ARG, "nmax must be in [1, NB_PERT_MAX]");
+    if (*j_lo < 0) *j_lo = 0;
+    if (*j_hi < 0 || *j_hi > ctx->n) *j_hi = ctx->n;
+    if (*j_hi < *j_lo) *j_hi = *j_lo;
+    return NB_OK;
+}
+
+static PertArgs pert_args(nb_ctx *ctx, int32_t nbin, const int32_t *pairs, double gamma, int32_t nmax,
+                          int64_t j_lo, int64_t j_hi, int32_t *lists, int32_t *counts)
+{
+    PertArgs P{};
+    P.n = ctx->n;
+    P.np = ctx->n_pad;
+    P.m = ctx->m;
+    P.x = ctx->x;
+    P.nbin = nbin;
+    P.pairs = pairs;
+    P.gamma = gamma;
+    P.nmax = nmax;
+    P.j_lo = j_lo;
+    P.j_hi = j_hi;
+    P.lists = lists;
+    P.counts = counts;
+    return P;
+}
+
+nb_status nb_perturbers_dev(nb_ctx *ctx, int32_t nbin, const int32_t *pairs_dev, double gamma, int32_t nmax,
+                            int64_t j_lo, int64_t j_hi, int32_t *lists_dev, int32_t *counts_dev)
+{
+    nb_status st = perturbers_args(ctx, nbin, pairs_dev, nmax, &j_lo, &j_hi, lists_dev, counts_dev);
+    if (st != NB_OK) return st;
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(ctx, NB_ERR_ARG, "gamma must be finite and > 0");
+    if (nbin == 0) return NB_OK;
+    CK(launch_perturbers(pert_args(ctx, nbin, pairs_dev, gamma, nmax, j_lo, j_hi, lists_dev, counts_dev),
+                         ctx->stream));
+    return NB_OK;
+}
+
+nb_status nb_perturbers(nb_ctx *ctx, int32_t nbin, const int32_t *pairs, double gamma, int32_t nmax,
+                        int64_t j_lo, int64_t j_hi, int32_t *lists, int32_t *counts)
+{
+    nb_status st = perturbers_args(ctx, nbin, pairs, nmax, &j_lo, &j_hi, lists, counts);
+    if (st != NB_OK) return st;
+    if (!(gamma > 0.0) || !std::isfinite(gamma)) return fail(ctx, NB_ERR_ARG, "gamma must be finite and > 0");
+    if (nbin == 0) return NB_OK;
+    for (int32_t b = 0; b < nbin; ++b) {
+        const int32_t i = pairs[2 * b], k = pairs[2 * b + 1];
+        if (i < 0 || k < 0 || i >= ctx->n || k >= ctx->n || i == k)
+            return fail(ctx, NB_ERR_ARG, "pair %d: members must be two distinct particles", (int)b);
+    }
+    int32_t *dp = nullptr, *dl = nullptr, *dc = nullptr;
+    cudaError_t e = cudaMalloc(&dp, sizeof(int32_t) * 2 * (size_t)nbin);
+    if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(int32_t) * (size_t)nbin * nmax);
+    if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(int32_t) * (size_t)nbin);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dp, pairs, sizeof(int32_t) * 2 * (size_t)nbin, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_perturbers(pert_args(ctx, nbin, dp, gamma, nmax, j_lo, j_hi, dl, dc), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lists, dl, sizeof(int32_t) * (size_t)nbin * nmax, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, dc, sizeof(int32_t) * (size_t)nbin, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dp);
+    cudaFree(dl);
+    cudaFree(dc);
+    if (e != cudaSuccess) return fail(ctx, NB_ERR_CUDA, "perturbers: %s", cudaGetErrorString(e));
+    return NB_OK;
+}
+
 nb_status nb_correct(nb_ctx *ctx, double t_block)
 {
     nb_status st = check_ctx(ctx, true);

@@ -88,6 +88,20 @@ struct ForceArgs {
     int32_t inject;       // test hook (see nb_config.inject)
 };
 
+// Perturber lists of binaries (nb_perturb.cu; Sect. 3.1).
+struct PertArgs {
+    int64_t n, np;          // particles, stride of the [3][np] position array
+    const double *m, *x;    // masses, positions [3][np]
+    int32_t nbin;
+    const int32_t *pairs;   // [nbin][2] member indices
+    double gamma;
+    int32_t nmax;
+    int64_t j_lo, j_hi;     // stars scanned: [j_lo, j_hi)
+    int32_t *lists;         // [nbin][nmax], -1 past the count
+    int32_t *counts;        // [nbin] perturbers found (may exceed nmax); -1 for an invalid pair
+};
+cudaError_t launch_perturbers(const PertArgs &p, cudaStream_t st);
+
 // Variant catalogue. Mixed: 0..kMixedVariants-1; FP64: 0..kF64Variants-1.
 constexpr int kMixedVariants = 7;
 constexpr int kMixedFallbackId = 4;   // tiled, one particle per thread: takes any size

@@ -57,6 +57,10 @@ class GpuOps:
         self.nb.nb_sync(self.ctx)
         return torch.cat([a, k, phi], dim=1)
 
+    def perturbers(self, pairs, gamma, nmax, j0, j1):
+        """This rank's perturber lists over its share [j0, j1) (Sect. 3.1): (lists, counts)."""
+        return self.nb.nb_perturbers(self.ctx, pairs, gamma=gamma, nmax=nmax, j_lo=j0, j_hi=j1)
+
     def correct(self, t, total):
         if self.device is None:
             self.nb.nb_correct_forces(self.ctx, t, np.ascontiguousarray(total[:, 0:3]),
@@ -103,6 +107,26 @@ class JParallel:
         for p in parts[1:]:
             total += p
         return total
+
+    def perturbers(self, pairs, gamma=1e-7, nmax=256):
+        """Perturber lists of the binaries ``pairs`` (Sect. 3.1), found in parallel and put back
+        in the serial order: each rank scans its own share of the stars (ascending), the
+        ranks' lists are gathered and concatenated in rank order (the shares ascend, so
+        this is the order of a serial scan) and cut at nmax, and the counts are added. The
+        paper broadcasts the lists and sorts them; here the shares' order makes the merge
+        a concatenation. Returns (lists [nbin][nmax] with -1 padding, counts), the same on
+        every rank."""
+        lists, counts = self.ops.perturbers(pairs, gamma, nmax, self.j0, self.j1)
+        if self.world == 1:
+            return lists, counts
+        all_l = self._gather(np.ascontiguousarray(lists, dtype=np.int32))
+        all_c = self._gather(np.ascontiguousarray(counts, dtype=np.int32))
+        nbin = lists.shape[0]
+        out = np.full((nbin, nmax), -1, dtype=np.int32)
+        for b in range(nbin):
+            cat = np.concatenate([lr[b][lr[b] >= 0] for lr in all_l])[:nmax]
+            out[b, :cat.size] = cat
+        return out, np.sum(np.stack(all_c), axis=0).astype(np.int32)
 
     def _agree(self, tn, s):
         """Every rank must be at the same block (the replicas are identical)."""

@@ -100,6 +100,8 @@ _SIGS = [
     ("nb_ensemble_energy", C.c_int, [_P, _P]),
     ("nb_ensemble_stats", C.c_int, [_P, _P, _P, _P]),
     ("nb_ensemble_get_state", C.c_int, [_P, _P]),
+    ("nb_perturbers", C.c_int, [_P, _I32, _P, _D, _I32, _I64, _I64, _P, _P]),
+    ("nb_perturbers_dev", C.c_int, [_P, _I32, _P, _D, _I32, _I64, _I64, _P, _P]),
     ("nb_ensemble_set_shape", C.c_int, [_P, _I32, _I32]),
     ("nb_ensemble_get_shape", C.c_int, [_P, _P, _P, _P]),
     ("nb_ensemble_autotune", C.c_int, [_P, _D, _P]),
@@ -394,6 +396,27 @@ def nb_ensemble_get_state(ctx, N):
     view = nb_state_view(N, *[_ptr(arr[key]) for key in ("m", "x", "v", "a", "k", "t", "dt")])
     _check(ctx, load().nb_ensemble_get_state(ctx, C.byref(view)))
     return arr
+
+
+NB_PERT_MAX = 4096
+
+
+def nb_perturbers(ctx, pairs, gamma=1e-7, nmax=256, j_lo=0, j_hi=-1):
+    """Perturber lists of the binaries pairs[b] = (i, k) from the context's positions
+    (Sect. 3.1): (lists [nbin][nmax] with -1 padding, counts [nbin])."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    nb = pairs.shape[0]
+    lists = np.full((nb, int(nmax)), -1, dtype=np.int32)
+    counts = np.zeros(nb, dtype=np.int32)
+    _check(ctx, load().nb_perturbers(ctx, nb, _ptr(pairs), float(gamma), int(nmax), int(j_lo), int(j_hi),
+                                     _ptr(lists), _ptr(counts)))
+    return lists, counts
+
+
+def nb_perturbers_dev(ctx, nbin, pairs_dev, gamma, nmax, j_lo, j_hi, lists_dev, counts_dev):
+    return _check(ctx, load().nb_perturbers_dev(ctx, int(nbin), C.c_void_p(pairs_dev), float(gamma), int(nmax),
+                                                int(j_lo), int(j_hi), C.c_void_p(lists_dev),
+                                                C.c_void_p(counts_dev)))
 
 
 def nb_ensemble_set_shape(ctx, cluster=0, split_cap=0):

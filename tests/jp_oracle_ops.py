@@ -44,6 +44,9 @@ class OracleOps:
         a, k, phi = self.orc.force(mm, self.xp, self.vp, self.eps2, self.idx, nthreads=self.nthreads)
         return np.concatenate([a, k, phi[:, None]], axis=1)
 
+    def perturbers(self, pairs, gamma, nmax, j0, j1):
+        return self.orc.perturbers(self.st["m"], self.st["x"], pairs, gamma=gamma, nmax=nmax, j_lo=j0, j_hi=j1)
+
     def correct(self, t, total):
         st = self.st
         self.last_forces = np.array(total, copy=True)

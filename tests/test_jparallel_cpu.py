@@ -11,7 +11,8 @@ ranks). Workload: Plummer N = 1024 (the C1 initial conditions), 16 block steps.
   * A second two-rank run is bitwise identical to the first (sums in rank order).
   * The shares of j are whole tiles and cover [0, n) without overlap, for several p.
 A rank whose replica diverges is reported by the driver's per-step agreement check: a
-rank made to start from a perturbed state raises on both ranks.
+rank made to start from a perturbed state raises on both ranks. Perturber lists of binaries
+(Sect. 3.1) found per share and merged in rank order equal the serial scan's.
 """
 import json
 import os
@@ -37,6 +38,13 @@ from tests.jp_oracle_ops import OracleOps
 from paper_0711_0643_gb300.jparallel import JParallel
 dist.init_process_group("gloo")
 rank = dist.get_rank()
+if os.environ.get("NB_PERTLIST"):
+    snap = ics.plummer_binaries(1024, 100, 20071106 + 48, 1.0 / 256, a_lo=1e-3, a_hi=3e-2)
+    jp = JParallel(OracleOps(oracle, snap))
+    lists, counts = jp.perturbers(snap.meta["pairs"], gamma=1e-7, nmax=32)
+    print(json.dumps({"lists": lists.tolist(), "counts": counts.tolist(), "j": [jp.j0, jp.j1]}))
+    dist.destroy_process_group()
+    sys.exit(0)
 ops = OracleOps(oracle, ics.config(1))
 if os.environ.get("NB_PERTURB") and rank == 1:
     ops.st["dt"] *= 0.5             # this replica's schedule differs from rank 0's
@@ -62,7 +70,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _two_ranks(perturb=False):
+def _two_ranks(perturb=False, pertlist=False):
     port = _free_port()
     procs = []
     for rank in range(2):
@@ -70,6 +78,8 @@ def _two_ranks(perturb=False):
                    MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
         if perturb:
             env["NB_PERTURB"] = "1"
+        if pertlist:
+            env["NB_PERTLIST"] = "1"
         procs.append(subprocess.Popen([sys.executable, "-c", CHILD], env=env, stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE, text=True))
     outs = []
@@ -109,6 +119,21 @@ def test_two_ranks_match_one_rank_and_rerun(orc):
         f2 = np.array(f2)
         scale = np.abs(f1).max(axis=0)
         assert np.all(np.abs(f2 - f1) <= 1e-12 * scale), np.abs(f2 - f1).max()
+
+
+def test_two_rank_perturber_lists_are_the_serial_lists(orc):
+    """Sect. 3.1: each rank finds the perturbers in its share of the stars; the lists merged
+    in rank order and cut at N_pert are the serial scan's lists on both ranks, counts summed
+    (Plummer N = 1024 with 100 binaries, N_pert = 32 so that some lists are cut)."""
+    pytest.importorskip("torch")
+    outs = _two_ranks(pertlist=True)
+    snap = ics.plummer_binaries(1024, 100, ics.BASE_SEED + 48, 1.0 / 256, a_lo=1e-3, a_hi=3e-2)
+    ref_l, ref_c = orc.perturbers(snap.m, snap.x, snap.meta["pairs"], gamma=1e-7, nmax=32)
+    assert outs[0]["j"] == [0, 512] and outs[1]["j"] == [512, 1024]
+    assert np.any(ref_c > 32) and np.any((ref_c > 0) & (ref_c < 32))
+    for o in outs:
+        assert np.array_equal(np.array(o["lists"]), ref_l)
+        assert np.array_equal(np.array(o["counts"]), ref_c)
 
 
 def test_diverged_replica_is_reported():
