@@ -109,4 +109,74 @@ __device__ __forceinline__ void ds_predict(const float2 *x2, const float2 *v2, c
     ds_predict_vals(X, V, A, K, d64, hi, lo, vel, m);
 }
 
+// Double-single helpers of the softened potential sums (the energy kernels of
+// the single-system path and of the ensemble). The two-sum steps rely on the
+// including file being compiled without multiply-add contraction.
+__device__ __forceinline__ void en_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void en_fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+// (ah + al) - (bh + bl) as a normalised double-single
+__device__ __forceinline__ void en_diff(float ah, float al, float bh, float bl, float &h, float &l)
+{
+    float s, e;
+    en_two_sum(ah, -bh, s, e);
+    e += al - bl;
+    en_fast_two_sum(s, e, h, l);
+}
+// h + l += bh + bl
+__device__ __forceinline__ void en_acc(float &h, float &l, float bh, float bl)
+{
+    float s, e;
+    en_two_sum(h, bh, s, e);
+    e += l + bl;
+    en_fast_two_sum(s, e, h, l);
+}
+
+// m_j / |r_ij| (softened) as a double-single, from double-single positions and
+// mass: r = x_j - x_i and r^2 + eps^2 to ~2^-46 relative (two-sums and exact
+// squares by FMA), q = (r^2 + eps^2)^(-1/2) from the MUFU estimate, one FP32 and
+// one double-single Newton step (the residual 1 - r^2 y^2 is exact to 2^-46),
+// error ~2^-44 relative.
+__device__ __forceinline__ void en_pair(float4 j0, float4 j1, float2 xi, float2 yi, float2 zi, float2 e2, float &th,
+                                        float &tl)
+{
+    float dh, dl, r2h, r2l, p, e;
+    en_diff(j0.x, j0.y, xi.x, xi.y, dh, dl);
+    r2h = dh * dh;
+    r2l = fmaf(dh, dh, -r2h);
+    r2l = fmaf(2.f * dh, dl, r2l);
+    en_diff(j0.z, j0.w, yi.x, yi.y, dh, dl);
+    p = dh * dh;
+    e = fmaf(dh, dh, -p);
+    e = fmaf(2.f * dh, dl, e);
+    en_acc(r2h, r2l, p, e);
+    en_diff(j1.x, j1.y, zi.x, zi.y, dh, dl);
+    p = dh * dh;
+    e = fmaf(dh, dh, -p);
+    e = fmaf(2.f * dh, dl, e);
+    en_acc(r2h, r2l, p, e);
+    en_acc(r2h, r2l, e2.x, e2.y);
+    float y = rsqrtf(r2h);
+    y = y * fmaf(-0.5f * r2h * y, y, 1.5f);
+    const float a2 = y * y;
+    const float a2e = fmaf(y, y, -a2);
+    const float c = r2h * a2;
+    const float ce = fmaf(r2h, a2, -c);
+    const float res = (1.f - c) - (ce + fmaf(r2h, a2e, r2l * a2));
+    float qh, ql;
+    en_fast_two_sum(y, 0.5f * y * res, qh, ql);
+    th = j1.z * qh;
+    tl = fmaf(j1.z, qh, -th);
+    tl = fmaf(j1.z, ql, tl);
+    tl = fmaf(j1.w, qh, tl);
+}
+
 }  // namespace nb

@@ -80,6 +80,7 @@ struct EnsArgs {
     float2 *x2, *v2, *a2, *k2;   // double-single copies of x, v, a, k
     float2 *t2;              // double-single copy of t (the predictor's time differences on the FP32 pipe)
     float *m32;              // FP32 masses (the j-records' mass)
+    float2 *m2;              // double-single masses (the potential sums)
     float4 *jh, *jl, *jv;    // predicted records
     int32_t *idx;            // per-rank candidate segments of the active list, member segments
     int32_t *idx2;           // the active list in rank order (block steps with many active particles)
@@ -430,37 +431,44 @@ __device__ __forceinline__ void sum_partials(const float2 *part, int64_t s, int6
 
 // ---------------------------------------------------------------- phases
 
-// K and W (softened, FP64) of the member's particles [c0, c1) summed by the CTA.
+// K and W (softened) of the member's particles [c0, c1) summed by the CTA.
 // Every pair once: particle q takes the (N - 1) / 2 particles after it on the
 // ring of the member's indices, and for even N the opposite particle with
 // weight 1/2 (that pair is reached from both ends), so each thread does the
-// same work.
+// same work. The sum of m_j / r over a particle's pairs is double-single on the
+// FP32 pipe (en_pair: r from double-single positions, r^2 + eps^2 to ~2^-46, a
+// Newton-refined inverse square root; ~2^-44 relative per pair); K, m_i phi_i
+// and the sums over particles are FP64, in a fixed order.
 __device__ void energy_chunk(const EnsArgs &E, int64_t base, int64_t N, int64_t c0, int64_t c1, double eps2,
                              EnsSmem *sm, double &K, double &W)
 {
     double ek = 0.0, ew = 0.0;
     const int64_t half = (N - 1) / 2;
+    const float2 e2 = rn_ds_pack(eps2);
+    const int64_t np = E.np;
     for (int64_t q = c0 + threadIdx.x; q < c1; q += kEnsThreads) {
         const int64_t i = base + q;
-        const double xi = E.x[i], yi = E.x[E.np + i], zi = E.x[2 * E.np + i];
-        double phi = 0.0;
+        const float2 xi = E.x2[i], yi = E.x2[np + i], zi = E.x2[2 * np + i];
+        float ph = 0.f, pl = 0.f;
         int64_t jj = q;
         for (int64_t d = 1; d <= half; ++d) {
             jj = jj + 1 < N ? jj + 1 : 0;
             const int64_t j = base + jj;
-            const double dx = E.x[j] - xi, dy = E.x[E.np + j] - yi, dz = E.x[2 * E.np + j] - zi;
-            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-            phi -= E.m[j] * rsqrt(r2);
+            const float2 xj = E.x2[j], yj = E.x2[np + j], zj = E.x2[2 * np + j], mj = E.m2[j];
+            float th, tl;
+            en_pair(make_float4(xj.x, xj.y, yj.x, yj.y), make_float4(zj.x, zj.y, mj.x, mj.y), xi, yi, zi, e2, th, tl);
+            en_acc(ph, pl, th, tl);
         }
         if ((N & 1) == 0) {
             const int64_t j = base + (q + N / 2 < N ? q + N / 2 : q - N / 2);
-            const double dx = E.x[j] - xi, dy = E.x[E.np + j] - yi, dz = E.x[2 * E.np + j] - zi;
-            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-            phi -= 0.5 * (E.m[j] * rsqrt(r2));
+            const float2 xj = E.x2[j], yj = E.x2[np + j], zj = E.x2[2 * np + j], mj = E.m2[j];
+            float th, tl;
+            en_pair(make_float4(xj.x, xj.y, yj.x, yj.y), make_float4(zj.x, zj.y, mj.x, mj.y), xi, yi, zi, e2, th, tl);
+            en_acc(ph, pl, 0.5f * th, 0.5f * tl);
         }
         const double vx = E.v[i], vy = E.v[E.np + i], vz = E.v[2 * E.np + i];
         ek += 0.5 * E.m[i] * (vx * vx + vy * vy + vz * vz);
-        ew += E.m[i] * phi;
+        ew -= E.m[i] * ((double)ph + (double)pl);
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
@@ -840,6 +848,7 @@ struct nb_ensemble {
            *tn = nullptr;
     float2 *x2 = nullptr, *v2 = nullptr, *a2 = nullptr, *k2 = nullptr, *t2 = nullptr;
     float *m32 = nullptr;
+    float2 *m2 = nullptr;
     float4 *jh = nullptr, *jl = nullptr, *jv = nullptr;
     int32_t *idx = nullptr, *idx2 = nullptr;
     float2 *part = nullptr;
@@ -856,7 +865,7 @@ void ensemble_free(nb_ensemble *e)
 {
     if (!e) return;
     void *ptrs[] = {e->off, e->eps2, e->order, e->m, e->x, e->v, e->a, e->k, e->t, e->dt, e->tn, e->x2, e->v2,
-                    e->a2, e->k2, e->t2, e->m32, e->jh, e->jl, e->jv,
+                    e->a2, e->k2, e->t2, e->m32, e->m2, e->jh, e->jl, e->jv,
                     e->idx, e->idx2, e->part, e->queue, e->ready, e->status, e->steps, e->inter, e->energy, e->stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -955,7 +964,7 @@ cudaError_t ensemble_launch(nb_ensemble *e, double t_end, double eta, double dt_
     E.np = e->ntot;
     E.m = e->m; E.x = e->x; E.v = e->v; E.a = e->a; E.k = e->k; E.t = e->t; E.dt = e->dt; E.tn = e->tn;
     E.x2 = e->x2; E.v2 = e->v2; E.a2 = e->a2; E.k2 = e->k2;
-    E.t2 = e->t2; E.m32 = e->m32;
+    E.t2 = e->t2; E.m32 = e->m32; E.m2 = e->m2;
     E.jh = e->jh; E.jl = e->jl; E.jv = e->jv;
     E.idx = e->idx;
     E.idx2 = e->idx2;
@@ -1130,6 +1139,7 @@ nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, cons
     for (float2 **p : {&e->x2, &e->v2, &e->a2, &e->k2}) ECK(ealloc(p, 3 * n));
     ECK(ealloc(&e->t2, n));
     ECK(ealloc(&e->m32, n));
+    ECK(ealloc(&e->m2, n));
     for (float4 **p : {&e->jh, &e->jl, &e->jv}) ECK(ealloc(p, n));
     ECK(ealloc(&e->idx, n));
     ECK(ealloc(&e->idx2, n));
@@ -1172,6 +1182,7 @@ nb_status nb_ensemble_init(nb_ctx *ctx, int32_t nc, const int64_t *offsets, cons
     ECK(cudaMemsetAsync(e->t, 0, n * sizeof(double), st));
     ECK(cudaMemsetAsync(e->t2, 0, n * sizeof(float2), st));
     ens_to_f32<<<blocks, 256, 0, st>>>(e->m, e->m32, n);
+    ens_to_ds<<<blocks, 256, 0, st>>>(e->m, e->m2, n);
     ECK(cudaMemsetAsync(e->ready, 0, nc * sizeof(int32_t), st));
     ECK(cudaMemsetAsync(e->status, 0, nc * sizeof(int32_t), st));
     ECK(cudaMemsetAsync(e->steps, 0, 2 * nc * sizeof(int64_t), st));
