@@ -253,16 +253,14 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
                 put_final(A, ii, c, (double)h + (double)l);
             }
         } else {
-            // many splits: a warp per (particle, component) sum; lane l adds splits l, l + 32,
-            // ... in ascending order (their loads issued together, kFinUnroll per round),
-            // then a fixed butterfly of two-sums combines the lanes. The order of every
-            // addition is the split order per lane, so the batching of the loads does not
-            // change the result.
+            // many splits. The order of every addition is the split order per lane, then a
+            // fixed tree over lanes, so the batching of the loads does not change the result.
             constexpr int kFinUnroll = 4;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             const float2 *base = reinterpret_cast<const float2 *>(A.part);
             if (cnt <= kThreads / 32) {
-                // one sum per warp
+                // one particle: a warp per component; lane l adds splits l, l + 32, ...
+                // (kFinUnroll loads per round), then a butterfly of two-sums over the lanes
                 if (warp < cnt) {
                     const float2 *src = base + (ib0 + warp / 7) * S * kPartStride + warp % 7;
                     float h = 0.f, l = 0.f;
@@ -279,48 +277,42 @@ __device__ void finish_item(const ForceArgs &A, int64_t s, int64_t bx, int S, in
                     if (lane == 0) put_final(A, ib0 + warp / 7, warp % 7, (double)h + (double)l);
                 }
             } else {
-                // four sums in flight per warp, their butterflies interleaved level by level
-                constexpr int kFinTasks = 4;
-                for (int q0 = warp * kFinTasks; q0 < cnt; q0 += (kThreads / 32) * kFinTasks) {
-                    float h[kFinTasks], l[kFinTasks];
-                    const float2 *src[kFinTasks];
+                // a warp per particle: the particle's S partials are S x 64 contiguous
+                // bytes, read with 16-byte loads (kFinLoads issued together). Lane l takes
+                // components 2 (l % 4) and 2 (l % 4) + 1 of splits l / 4, l / 4 + 8, ... and
+                // adds them in ascending split order; a fixed tree over the eight lanes of
+                // each component pair (lane distance 4, 8, 16) finishes the sum.
+                constexpr int kFinLoads = 16;
+                const int qc = lane & 3, sub = lane >> 2;
+                const int np = (int)(ib1 - ib0);
+                for (int pi = warp; pi < np; pi += kThreads / 32) {
+                    const int64_t ii = ib0 + pi;
+                    const float4 *src = reinterpret_cast<const float4 *>(A.part) + ii * S * (kPartStride / 2) + qc;
+                    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+                    for (int sp0 = sub; sp0 < S; sp0 += 8 * kFinLoads) {
+                        float4 v[kFinLoads];
 #pragma unroll
-                    for (int t = 0; t < kFinTasks; ++t) {
-                        h[t] = 0.f;
-                        l[t] = 0.f;
-                        const int q = q0 + t < cnt ? q0 + t : cnt - 1;
-                        src[t] = base + (ib0 + q / 7) * S * kPartStride + q % 7;
-                    }
-                    for (int sp0 = lane; sp0 < S; sp0 += 32 * kFinUnroll) {
-                        float2 v[kFinTasks][kFinUnroll];
-#pragma unroll
-                        for (int t = 0; t < kFinTasks; ++t)
-#pragma unroll
-                            for (int u = 0; u < kFinUnroll; ++u) {
-                                const int sp = sp0 + 32 * u;
-                                v[t][u] = sp < S ? __ldcg(src[t] + sp * kPartStride) : make_float2(0.f, 0.f);
-                            }
-#pragma unroll
-                        for (int t = 0; t < kFinTasks; ++t)
-#pragma unroll
-                            for (int u = 0; u < kFinUnroll; ++u)
-                                if (sp0 + 32 * u < S) ds_add(h[t], l[t], v[t][u].x, v[t][u].y);
-                    }
-#pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        float h2[kFinTasks], l2[kFinTasks];
-#pragma unroll
-                        for (int t = 0; t < kFinTasks; ++t) {
-                            h2[t] = __shfl_xor_sync(0xffffffffu, h[t], off);
-                            l2[t] = __shfl_xor_sync(0xffffffffu, l[t], off);
+                        for (int u = 0; u < kFinLoads; ++u) {
+                            const int sp = sp0 + 8 * u;
+                            v[u] = sp < S ? __ldcg(src + (int64_t)sp * (kPartStride / 2)) : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
 #pragma unroll
-                        for (int t = 0; t < kFinTasks; ++t) ds_add(h[t], l[t], h2[t], l2[t]);
+                        for (int u = 0; u < kFinLoads; ++u)
+                            if (sp0 + 8 * u < S) {
+                                ds_add(h0, l0, v[u].x, v[u].y);
+                                if (qc < 3) ds_add(h1, l1, v[u].z, v[u].w);   // component 7 is padding
+                            }
                     }
 #pragma unroll
-                    for (int t = 0; t < kFinTasks; ++t) {
-                        const int q = q0 + t;
-                        if (lane == 0 && q < cnt) put_final(A, ib0 + q / 7, q % 7, (double)h[t] + (double)l[t]);
+                    for (int off = 4; off <= 16; off <<= 1) {
+                        const float a0 = __shfl_xor_sync(0xffffffffu, h0, off), b0 = __shfl_xor_sync(0xffffffffu, l0, off);
+                        const float a1 = __shfl_xor_sync(0xffffffffu, h1, off), b1 = __shfl_xor_sync(0xffffffffu, l1, off);
+                        ds_add(h0, l0, a0, b0);
+                        ds_add(h1, l1, a1, b1);
+                    }
+                    if (sub == 0) {
+                        put_final(A, ii, 2 * qc, (double)h0 + (double)l0);
+                        if (qc < 3) put_final(A, ii, 2 * qc + 1, (double)h1 + (double)l1);
                     }
                 }
             }

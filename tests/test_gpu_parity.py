@@ -116,6 +116,27 @@ def test_force_all_variants(nb, orc, prec, n, eps):
                     _check(prec, e, (nb.nb_variant_name(c.ctx, v), split, idx.size))
 
 
+def test_force_many_splits_wide_blocks(nb, orc):
+    """Split sums with many splits over wide i-blocks (256 and 32 particles): up to 256
+    split partials per particle (more than one batch of loads per lane in the final
+    sum), a ragged last i-block, against the oracle on the same predicted records."""
+    n = 65536
+    snap = ics.plummer(n, seed=n, eps=1.0 / 256)
+    rng = ics.SplitMix64(n + 1)
+    idx = np.unique(rng.next_u64(700) % n).astype(np.int32)[:600]
+    with nb.Context(precision=0) as c:
+        c.init(snap)
+        nb.nb_predict(c.ctx, 0.0)
+        names = [nb.nb_variant_name(c.ctx, v) for v in range(nb.nb_num_variants(c.ctx))]
+        for name, splits in (("tile R=1 TJ=1", (5, 9, 150, 256)), ("tile R=1 TJ=8", (7, 150))):
+            v = names.index(name)
+            for split in splits:
+                for b in range(32):
+                    nb.nb_set_tuning(c.ctx, b, v, split)
+                e = _forces_vs_oracle(nb, orc, c, snap, idx, 0)
+                _check(0, e, (name, split, idx.size))
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_force_plummer_16k_all_blocks(nb, orc, prec):
     """Plummer N = 16384 (eps = 1/1024): tuned launch configuration, s = 1 .. N."""
