@@ -1385,12 +1385,16 @@ nb_status nb_autotune(nb_ctx *ctx)
                 CK(cudaEventSynchronize(e1));
                 CK(cudaEventElapsedTime(&t3[0], e0, e1));
                 const int reps = t3[0] > 50.f ? 1 : 3;   // long launches: one timing is enough
+                // short launches in batches of k back to back (the event timer reads in
+                // steps of about a microsecond, the size of the differences being ranked)
+                const int k = t3[0] < 0.2f ? std::min(32, std::max(1, (int)(0.2f / std::max(t3[0], 0.005f)))) : 1;
                 for (int r = 0; r < reps; ++r) {
                     CK(cudaEventRecord(e0, ctx->stream));
-                    CK(launch_force(ctx, F));
+                    for (int q = 0; q < k; ++q) CK(launch_force(ctx, F));
                     CK(cudaEventRecord(e1, ctx->stream));
                     CK(cudaEventSynchronize(e1));
                     CK(cudaEventElapsedTime(&t3[r], e0, e1));
+                    t3[r] /= (float)k;
                 }
                 const float tm = reps == 3 ? std::max(std::min(t3[0], t3[1]), std::min(std::max(t3[0], t3[1]), t3[2]))
                                            : t3[0];
