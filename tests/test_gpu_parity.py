@@ -66,7 +66,7 @@ def _errors(prec, a, k, phi, ar, kr, pr, A, K):
     else:
         ea, ek = _cond_scaled(a, ar, A), _cond_scaled(k, kr, K)
     ep = rel_scalar(phi, pr)
-    with np.errstate(divide="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore"):
         kap_a = A / np.linalg.norm(ar, axis=1)
         kap_k = K / np.linalg.norm(kr, axis=1)
     return {"ea": ea, "ek": ek, "ep": ep, "eaf": ea_fwd, "ekf": ek_fwd, "kap_a": kap_a, "kap_k": kap_k}
