@@ -49,6 +49,9 @@ MUTANTS = [
     ("next_block: max for min", "if (ti < tmin) tmin = ti;\n    }\n    int64_t s", "if (ti > tmin) tmin = ti;\n    }\n    int64_t s"),
     # energy
     ("energy: W double-counted", "pot += 0.5 * m[i] * phi[i];", "pot += m[i] * phi[i];"),
+    ("energy: sign of W", "pot += 0.5 * m[i] * phi[i];", "pot -= 0.5 * m[i] * phi[i];"),
+    ("energy: K without the 1/2", "kin += 0.5 * m[i] * v2;", "kin += m[i] * v2;"),
+    ("energy: v^2 drops z", " + v[3 * i + 2] * v[3 * i + 2];", ";"),
     # perturber lists (Sect. 3.1)
     ("perturbers: factor 2 dropped", "double tm = 2.0 * m[j];", "double tm = m[j];"),
     ("perturbers: d^4 for d^6", "double d6 = d2 * d2 * d2;", "double d6 = d2 * d2;"),
