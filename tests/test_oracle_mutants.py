@@ -45,8 +45,15 @@ MUTANTS = [
     # block steps
     ("quantise: 2^ceil", "return ldexp(1.0, e - 1);", "return ldexp(1.0, e);"),
     ("quantise: doubles anywhere", "dt = (u == floor(u)) ? dt2 : dt_old;", "dt = dt2;"),
+    ("quantise: doubles only above 2 dt_old", "} else if (q >= dt2 && dt2 <= dt_max) {", "} else if (q > dt2 && dt2 <= dt_max) {"),
+    ("quantise: no dt_min floor", "    if (dt > dt_max) dt = dt_max;\n    if (dt < dt_min) return 0.0;\n    return dt;\n}\n\ndouble orc_initial_dt",
+     "    if (dt > dt_max) dt = dt_max;\n    return dt;\n}\n\ndouble orc_initial_dt"),
     ("initial dt: |k|/|a|", "eta * amag / kmag", "eta * kmag / amag"),
+    ("initial dt: eta dropped", "eta * amag / kmag", "amag / kmag"),
+    ("initial dt: no power-of-two floor", "double dt = isinf(cand) ? dt_max : pow2_floor(cand);", "double dt = isinf(cand) ? dt_max : cand;"),
     ("next_block: max for min", "if (ti < tmin) tmin = ti;\n    }\n    int64_t s", "if (ti > tmin) tmin = ti;\n    }\n    int64_t s"),
+    ("next_block: first hit only", "if (t[i] + dt[i] == tmin) {", "if (t[i] + dt[i] == tmin && s == 0) {"),
+    ("next_block: t_i for t_i + dt_i", "double ti = t[i] + dt[i];", "double ti = t[i];"),
     # energy
     ("energy: W double-counted", "pot += 0.5 * m[i] * phi[i];", "pot += m[i] * phi[i];"),
     ("energy: sign of W", "pot += 0.5 * m[i] * phi[i];", "pot -= 0.5 * m[i] * phi[i];"),

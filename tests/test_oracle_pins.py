@@ -242,6 +242,9 @@ def test_quantise_rules(orc):
     assert q(10.0, 2.0 ** -8, 3 * 2.0 ** -8) == 2.0 ** -8
     assert q(10.0, 1.0 / 16, 1.0) == 1.0 / 16
     assert q(float("inf"), 2.0 ** -8, 2.0 ** -7) == 2.0 ** -7
+    # a candidate whose power of two is exactly 2 dt_old doubles as well
+    assert q(1.5 * 2.0 ** -7, 2.0 ** -8, 2.0 ** -7) == 2.0 ** -7
+    assert q(1.5 * 2.0 ** -7, 2.0 ** -8, 3 * 2.0 ** -8) == 2.0 ** -8
     # errors
     assert q(float("nan"), 0.5, 0.5, dt_max=1.0) == 0.0
     assert q(0.0, 0.5, 0.5, dt_max=1.0) == 0.0
