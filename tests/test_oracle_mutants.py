@@ -30,10 +30,16 @@ MUTANTS = [
     ("predict: a d^2/6", "a[q] * d2 / 2.0 + k[q] * d3 / 6.0;", "a[q] * d2 / 6.0 + k[q] * d3 / 6.0;"),
     ("predict: k d^3/2", "a[q] * d2 / 2.0 + k[q] * d3 / 6.0;", "a[q] * d2 / 2.0 + k[q] * d3 / 2.0;"),
     ("predict: jerk dropped from v", "vp[q] = v[q] + a[q] * d + k[q] * d2 / 2.0;", "vp[q] = v[q] + a[q] * d;"),
+    ("predict: v d dropped from x", "xp[q] = x[q] + v[q] * d + a[q]", "xp[q] = x[q] + a[q]"),
+    ("predict: a d^2 in v", "vp[q] = v[q] + a[q] * d + k[q] * d2 / 2.0;", "vp[q] = v[q] + a[q] * d2 + k[q] * d2 / 2.0;"),
     # corrector
     ("correct: sign of 6 da", "a2[c] = -6.0 * da / dt2", "a2[c] = 6.0 * da / dt2"),
     ("correct: k_old/k_new swapped", "(4.0 * k_old[c] + 2.0 * k_new[c])", "(2.0 * k_old[c] + 4.0 * k_new[c])"),
     ("correct: 12 da / dt^2", "a3[c] = 12.0 * da / dt3", "a3[c] = 12.0 * da / dt2"),
+    ("correct: da = a_new - a_old", "double da = a_old[c] - a_new[c];", "double da = a_new[c] - a_old[c];"),
+    ("correct: a3 from k_old - k_new", "6.0 * (k_old[c] + k_new[c]) / dt2", "6.0 * (k_old[c] - k_new[c]) / dt2"),
+    ("correct: x a2 dt^4/6", "x1[c] = xp[c] + a2[c] * dt4 / 24.0", "x1[c] = xp[c] + a2[c] * dt4 / 6.0"),
+    ("correct: v a3 dt^4/6", "a3[c] * dt4 / 24.0;", "a3[c] * dt4 / 6.0;"),
     ("correct: a3 dt^5/24", "a3[c] * dt5 / 120.0", "a3[c] * dt5 / 24.0"),
     ("correct: a2 dt^3/2", "v1[c] = vp[c] + a2[c] * dt3 / 6.0", "v1[c] = vp[c] + a2[c] * dt3 / 2.0"),
     ("step: a2p without a3 dt", "a2p[c] = a2[c] + a3[c] * dt;", "a2p[c] = a2[c];"),
@@ -42,6 +48,7 @@ MUTANTS = [
     ("aarseth: |a||a3|", "double num = amag * a2mag + dot3(k_new, k_new);", "double num = amag * a3mag + dot3(k_new, k_new);"),
     ("aarseth: |k||a2|", "double den = kmag * a3mag + dot3(a2p, a2p);", "double den = kmag * a2mag + dot3(a2p, a2p);"),
     ("aarseth: no square root", "return sqrt(eta * num / den);", "return eta * num / den;"),
+    ("aarseth: |a2|^2 dropped", "double den = kmag * a3mag + dot3(a2p, a2p);", "double den = kmag * a3mag;"),
     # block steps
     ("quantise: 2^ceil", "return ldexp(1.0, e - 1);", "return ldexp(1.0, e);"),
     ("quantise: doubles anywhere", "dt = (u == floor(u)) ? dt2 : dt_old;", "dt = dt2;"),
